@@ -18,6 +18,8 @@ def test_golden_config1_reproduced():
         r = fn(C, p.a, p.b, p.eps, p.rho1, p.rho2, d["iters"])
         assert (r.f - torch.tensor(d[name]["f"], dtype=torch.float64)).abs().max() < 1e-13
         assert (r.g - torch.tensor(d[name]["g"], dtype=torch.float64)).abs().max() < 1e-13
-    # both algorithms reach the same fixed point (T3) on this workload
-    assert max(abs(u - v) for u, v in zip(d["plain"]["f"], d["ti"]["f"])) < 1e-10
+    # both algorithms reach the same fixed point (T3) on this workload; plain Sinkhorn's
+    # residual 8.8e-12 at rate ~0.98 per iteration leaves an error of ~residual / 0.02
+    assert d["plain"]["residual"] < 1e-11 and d["ti"]["residual"] < 1e-15
+    assert max(abs(u - v) for u, v in zip(d["plain"]["f"], d["ti"]["f"])) < 1e-9
     assert abs(d["plain"]["value"] - d["ti"]["value"]) < 1e-12
