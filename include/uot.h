@@ -1,0 +1,174 @@
+/*
+ * uot.h -- C ABI of libuot: entropic unbalanced optimal transport with
+ * rho*KL marginal penalties on one GB300 (sm_103a), solved by log-domain
+ * Sinkhorn and by translation-invariant Sinkhorn (H-Sinkhorn).
+ *
+ * Method: Sejourne, Vialard, Peyre, "Faster Unbalanced Optimal Transport:
+ * Translation invariant Sinkhorn and 1-D Frank-Wolfe" (AISTATS 2022).
+ *
+ *   primal  UOT(a,b) = min_{pi>=0} <pi,C> + eps KL(pi|a(x)b)
+ *                      + rho1 KL(pi 1|a) + rho2 KL(pi^T 1|b)      Sec. 1, Eq. (eq-primal-uot-kl)
+ *   dual    F_eps(f,g) = <a, rho1(1-e^{-f/rho1})> + <b, rho2(1-e^{-g/rho2})>
+ *                      - eps <a(x)b, e^{(f(+)g-C)/eps} - 1>       Sec. 1, Eq. (eq-dual-uot-kl)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - f, x, a, rho1 and index i (N of them) form one side; g, y, b, rho2 and
+ *    index j (M of them) the other.  C is N x M.
+ *  - All data pointers are DEVICE pointers on the current CUDA device and are
+ *    owned by the caller: inputs, outputs and the workspace.  The library
+ *    allocates no device memory.
+ *  - Float data is FP32, row-major and contiguous: x is N x dim, y is M x dim,
+ *    C is N x M.  Weights may contain zeros (those points drop out of every
+ *    sum) but no negative, NaN or infinite entries, and each side needs at
+ *    least one positive weight; such data errors are detected on the device
+ *    and reported as UOT_ERR_NONFINITE.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it.  uot_sinkhorn and uot_ti_sinkhorn synchronise the stream
+ *    at every residual check (they decide on the host when to stop) and on
+ *    return; the other calls are asynchronous.
+ *  - `ws` is a device workspace of at least uot_workspace_size() bytes,
+ *    256-byte aligned.  Calls sharing a workspace must not overlap in time.
+ *  - Argument errors are detected on the host before anything is enqueued;
+ *    the call then returns UOT_ERR_INVALID_ARG / UOT_ERR_WORKSPACE /
+ *    UOT_ERR_UNSUPPORTED and uot_last_error() describes the problem.
+ *  - No exception, abort or device trap crosses this interface.
+ */
+#ifndef UOT_H
+#define UOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define UOT_API __attribute__((visibility("default")))
+#else
+#define UOT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  UOT_OK = 0,
+  UOT_ERR_INVALID_ARG = 1,  /* bad size, parameter or pointer                   */
+  UOT_ERR_WORKSPACE = 2,    /* workspace missing, too small or misaligned       */
+  UOT_ERR_CUDA = 3,         /* a CUDA runtime call failed (see uot_last_error)  */
+  UOT_ERR_NONFINITE = 4,    /* NaN/Inf met on the device, or invalid weights    */
+  UOT_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait gave up          */
+  UOT_NOT_CONVERGED = 6,    /* max_iter reached above tol; outputs are valid    */
+  UOT_ERR_UNSUPPORTED = 7   /* valid request this build does not implement      */
+} uot_status;
+
+typedef enum { UOT_COST_POINTS = 0, UOT_COST_DENSE = 1 } uot_cost_kind;
+
+/* One problem.  Cost C_ij = |x_i - y_j|_2^p (points, computed on the fly and
+ * never stored; Sec. 1 and the 1-D experiments of Sec. 4) or a stored matrix
+ * (dense).  eps, rho1, rho2 > 0 and finite (Sec. 1). */
+typedef struct {
+  int32_t n, m;        /* N >= 1 rows (x, a, f), M >= 1 columns (y, b, g)           */
+  int32_t dim;         /* point dimension, 1..64 (points); ignored for dense          */
+  int32_t cost_kind;   /* uot_cost_kind                                               */
+  float p;             /* exponent p >= 1 of the points cost; p == 2 is the fast path */
+  int32_t reserved;
+  double eps, rho1, rho2;
+  const float* x;      /* device, N x dim (points)        */
+  const float* y;      /* device, M x dim (points)        */
+  const float* C;      /* device, N x M (dense)           */
+  const float* a;      /* device, N weights, a_i >= 0      */
+  const float* b;      /* device, M weights, b_j >= 0      */
+} uot_problem;
+
+/* Iteration control for uot_sinkhorn / uot_ti_sinkhorn. */
+typedef struct {
+  int32_t max_iter;          /* >= 1 full iterations (g half-step, then f half-step)          */
+  int32_t check_every;       /* >= 1: residual tested against tol every check_every iterations */
+  double tol;                /* >= 0 fixed-point residual tolerance in cost units; 0 = run     */
+                             /* exactly max_iter iterations                                      */
+  int32_t warm_start;        /* nonzero: f holds the initial potential on entry                 */
+  int32_t reserved;
+  float* residual_history;   /* device, nullable, >= max_iter+1 floats: entry t is the residual */
+                             /* of iterate t (t = 1..iters); entry 0 is unused                   */
+} uot_options;
+
+/* Outcome of a solve, written to host memory before the call returns. */
+typedef struct {
+  int32_t iters;       /* index T of the returned iterate                                   */
+  int32_t converged;   /* 1 if residual <= tol                                              */
+  int32_t status;      /* uot_status of the solve                                           */
+  int32_t reserved;
+  double residual;     /* fixed-point residual of the returned (f, g), see below            */
+  double lambda;       /* TI: lambda*(fb_T, gb_T) of Prop. 2; plain: 0                      */
+} uot_result;
+
+/* Bytes of device workspace needed by any entry point on `prob` (0 on an
+ * invalid problem; uot_last_error() then says why).  Depends on the problem's
+ * sizes, dim, cost kind and on the current device's SM count. */
+UOT_API size_t uot_workspace_size(const uot_problem* prob);
+
+/* Row or column softmin sweep, the O(NM) primitive of every Sinkhorn variant
+ * (Sec. 3, definition of Smin):
+ *   axis 0: out_i = Smin_b^eps(C(x_i,.) - pot) = -eps log sum_j b_j exp((pot_j - C_ij)/eps),
+ *           pot and out are M- and N-vectors;
+ *   axis 1: out_j = Smin_a^eps(C(.,y_j) - pot) = -eps log sum_i a_i exp((pot_i - C_ij)/eps),
+ *           pot and out are N- and M-vectors.
+ * Asynchronous. */
+UOT_API uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, float* out,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Plain (F-)Sinkhorn, Sec. 3:
+ *   g_{t+1} = rho2/(rho2+eps) Smin_a^eps(C - f_t),  f_{t+1} = rho1/(rho1+eps) Smin_b^eps(C - g_{t+1}),
+ * from f_0 = 0 (or f on entry when warm_start).  On return f, g hold (f_T, g_T).
+ * The residual is the sup-norm violation of the F-Sinkhorn fixed-point
+ * equations by the returned pair (cost units):
+ *   r = max(|f - rho1/(rho1+eps) Smin_b^eps(C - g)|_inf, |g - rho2/(rho2+eps) Smin_a^eps(C - f)|_inf);
+ * the first term is zero up to rounding because f is computed from g, so the
+ * library evaluates the second, which costs one more column sweep at exit.
+ * Returns UOT_OK, UOT_NOT_CONVERGED (outputs valid) or an error. */
+UOT_API uot_status uot_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                        uot_result* result, void* ws, size_t ws_bytes, void* stream);
+
+/* Translation-invariant Sinkhorn = H-Sinkhorn (Sec. 3, Prop. 4; general
+ * rho1 != rho2 from the proof of Prop. 4 in App. B):
+ *   g_hat = rho2/(rho2+eps) Smin_a^eps(C - fb) - eps/(eps+rho2) rho2/(rho1+rho2) Smin_a^rho1(fb)
+ *   gb    = g_hat + k_g/(1-k_g) Smin_b^rho2(g_hat),   k_g = eps/(eps+rho2) rho1/(rho1+rho2)
+ * and symmetrically for fb, from fb_0 = 0 (or f on entry).  The two mass
+ * reductions Smin^rho and the optimal translation lambda* (Prop. 2) are FP64.
+ * On return f, g hold (f, g) = Phi(fb_T, gb_T) = (fb_T + lambda*, gb_T - lambda*).
+ * Residual as for uot_sinkhorn, on the translated pair. */
+UOT_API uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                           uot_result* result, void* ws, size_t ws_bytes, void* stream);
+
+/* Dual objective F_eps(f, g) (Sec. 1, Eq. eq-dual-uot-kl), FP64, written to
+ * out[0] (device).  If out has room for 3 doubles (want_primal != 0) it also
+ * writes out[1] = primal objective (Eq. eq-primal-uot-kl) of the plan
+ * pi_ij = a_i b_j e^{(f_i+g_j-C_ij)/eps} and out[2] = m(pi); at the optimum
+ * out[0] == out[1] (zero duality gap).  One row sweep (two with the primal)
+ * plus O(N+M) FP64 reductions.  Asynchronous. */
+UOT_API uot_status uot_dual_value(const uot_problem* prob, const float* f, const float* g, double* out,
+                          int32_t want_primal, void* ws, size_t ws_bytes, void* stream);
+
+/* Gradient of UOT = F_eps(f*, g*) with respect to a, b, x, y by the envelope
+ * theorem (used by the paper in the proof of Prop. 1): the partial
+ * derivatives of F_eps at the given (f, g), which should be the optimal pair:
+ *   grad_a_i = rho1 (1 - e^{-f_i/rho1}) - eps (e^{(f_i - S_i)/eps} - m(b)),  S = Smin_b^eps(C - g)
+ *   grad_b_j = rho2 (1 - e^{-g_j/rho2}) - eps (e^{(g_j - S'_j)/eps} - m(a)), S' = Smin_a^eps(C - f)
+ *   grad_x_i = sum_j pi_ij dC_ij/dx_i,   grad_y_j = sum_i pi_ij dC_ij/dy_j,
+ * with pi formed on the fly and never stored.  Each output pointer may be NULL
+ * (not computed); grad_x / grad_y need the points cost.  Asynchronous. */
+UOT_API uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, float* grad_a,
+                    float* grad_b, float* grad_x, float* grad_y, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* Message describing the last error of the calling thread ("" if none). */
+UOT_API const char* uot_last_error(void);
+
+/* Library version string. */
+UOT_API const char* uot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UOT_H */

@@ -1,0 +1,373 @@
+// C ABI of libuot (declared in include/uot.h): argument validation, workspace
+// layout, and the host-side iteration driver of plain and translation-invariant
+// Sinkhorn.  All arithmetic runs in the kernels of sweep_points.cu,
+// sweep_dense.cu and epilogue.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "uot_internal.cuh"
+
+namespace uot {
+
+namespace {
+thread_local std::string g_last_error;
+
+uot_status fail(uot_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+uot_status fail(uot_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+uot_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(UOT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define UOT_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+uot_status validate(const uot_problem* p) {
+  if (!p) return fail(UOT_ERR_INVALID_ARG, "problem is NULL");
+  if (p->n < 1 || p->m < 1) return fail(UOT_ERR_INVALID_ARG, "n and m must be >= 1 (got %d, %d)", p->n, p->m);
+  if (!finite_pos(p->eps) || !finite_pos(p->rho1) || !finite_pos(p->rho2))
+    return fail(UOT_ERR_INVALID_ARG, "eps, rho1, rho2 must be finite and > 0");
+  if (!p->a || !p->b) return fail(UOT_ERR_INVALID_ARG, "weights a and b must be device pointers");
+  if (p->cost_kind == UOT_COST_POINTS) {
+    if (p->dim < 1 || p->dim > 64) return fail(UOT_ERR_INVALID_ARG, "dim must be in 1..64 (got %d)", p->dim);
+    if (!(p->p >= 1.0f) || !isfinite(p->p)) return fail(UOT_ERR_INVALID_ARG, "cost exponent p must be >= 1");
+    if (!p->x || !p->y) return fail(UOT_ERR_INVALID_ARG, "points x and y must be device pointers");
+    if ((long long)p->n * p->dim > (1ll << 31) || (long long)p->m * p->dim > (1ll << 31))
+      return fail(UOT_ERR_INVALID_ARG, "point arrays larger than 2^31 elements");
+  } else if (p->cost_kind == UOT_COST_DENSE) {
+    if (!p->C) return fail(UOT_ERR_INVALID_ARG, "dense cost C must be a device pointer");
+    if (reinterpret_cast<uintptr_t>(p->C) & 15) return fail(UOT_ERR_INVALID_ARG, "C must be 16-byte aligned");
+  } else {
+    return fail(UOT_ERR_INVALID_ARG, "unknown cost_kind %d", p->cost_kind);
+  }
+  return UOT_OK;
+}
+
+struct PartSizes { size_t rows, cols; };
+
+PartSizes part_sizes(const uot_problem& p) {
+  PartSizes ps{0, 0};
+  if (p.cost_kind == UOT_COST_POINTS) {
+    for (int mom = 0; mom < 2; ++mom) {
+      const int ch = 2 + (mom ? p.dim : 0);
+      SweepGeom gr = points_geom(p.n, p.m, p.dim, mom);
+      SweepGeom gc = points_geom(p.m, p.n, p.dim, mom);
+      ps.rows = ps.rows > (size_t)gr.splits * ch * p.n ? ps.rows : (size_t)gr.splits * ch * p.n;
+      ps.cols = ps.cols > (size_t)gc.splits * ch * p.m ? ps.cols : (size_t)gc.splits * ch * p.m;
+    }
+  } else {
+    SweepGeom gr = dense_row_geom(p.n, p.m);
+    SweepGeom gc = dense_col_geom(p.n, p.m);
+    ps.rows = (size_t)gr.splits * 2 * p.n;
+    ps.cols = (size_t)gc.splits * 2 * p.m;
+  }
+  return ps;
+}
+
+struct WsLayout {
+  size_t state, ln_a, ln_b, l2_a, l2_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, total;
+};
+
+WsLayout ws_layout(const uot_problem& p) {
+  WsLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  L.state = take(sizeof(DevState));
+  L.ln_a = take(sizeof(double) * p.n);
+  L.ln_b = take(sizeof(double) * p.m);
+  L.l2_a = take(sizeof(float) * p.n);
+  L.l2_b = take(sizeof(float) * p.m);
+  L.g_alt = take(sizeof(float) * p.m);
+  L.f_tmp = take(sizeof(float) * p.n);
+  L.g_tmp = take(sizeof(float) * p.m);
+  const PartSizes ps = part_sizes(p);
+  L.part_r = take(sizeof(float) * ps.rows);
+  L.part_c = take(sizeof(float) * ps.cols);
+  L.blk = take(sizeof(double) * kMaxBlocks * 10);
+  L.total = off;
+  return L;
+}
+
+struct Ctx {
+  uot_problem p;
+  DevState* state;
+  double *ln_a, *ln_b, *blk;
+  float *l2_a, *l2_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;
+  cudaStream_t st;
+  double s;  // log2(e) / eps
+};
+
+uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* stream, Ctx* c) {
+  uot_status v = validate(prob);
+  if (v != UOT_OK) return v;
+  if (!ws) return fail(UOT_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(UOT_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  const WsLayout L = ws_layout(*prob);
+  if (ws_bytes < L.total)
+    return fail(UOT_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.total);
+  char* b = static_cast<char*>(ws);
+  c->p = *prob;
+  c->state = reinterpret_cast<DevState*>(b + L.state);
+  c->ln_a = reinterpret_cast<double*>(b + L.ln_a);
+  c->ln_b = reinterpret_cast<double*>(b + L.ln_b);
+  c->l2_a = reinterpret_cast<float*>(b + L.l2_a);
+  c->l2_b = reinterpret_cast<float*>(b + L.l2_b);
+  c->g_alt = reinterpret_cast<float*>(b + L.g_alt);
+  c->f_tmp = reinterpret_cast<float*>(b + L.f_tmp);
+  c->g_tmp = reinterpret_cast<float*>(b + L.g_tmp);
+  c->part_r = reinterpret_cast<float*>(b + L.part_r);
+  c->part_c = reinterpret_cast<float*>(b + L.part_c);
+  c->blk = reinterpret_cast<double*>(b + L.blk);
+  c->st = static_cast<cudaStream_t>(stream);
+  c->s = kLog2e / prob->eps;
+  return UOT_OK;
+}
+
+// Common preamble: zero the state, log weights of both sides.
+uot_status prepare(Ctx& c) {
+  UOT_CUDA(cudaMemsetAsync(c.state, 0, sizeof(DevState), c.st));
+  UOT_CUDA(launch_log_weights(c.p.a, c.p.n, c.ln_a, c.l2_a, c.state, c.st));
+  UOT_CUDA(launch_log_weights(c.p.b, c.p.m, c.ln_b, c.l2_b, c.state, c.st));
+  return UOT_OK;
+}
+
+// One softmin sweep: axis 0 -> queries are rows (x side), keys the y side;
+// axis 1 -> queries are columns (y side), keys the x side.  Returns the number
+// of key chunks (splits) written to the partial buffer.
+uot_status sweep(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits) {
+  const uot_problem& p = c.p;
+  float* part = axis == 0 ? c.part_r : c.part_c;
+  if (p.cost_kind == UOT_COST_POINTS) {
+    SideDesc X{p.x, c.l2_a, c.ln_a, p.n}, Y{p.y, c.l2_b, c.ln_b, p.m};
+    const SideDesc& q = axis == 0 ? X : Y;
+    const SideDesc& k = axis == 0 ? Y : X;
+    SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
+    *splits = g.splits;
+    UOT_CUDA(launch_points_sweep(q, k, p.dim, p.p, pot, shift, c.s, moments, part, g, c.st));
+  } else {
+    SweepGeom g = axis == 0 ? dense_row_geom(p.n, p.m) : dense_col_geom(p.n, p.m);
+    *splits = g.splits;
+    UOT_CUDA(launch_dense_sweep(axis, p.C, p.n, p.m, axis == 0 ? c.l2_b : c.l2_a, pot, shift, c.s, part, g,
+                                c.st));
+  }
+  return UOT_OK;
+}
+
+uot_status read_flags(Ctx& c, int* status, float* resid) {
+  struct { int status; float resid; } h;
+  UOT_CUDA(cudaMemcpyAsync(&h, &c.state->status, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+  UOT_CUDA(cudaStreamSynchronize(c.st));
+  *status = h.status;
+  *resid = h.resid;
+  return UOT_OK;
+}
+
+uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                 uot_result* res, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
+  if (v != UOT_OK) return v;
+  if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");
+  if (!f || !g) return fail(UOT_ERR_INVALID_ARG, "f and g must be device pointers");
+  if (opt->max_iter < 1) return fail(UOT_ERR_INVALID_ARG, "max_iter must be >= 1");
+  if (opt->check_every < 1) return fail(UOT_ERR_INVALID_ARG, "check_every must be >= 1");
+  if (!(opt->tol >= 0.0) || !isfinite(opt->tol)) return fail(UOT_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  const uot_problem& p = c.p;
+  v = prepare(c);
+  if (v != UOT_OK) return v;
+  if (!opt->warm_start) UOT_CUDA(cudaMemsetAsync(f, 0, sizeof(float) * p.n, c.st));
+  UOT_CUDA(cudaMemsetAsync(g, 0, sizeof(float) * p.m, c.st));
+  if (ti) UOT_CUDA(launch_ti_init(f, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
+  float* gbuf[2] = {g, c.g_alt};
+  const int mode = ti ? EPI_TI : EPI_PLAIN;
+  int t = 0, status = 0;
+  float r = NAN;
+  for (;;) {
+    // g half-step of iteration t+1: column sweep over x with fb_t = f_hat + cf
+    const int so = (t + 1) & 1, si = t & 1;
+    int splits = 0;
+    v = sweep(c, 1, f, ti ? &c.state->slot[si].cf : nullptr, false, &splits);
+    if (v != UOT_OK) return v;
+    EpiParams e{};
+    e.mode = mode; e.nq = p.m; e.splits = splits; e.moments = 0; e.s = c.s;
+    e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1; e.out_is_f = 0; e.lnw_o = c.ln_b;
+    e.old_out = (t >= 1) ? gbuf[si] : nullptr; e.out = gbuf[so];
+    e.resid_hist = opt->residual_history; e.hist_index = t;
+    e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
+    UOT_CUDA(launch_combine(e, c.st));
+    const bool last = (t == opt->max_iter);
+    if (t >= 1 && (last || (opt->tol > 0.0 && t % opt->check_every == 0))) {
+      v = read_flags(c, &status, &r);
+      if (v != UOT_OK) return v;
+      if (status != 0 || isnan(r)) break;
+      if (last || r <= opt->tol) break;
+    }
+    // f half-step of iteration t+1: row sweep over y with gb_{t+1} = g_hat + cg
+    v = sweep(c, 0, gbuf[so], ti ? &c.state->slot[so].cg : nullptr, false, &splits);
+    if (v != UOT_OK) return v;
+    EpiParams ef = e;
+    ef.nq = p.n; ef.splits = splits; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
+    ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = f; ef.resid_hist = nullptr;
+    ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r;
+    UOT_CUDA(launch_combine(ef, c.st));
+    ++t;
+  }
+  UOT_CUDA(launch_finalize(ti ? 1 : 0, f, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.st));
+  Slot slot{};
+  UOT_CUDA(cudaMemcpyAsync(&slot, &c.state->slot[t & 1], sizeof(Slot), cudaMemcpyDeviceToHost, c.st));
+  UOT_CUDA(cudaStreamSynchronize(c.st));
+  uot_status out = UOT_OK;
+  const bool converged = !isnan(r) && r <= opt->tol;
+  if (status & kStatusBadWeights) out = fail(UOT_ERR_NONFINITE, "negative, NaN or infinite weights");
+  else if (status != 0 || isnan(r)) out = fail(UOT_ERR_NONFINITE, "non-finite value met during the iteration");
+  else if (opt->tol > 0.0 && !converged) out = UOT_NOT_CONVERGED;
+  if (res) {
+    res->iters = t;
+    res->converged = converged ? 1 : 0;
+    res->status = out;
+    res->reserved = 0;
+    res->residual = r;
+    res->lambda = ti ? slot.lam : 0.0;
+  }
+  return out;
+}
+
+}  // namespace
+
+int device_sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+}  // namespace uot
+
+using namespace uot;
+
+extern "C" {
+
+size_t uot_workspace_size(const uot_problem* prob) {
+  if (validate(prob) != UOT_OK) return 0;
+  return ws_layout(*prob).total;
+}
+
+uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, float* out, void* ws,
+                       size_t ws_bytes, void* stream) {
+  Ctx c;
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
+  if (v != UOT_OK) return v;
+  if (axis != 0 && axis != 1) return fail(UOT_ERR_INVALID_ARG, "axis must be 0 or 1");
+  if (!pot || !out) return fail(UOT_ERR_INVALID_ARG, "pot and out must be device pointers");
+  v = prepare(c);
+  if (v != UOT_OK) return v;
+  int splits = 0;
+  v = sweep(c, axis, pot, nullptr, false, &splits);
+  if (v != UOT_OK) return v;
+  EpiParams e{};
+  e.mode = EPI_SOFTMIN; e.nq = axis == 0 ? c.p.n : c.p.m; e.splits = splits; e.s = c.s;
+  e.eps = c.p.eps; e.rho_o = axis == 0 ? c.p.rho1 : c.p.rho2; e.rho_i = axis == 0 ? c.p.rho2 : c.p.rho1;
+  e.out_is_f = axis == 0; e.lnw_o = axis == 0 ? c.ln_a : c.ln_b; e.out = out; e.state = c.state;
+  e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk;
+  UOT_CUDA(launch_combine(e, c.st));
+  return UOT_OK;
+}
+
+uot_status uot_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                        uot_result* result, void* ws, size_t ws_bytes, void* stream) {
+  return solve(false, prob, opt, f, g, result, ws, ws_bytes, stream);
+}
+
+uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                           uot_result* result, void* ws, size_t ws_bytes, void* stream) {
+  return solve(true, prob, opt, f, g, result, ws, ws_bytes, stream);
+}
+
+uot_status uot_dual_value(const uot_problem* prob, const float* f, const float* g, double* out,
+                          int32_t want_primal, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
+  if (v != UOT_OK) return v;
+  if (!f || !g || !out) return fail(UOT_ERR_INVALID_ARG, "f, g and out must be device pointers");
+  v = prepare(c);
+  if (v != UOT_OK) return v;
+  int sr = 0, sc = 0;
+  v = sweep(c, 0, g, nullptr, false, &sr);
+  if (v != UOT_OK) return v;
+  if (want_primal) {
+    v = sweep(c, 1, f, nullptr, false, &sc);
+    if (v != UOT_OK) return v;
+  }
+  DualParams d{};
+  d.n = c.p.n; d.m = c.p.m; d.splits_r = sr; d.splits_c = sc; d.s = c.s; d.eps = c.p.eps;
+  d.rho1 = c.p.rho1; d.rho2 = c.p.rho2; d.f = f; d.g = g; d.a = c.p.a; d.b = c.p.b;
+  d.ln_a = c.ln_a; d.ln_b = c.ln_b; d.part_r = c.part_r; d.part_c = want_primal ? c.part_c : nullptr;
+  d.blk = c.blk; d.state = c.state; d.out = out; d.want_primal = want_primal;
+  UOT_CUDA(launch_dual(d, c.st));
+  return UOT_OK;
+}
+
+uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, float* grad_a, float* grad_b,
+                    float* grad_x, float* grad_y, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
+  if (v != UOT_OK) return v;
+  if (!f || !g) return fail(UOT_ERR_INVALID_ARG, "f and g must be device pointers");
+  if ((grad_x || grad_y) && c.p.cost_kind != UOT_COST_POINTS)
+    return fail(UOT_ERR_INVALID_ARG, "point gradients need the points cost");
+  v = prepare(c);
+  if (v != UOT_OK) return v;
+  const uot_problem& p = c.p;
+  for (int side = 0; side < 2; ++side) {
+    float* gw = side == 0 ? grad_a : grad_b;
+    float* gpts = side == 0 ? grad_x : grad_y;
+    if (!gw && !gpts) continue;
+    const bool mom = gpts != nullptr;
+    int splits = 0;
+    // side 0: rows (x side) against y with pot g; side 1: columns against x with pot f
+    v = sweep(c, side, side == 0 ? g : f, nullptr, mom, &splits);
+    if (v != UOT_OK) return v;
+    UOT_CUDA(launch_mass(side == 0 ? p.b : p.a, side == 0 ? p.m : p.n, c.blk, c.state, 0, c.st));
+    GradParams gp{};
+    gp.nq = side == 0 ? p.n : p.m; gp.splits = splits; gp.dim = p.dim; gp.moments = mom ? p.dim : 0;
+    gp.s = c.s; gp.eps = p.eps; gp.rho_o = side == 0 ? p.rho1 : p.rho2; gp.p = p.p;
+    gp.pot_o = side == 0 ? f : g; gp.part = side == 0 ? c.part_r : c.part_c;
+    gp.grad_w = gw; gp.grad_pts = gpts; gp.lnw_o = side == 0 ? c.ln_a : c.ln_b; gp.state = c.state;
+    UOT_CUDA(launch_grad_epilogue(gp, c.st));
+  }
+  return UOT_OK;
+}
+
+const char* uot_last_error(void) { return g_last_error.c_str(); }
+
+const char* uot_version(void) { return "uot 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

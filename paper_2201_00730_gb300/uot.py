@@ -1,0 +1,276 @@
+"""Python binding of libuot (ctypes over the C ABI of include/uot.h).
+
+Argument marshalling only: every step of every solve runs in the CUDA kernels
+of libuot.so.  PyTorch provides device memory and the current stream.  There
+is no CPU fallback: if the library is missing or no GPU is present, calls
+raise.
+
+Paper: Sejourne, Vialard, Peyre, "Faster Unbalanced Optimal Transport:
+Translation invariant Sinkhorn and 1-D Frank-Wolfe" (AISTATS 2022).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libuot.so")
+
+UOT_OK = 0
+UOT_NOT_CONVERGED = 6
+STATUS_NAMES = {0: "UOT_OK", 1: "UOT_ERR_INVALID_ARG", 2: "UOT_ERR_WORKSPACE", 3: "UOT_ERR_CUDA",
+                4: "UOT_ERR_NONFINITE", 5: "UOT_ERR_TIMEOUT", 6: "UOT_NOT_CONVERGED", 7: "UOT_ERR_UNSUPPORTED"}
+COST_POINTS, COST_DENSE = 0, 1
+
+
+class UOTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("dim", C.c_int32), ("cost_kind", C.c_int32),
+                ("p", C.c_float), ("reserved", C.c_int32),
+                ("eps", C.c_double), ("rho1", C.c_double), ("rho2", C.c_double),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("C", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double),
+                ("warm_start", C.c_int32), ("reserved", C.c_int32), ("residual_history", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("residual", C.c_double), ("lambda_", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libuot.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libuot.so not found at {LIB_PATH}: build it with "
+                               f"`python -m paper_2201_00730_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        P, V, S = C.POINTER(Problem), C.c_void_p, C.c_size_t
+        L.uot_workspace_size.argtypes = [P]
+        L.uot_workspace_size.restype = S
+        L.uot_softmin.argtypes = [P, C.c_int32, V, V, V, S, V]
+        L.uot_softmin.restype = C.c_int
+        for fn in (L.uot_sinkhorn, L.uot_ti_sinkhorn):
+            fn.argtypes = [P, C.POINTER(Options), V, V, C.POINTER(Result), V, S, V]
+            fn.restype = C.c_int
+        L.uot_dual_value.argtypes = [P, V, V, V, C.c_int32, V, S, V]
+        L.uot_dual_value.restype = C.c_int
+        L.uot_grad.argtypes = [P, V, V, V, V, V, V, V, S, V]
+        L.uot_grad.restype = C.c_int
+        L.uot_last_error.argtypes = []
+        L.uot_last_error.restype = C.c_char_p
+        L.uot_version.argtypes = []
+        L.uot_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, allow=(UOT_OK,)) -> int:
+    if status not in allow:
+        raise UOTError(status, lib().uot_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev_f32(t, name, shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Spec:
+    """Device-resident problem: points (x, y) or a dense cost C, weights a, b, parameters."""
+    a: torch.Tensor
+    b: torch.Tensor
+    eps: float
+    rho1: float
+    rho2: float
+    x: torch.Tensor | None = None
+    y: torch.Tensor | None = None
+    C: torch.Tensor | None = None
+    p: float = 2.0
+
+    def __post_init__(self):
+        if self.C is None and (self.x is None or self.y is None):
+            raise ValueError("give points x and y, or a dense cost C")
+        if self.x is not None and self.x.dim() == 1:
+            self.x = self.x[:, None].contiguous()
+        if self.y is not None and self.y.dim() == 1:
+            self.y = self.y[:, None].contiguous()
+        n, m = self.a.shape[0], self.b.shape[0]
+        _dev_f32(self.a, "a", (n,))
+        _dev_f32(self.b, "b", (m,))
+        if self.C is not None:
+            _dev_f32(self.C, "C", (n, m))
+        else:
+            _dev_f32(self.x, "x", (n, self.x.shape[1]))
+            _dev_f32(self.y, "y", (m, self.x.shape[1]))
+
+    @property
+    def n(self):
+        return self.a.shape[0]
+
+    @property
+    def m(self):
+        return self.b.shape[0]
+
+    def struct(self) -> Problem:
+        dense = self.C is not None
+        return Problem(self.n, self.m, 0 if dense else self.x.shape[1], COST_DENSE if dense else COST_POINTS,
+                       float(self.p), 0, float(self.eps), float(self.rho1), float(self.rho2),
+                       None if dense else self.x.data_ptr(), None if dense else self.y.data_ptr(),
+                       self.C.data_ptr() if dense else None, self.a.data_ptr(), self.b.data_ptr())
+
+    def workspace(self) -> torch.Tensor:
+        pr = self.struct()
+        nbytes = lib().uot_workspace_size(C.byref(pr))
+        if nbytes == 0:
+            raise UOTError(1, lib().uot_last_error().decode())
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.a.device)
+
+
+def workspace_size(spec: Spec) -> int:
+    pr = spec.struct()
+    return int(lib().uot_workspace_size(C.byref(pr)))
+
+
+def softmin(spec: Spec, pot: torch.Tensor, axis: int, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """axis 0: Smin_b^eps(C(x_i,.) - pot) for every i; axis 1: Smin_a^eps(C(.,y_j) - pot) for every j."""
+    pr = spec.struct()
+    nq, nk = (spec.n, spec.m) if axis == 0 else (spec.m, spec.n)
+    _dev_f32(pot, "pot", (nk,))
+    out = torch.empty(nq, dtype=torch.float32, device=spec.a.device)
+    ws = spec.workspace() if ws is None else ws
+    _check(lib().uot_softmin(C.byref(pr), axis, _ptr(pot), _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+@dataclass
+class SolveOut:
+    f: torch.Tensor
+    g: torch.Tensor
+    iters: int
+    converged: bool
+    status: int
+    residual: float
+    lam: float
+    history: torch.Tensor | None = None
+
+
+def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0, check_every: int = 10,
+          f0: torch.Tensor | None = None, history: bool = False, ws: torch.Tensor | None = None,
+          f: torch.Tensor | None = None, g: torch.Tensor | None = None) -> SolveOut:
+    """Plain ('plain') or translation-invariant ('ti') Sinkhorn on the device.
+
+    Returns the translated potentials (f, g), the iteration count and the
+    fixed-point residual of the returned pair.
+    """
+    pr = spec.struct()
+    dev = spec.a.device
+    f = torch.empty(spec.n, dtype=torch.float32, device=dev) if f is None else _dev_f32(f, "f", (spec.n,))
+    g = torch.empty(spec.m, dtype=torch.float32, device=dev) if g is None else _dev_f32(g, "g", (spec.m,))
+    if f0 is not None:
+        f.copy_(f0)
+    hist = torch.full((max_iter + 1,), float("nan"), dtype=torch.float32, device=dev) if history else None
+    opt = Options(int(max_iter), int(check_every), float(tol), 1 if f0 is not None else 0, 0,
+                  None if hist is None else hist.data_ptr())
+    res = Result()
+    ws = spec.workspace() if ws is None else ws
+    fn = lib().uot_ti_sinkhorn if method == "ti" else lib().uot_sinkhorn
+    if method not in ("ti", "plain"):
+        raise ValueError("method must be 'ti' or 'plain'")
+    st = fn(C.byref(pr), C.byref(opt), _ptr(f), _ptr(g), C.byref(res), _ptr(ws), ws.numel(), _stream())
+    _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
+    return SolveOut(f, g, res.iters, bool(res.converged), st, res.residual, res.lambda_, hist)
+
+
+def dual_value(spec: Spec, f: torch.Tensor, g: torch.Tensor, primal: bool = False,
+               ws: torch.Tensor | None = None) -> torch.Tensor:
+    """F_eps(f, g) (and, with primal=True, the primal value of the induced plan and its mass), FP64."""
+    pr = spec.struct()
+    _dev_f32(f, "f", (spec.n,))
+    _dev_f32(g, "g", (spec.m,))
+    out = torch.zeros(3, dtype=torch.float64, device=spec.a.device)
+    ws = spec.workspace() if ws is None else ws
+    _check(lib().uot_dual_value(C.byref(pr), _ptr(f), _ptr(g), _ptr(out), 1 if primal else 0, _ptr(ws),
+                                ws.numel(), _stream()))
+    return out if primal else out[:1]
+
+
+def grad(spec: Spec, f: torch.Tensor, g: torch.Tensor, wrt=("a", "b", "x", "y"),
+         ws: torch.Tensor | None = None) -> dict:
+    """Envelope gradients of UOT at the optimal pair (f, g) with respect to a, b, x, y."""
+    pr = spec.struct()
+    _dev_f32(f, "f", (spec.n,))
+    _dev_f32(g, "g", (spec.m,))
+    dev = spec.a.device
+    out = {}
+    if "a" in wrt:
+        out["a"] = torch.empty(spec.n, dtype=torch.float32, device=dev)
+    if "b" in wrt:
+        out["b"] = torch.empty(spec.m, dtype=torch.float32, device=dev)
+    if "x" in wrt and spec.C is None:
+        out["x"] = torch.empty_like(spec.x)
+    if "y" in wrt and spec.C is None:
+        out["y"] = torch.empty_like(spec.y)
+    ws = spec.workspace() if ws is None else ws
+    _check(lib().uot_grad(C.byref(pr), _ptr(f), _ptr(g), _ptr(out.get("a")), _ptr(out.get("b")),
+                          _ptr(out.get("x")), _ptr(out.get("y")), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+class UOTLoss(torch.autograd.Function):
+    """UOT(a, b; x, y) as a differentiable scalar.
+
+    Forward: TI-Sinkhorn to `tol`, then the FP64 dual value at the returned pair.
+    Backward: envelope gradients (uot_grad) scaled by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, x, y, a, b, eps, rho1, rho2, max_iter=10000, tol=1e-6, check_every=10):
+        spec = Spec(a.detach().contiguous(), b.detach().contiguous(), eps, rho1, rho2,
+                    x=x.detach().contiguous(), y=y.detach().contiguous())
+        ws = spec.workspace()
+        r = solve(spec, "ti", max_iter=max_iter, tol=tol, check_every=check_every, ws=ws)
+        val = dual_value(spec, r.f, r.g, ws=ws)[0]
+        ctx.spec, ctx.f, ctx.g = spec, r.f, r.g
+        return val.to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, gout):
+        gr = grad(ctx.spec, ctx.f, ctx.g)
+        s = gout.to(torch.float32)
+        return (gr["x"] * s, gr["y"] * s, gr["a"] * s, gr["b"] * s, None, None, None, None, None, None)
+
+
+def version() -> str:
+    return lib().uot_version().decode()

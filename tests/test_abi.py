@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every entry point of include/uot.h;
+struct layouts agree between the header and the Python binding; argument errors
+come back before any device work (no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "uot.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2201_00730_gb300 import build, uot
+    build.build()
+    return uot.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"UOT_API\s+[\w\s\*]+?\b(uot_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "uot_ti_sinkhorn" in names and len(names) >= 8
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", L._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (uot_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_struct_layout_matches_header():
+    from paper_2201_00730_gb300 import uot
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "uot.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(uot_problem), offsetof(uot_problem, eps), offsetof(uot_problem, b),
+         sizeof(uot_options), offsetof(uot_options, residual_history), sizeof(uot_result));
+  printf("%zu\n", offsetof(uot_result, lambda));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    P, O, R = uot.Problem, uot.Options, uot.Result
+    assert vals == [C.sizeof(P), P.eps.offset, P.b.offset, C.sizeof(O), O.residual_history.offset, C.sizeof(R),
+                    R.lambda_.offset]
+
+
+def test_argument_errors_without_device_work(L):
+    from paper_2201_00730_gb300 import uot
+    assert L.uot_workspace_size(None) == 0
+    assert b"NULL" in L.uot_last_error()
+    bad = uot.Problem(0, 5, 1, 0, 2.0, 0, 0.1, 1.0, 1.0, 8, 8, None, 8, 8)
+    assert L.uot_workspace_size(C.byref(bad)) == 0
+    assert b"n and m" in L.uot_last_error()
+    neg = uot.Problem(4, 5, 1, 0, 2.0, 0, -0.1, 1.0, 1.0, 8, 8, None, 8, 8)
+    st = L.uot_ti_sinkhorn(C.byref(neg), None, None, None, None, None, 0, None)
+    assert st == 1 and b"eps" in L.uot_last_error()
+    ok = uot.Problem(4, 5, 1, 0, 2.0, 0, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
+    st = L.uot_sinkhorn(C.byref(ok), None, None, None, None, None, 0, None)
+    assert st == 2  # no workspace
+    st = L.uot_softmin(C.byref(ok), 3, 256, 256, 256, 1 << 30, None)
+    assert st == 1 and b"axis" in L.uot_last_error()
+    dense_unaligned = uot.Problem(4, 5, 0, 1, 2.0, 0, 0.1, 1.0, 1.0, None, None, 260, 256, 256)
+    assert L.uot_workspace_size(C.byref(dense_unaligned)) == 0
+    assert b"16-byte" in L.uot_last_error()
+    assert L.uot_version().startswith(b"uot")

@@ -1,0 +1,280 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances.  Potentials and softmins: |gpu - oracle| <= 1e-4 eps + 2 ulp_f32(|oracle|):
+the first term is the stated 1e-4*eps-relative bar, the second the rounding of a
+float32 output (a float32 result cannot be closer than half an ulp).  Values:
+relative 1e-6.  Gradients: |gpu - oracle|_2 <= 1e-4 |oracle|_2 per tensor.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import uot as O
+from paper_2201_00730_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "config1_1000iters.json")
+
+
+@pytest.fixture(scope="module")
+def U():
+    from paper_2201_00730_gb300 import build, uot
+    build.build()
+    return uot
+
+
+def spec_of(U, p, dense=False):
+    dev = torch.device("cuda:0")
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+    if dense:
+        return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, C=t(W.dense_cost_f32(p.x, p.y)), p=p.p)
+    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), p=p.p)
+
+
+def pot_tol(eps, ref):
+    ref = torch.as_tensor(ref, dtype=torch.float64)
+    return 1e-4 * eps + 2.0 * 2.0 ** -23 * ref.abs()
+
+
+def assert_pot_close(got, ref, eps, what=""):
+    got = got.detach().double().cpu()
+    ref = torch.as_tensor(ref, dtype=torch.float64)
+    err = (got - ref).abs()
+    tol = pot_tol(eps, ref)
+    bad = err > tol
+    assert not bool(bad.any()), (f"{what}: max err {err.max().item():.3e} (eps={eps}); "
+                                 f"{int(bad.sum())} of {err.numel()} outside 1e-4*eps + 2ulp")
+
+
+def rel_l2(got, ref):
+    got = got.detach().double().cpu()
+    ref = torch.as_tensor(ref, dtype=torch.float64)
+    return ((got - ref).norm() / ref.norm()).item()
+
+
+# ------------------------------------------------------------------ sweeps
+
+SWEEP_CASES = [
+    # n, m, d, eps, p, zero_frac
+    (1000, 777, 1, 1e-2, 2.0, 0.0),
+    (3000, 2049, 3, 2e-2, 2.0, 0.0),
+    (517, 3001, 2, 5e-2, 2.0, 0.3),
+    (1, 1000, 3, 1e-1, 2.0, 0.0),
+    (1000, 1, 2, 1e-1, 2.0, 0.0),
+    (700, 300, 5, 5e-2, 1.5, 0.1),
+    (300, 650, 16, 0.2, 2.0, 0.0),
+    (129, 257, 64, 0.5, 2.0, 0.0),
+    (70000, 1500, 3, 1e-2, 2.0, 0.0),
+]
+
+
+@pytest.mark.parametrize("n,m,d,eps,p,zf", SWEEP_CASES)
+def test_softmin_points(U, n, m, d, eps, p, zf):
+    pr = W.random_problem(n, m, d, seed=n + m + d, eps=eps, zero_frac=zf, p=p)
+    spec = spec_of(U, pr)
+    rng = np.random.default_rng(7)
+    g = (0.3 * rng.standard_normal(m)).astype(np.float32)
+    f = (0.3 * rng.standard_normal(n)).astype(np.float32)
+    C = O.cost_matrix(pr.x, pr.y, p)
+    S = U.softmin(spec, torch.from_numpy(g).cuda(), 0)
+    assert_pot_close(S, O.smin_rows(C, pr.b, g, eps), eps, "row sweep")
+    Sp = U.softmin(spec, torch.from_numpy(f).cuda(), 1)
+    assert_pot_close(Sp, O.smin_cols(C, pr.a, f, eps), eps, "column sweep")
+
+
+@pytest.mark.parametrize("n,m,eps", [(1000, 780, 1e-2), (513, 1301, 5e-2), (3, 5, 0.1), (9000, 2052, 2e-2)])
+def test_softmin_dense(U, n, m, eps):
+    pr = W.random_problem(n, m, 2, seed=n * 7 + m, eps=eps, zero_frac=0.05)
+    spec = spec_of(U, pr, dense=True)
+    rng = np.random.default_rng(8)
+    g = (0.3 * rng.standard_normal(m)).astype(np.float32)
+    f = (0.3 * rng.standard_normal(n)).astype(np.float32)
+    C = O._t(W.dense_cost_f32(pr.x, pr.y))  # the same float32 matrix the GPU reads
+    assert_pot_close(U.softmin(spec, torch.from_numpy(g).cuda(), 0), O.smin_rows(C, pr.b, g, eps), eps, "dense rows")
+    assert_pot_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, pr.a, f, eps), eps, "dense cols")
+
+
+def test_softmin_shift_property(U):
+    """Smin(h + tau) = Smin(h) + tau on the device (App. B)."""
+    pr = W.random_problem(2000, 1500, 3, seed=3, eps=0.02)
+    spec = spec_of(U, pr)
+    g = torch.zeros(1500, device="cuda")
+    S0 = U.softmin(spec, g, 0).double()
+    S1 = U.softmin(spec, g + 0.25, 0).double()
+    assert (S1 - (S0 - 0.25)).abs().max().item() < 1e-4 * 0.02 + 1e-6
+
+
+# ------------------------------------------------------------------ solvers
+
+@pytest.mark.parametrize("method", ["plain", "ti"])
+def test_config1_1000_iterations_match_golden(U, method):
+    d = json.load(open(GOLDEN))
+    pr = W.config1()
+    spec = spec_of(U, pr)
+    r = U.solve(spec, method, max_iter=1000, tol=0.0)
+    assert r.iters == 1000
+    key = "plain" if method == "plain" else "ti"
+    assert_pot_close(r.f, d[key]["f"], pr.eps, f"{method} f")
+    assert_pot_close(r.g, d[key]["g"], pr.eps, f"{method} g")
+    if method == "ti":
+        assert abs(r.lam - d["ti"]["lambda"]) < 1e-4 * pr.eps
+    val = U.dual_value(spec, r.f, r.g)[0].item()
+    assert abs(val - d[key]["value"]) < 1e-6 * abs(d[key]["value"])
+
+
+@pytest.mark.parametrize("method", ["plain", "ti"])
+@pytest.mark.parametrize("dense", [False, True])
+def test_iterates_match_oracle_ragged(U, method, dense):
+    """N != M, rho1 != rho2, unequal masses, zero weights: iterate-by-iterate parity."""
+    pr = W.random_problem(611, 437, 2, seed=21, eps=0.05, rho1=0.3, rho2=2.0, mass_a=1.3, mass_b=0.6,
+                          zero_frac=0.1)
+    spec = spec_of(U, pr, dense=dense)
+    C = O._t(W.dense_cost_f32(pr.x, pr.y)) if dense else O.cost_matrix(pr.x, pr.y)
+    for T in (1, 7, 60):
+        r = U.solve(spec, method, max_iter=T)
+        ref = (O.ti_sinkhorn if method == "ti" else O.sinkhorn)(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
+        assert_pot_close(r.f, ref.f, pr.eps, f"f after {T}")
+        assert_pot_close(r.g, ref.g, pr.eps, f"g after {T}")
+        res_ref = O.fixed_point_residual(C, pr.a, pr.b, ref.f, ref.g, pr.eps, pr.rho1, pr.rho2).item()
+        assert abs(r.residual - res_ref) <= 1e-4 * pr.eps + 1e-3 * res_ref
+        if method == "ti":
+            assert abs(r.lam - ref.lam) < 1e-4 * pr.eps
+
+
+def test_residual_history_and_early_stop(U):
+    pr = W.random_problem(400, 300, 1, seed=5, eps=0.05, rho1=1.0, rho2=0.5)
+    spec = spec_of(U, pr)
+    C = O.cost_matrix(pr.x, pr.y)
+    r = U.solve(spec, "ti", max_iter=30, history=True)
+    h = r.history.cpu().double()
+    ref = O.ti_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 30, keep_iterates=True)
+    for t, f, g in ref.history:
+        rr = O.fixed_point_residual(C, pr.a, pr.b, f, g, pr.eps, pr.rho1, pr.rho2).item()
+        assert abs(h[t].item() - rr) <= 1e-4 * pr.eps + 1e-3 * rr, (t, h[t].item(), rr)
+    # early stop: first check at or below tol, checked every 5 iterations
+    tol = 1e-4
+    r2 = U.solve(spec, "ti", max_iter=500, tol=tol, check_every=5)
+    assert r2.converged and r2.residual <= tol and r2.iters % 5 == 0
+    ref_stop = O.ti_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 500, tol=tol, check_every=5)
+    assert abs(r2.iters - ref_stop.iters) <= 5
+
+
+def test_ti_faster_than_plain_same_fixed_point(U):
+    pr = W.random_problem(1500, 1200, 2, seed=9, eps=0.01, rho1=1.0, rho2=1.0, mass_a=1.0, mass_b=1.5)
+    spec = spec_of(U, pr)
+    ti = U.solve(spec, "ti", max_iter=20000, tol=1e-6, check_every=10)
+    pl = U.solve(spec, "plain", max_iter=20000, tol=1e-6, check_every=10)
+    assert ti.converged and pl.converged
+    assert ti.iters < pl.iters
+    # same fixed point (T3) to within the residual-implied error
+    assert (ti.f - pl.f).abs().max().item() < 2e-4
+
+
+def test_mass_equality_after_translation(U):
+    """(f, g) = Phi(fb, gb) has <a, e^{-f/rho1}> = <b, e^{-g/rho2}> at every iterate (Prop. 1)."""
+    pr = W.random_problem(800, 900, 3, seed=2, eps=0.05, rho1=0.4, rho2=3.0, mass_a=2.0, mass_b=0.5)
+    spec = spec_of(U, pr)
+    for T in (1, 3, 25):
+        r = U.solve(spec, "ti", max_iter=T)
+        f, g = r.f.double().cpu(), r.g.double().cpu()
+        A = (O._t(pr.a) * torch.exp(-f / pr.rho1)).sum().item()
+        B = (O._t(pr.b) * torch.exp(-g / pr.rho2)).sum().item()
+        assert abs(A - B) < 1e-5 * A
+
+
+def test_n1_and_degenerate_sizes(U):
+    for (n, m) in ((1, 1), (1, 300), (257, 1)):
+        pr = W.random_problem(n, m, 2, seed=n + m, eps=0.1, rho1=0.7, rho2=1.3)
+        spec = spec_of(U, pr)
+        C = O.cost_matrix(pr.x, pr.y)
+        r = U.solve(spec, "ti", max_iter=200, tol=1e-7, check_every=1)
+        ref = O.ti_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 5000, tol=1e-13)
+        assert_pot_close(r.f, ref.f, pr.eps, f"f n={n} m={m}")
+        assert_pot_close(r.g, ref.g, pr.eps, f"g n={n} m={m}")
+    # N = M = 1 closed form (derived from the primal)
+    a, b, c, eps, r1, r2 = 0.4, 2.2, 1.7, 0.2, 0.3, 5.0
+    logpi = (eps * math.log(a * b) + r1 * math.log(a) + r2 * math.log(b) - c) / (eps + r1 + r2)
+    pi = math.exp(logpi)
+    dev = torch.device("cuda:0")
+    spec = U.Spec(torch.tensor([a], device=dev), torch.tensor([b], device=dev), eps, r1, r2,
+                  x=torch.tensor([[0.0]], device=dev), y=torch.tensor([[math.sqrt(c)]], device=dev))
+    r = U.solve(spec, "ti", max_iter=5)
+    assert abs(r.f.item() - (-r1 * math.log(pi / a))) < 1e-4 * eps + 1e-6
+    assert abs(r.g.item() - (-r2 * math.log(pi / b))) < 1e-4 * eps + 1e-6
+    val = eps * a * b + r1 * a + r2 * b - (eps + r1 + r2) * pi
+    assert abs(U.dual_value(spec, r.f, r.g)[0].item() - val) < 1e-6 * abs(val)
+
+
+def test_warm_start_translation_recovery(U):
+    """TI from the optimum plus a constant returns to the optimum after one iteration (T2)."""
+    pr = W.random_problem(500, 600, 2, seed=4, eps=0.05, rho1=0.8, rho2=0.8)
+    spec = spec_of(U, pr)
+    r = U.solve(spec, "ti", max_iter=5000, tol=1e-7, check_every=5)
+    r1 = U.solve(spec, "ti", max_iter=1, f0=r.f + 0.5)
+    assert (r1.f - r.f).abs().max().item() < 1e-4 * pr.eps + 1e-6
+    assert (r1.g - r.g).abs().max().item() < 1e-4 * pr.eps + 1e-6
+
+
+# --------------------------------------------------------- value, gradients
+
+@pytest.mark.parametrize("d,p", [(1, 2.0), (3, 2.0), (2, 1.5), (8, 2.0)])
+def test_dual_primal_and_envelope_grads(U, d, p):
+    pr = W.random_problem(700, 500, d, seed=10 + d, eps=0.05, rho1=0.6, rho2=1.4, mass_a=1.1, mass_b=0.8, p=p)
+    spec = spec_of(U, pr)
+    r = U.solve(spec, "ti", max_iter=5000, tol=1e-7, check_every=5)
+    f64, g64 = r.f.double().cpu(), r.g.double().cpu()
+    C = O.cost_matrix(pr.x, pr.y, p)
+    out = U.dual_value(spec, r.f, r.g, primal=True).cpu()
+    D = O.dual_value(C, pr.a, pr.b, f64, g64, pr.eps, pr.rho1, pr.rho2).item()
+    P = O.primal_value(C, pr.a, pr.b, O.transport_plan(C, pr.a, pr.b, f64, g64, pr.eps),
+                       pr.eps, pr.rho1, pr.rho2).item()
+    assert abs(out[0].item() - D) < 1e-6 * abs(D)
+    assert abs(out[1].item() - P) < 1e-6 * abs(P)
+    assert abs(out[1].item() - out[0].item()) < 1e-5 * abs(D)  # gap -> 0 at the optimum (T4)
+    gr = U.grad(spec, r.f, r.g)
+    ea, eb, ex, ey = O.envelope_grads(pr.x, pr.y, pr.a, pr.b, f64, g64, pr.eps, pr.rho1, pr.rho2, p)
+    for k, ref in (("a", ea), ("b", eb), ("x", ex), ("y", ey)):
+        assert rel_l2(gr[k], ref) < 1e-4, (k, rel_l2(gr[k], ref))
+
+
+def test_dense_grads_weights_only(U):
+    pr = W.random_problem(300, 404, 2, seed=31, eps=0.05, rho1=0.6, rho2=1.4)
+    spec = spec_of(U, pr, dense=True)
+    r = U.solve(spec, "ti", max_iter=3000, tol=1e-7, check_every=5)
+    gr = U.grad(spec, r.f, r.g, wrt=("a", "b"))
+    ea, eb, _, _ = O.envelope_grads(pr.x, pr.y, pr.a, pr.b, r.f.double().cpu(), r.g.double().cpu(),
+                                    pr.eps, pr.rho1, pr.rho2)
+    assert rel_l2(gr["a"], ea) < 1e-4 and rel_l2(gr["b"], eb) < 1e-4
+
+
+def test_autograd_function(U):
+    pr = W.random_problem(256, 300, 2, seed=12, eps=0.1, rho1=0.5, rho2=0.5)
+    spec = spec_of(U, pr)
+    x = spec.x.clone().requires_grad_(True)
+    a = spec.a.clone().requires_grad_(True)
+    val = U.UOTLoss.apply(x, spec.y, a, spec.b, pr.eps, pr.rho1, pr.rho2, 10000, 1e-7, 5)
+    val.backward()
+    r = U.solve(spec, "ti", max_iter=10000, tol=1e-7, check_every=5)
+    ea, eb, ex, ey = O.envelope_grads(pr.x, pr.y, pr.a, pr.b, r.f.double().cpu(), r.g.double().cpu(),
+                                      pr.eps, pr.rho1, pr.rho2)
+    assert rel_l2(x.grad, ex) < 1e-4 and rel_l2(a.grad, ea) < 1e-4
+
+
+# ------------------------------------------------------------ bad device data
+
+def test_bad_weights_reported(U):
+    pr = W.random_problem(100, 120, 1, seed=1)
+    spec = spec_of(U, pr)
+    spec.a[3] = -1.0
+    with pytest.raises(U.UOTError) as ei:
+        U.solve(spec, "ti", max_iter=5)
+    assert ei.value.status == 4
+    spec.a[3] = 0.5
+    spec.b.zero_()
+    with pytest.raises(U.UOTError):
+        U.solve(spec, "ti", max_iter=5)
