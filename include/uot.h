@@ -161,6 +161,21 @@ UOT_API uot_status uot_grad(const uot_problem* prob, const float* f, const float
                     float* grad_b, float* grad_x, float* grad_y, void* ws, size_t ws_bytes,
                     void* stream);
 
+/* Measurement hooks (no counterpart in the paper).
+ * uot_kernel_launches: number of CUDA kernels this library has launched in the
+ * process so far (all threads).
+ * uot_profile_begin / uot_profile_end: while a profile is open on the calling
+ * thread, every softmin sweep kernel launched by that thread is bracketed by a
+ * pair of CUDA events recorded on its launch stream (at most 65536 launches are
+ * bracketed; later ones are counted but not timed).  uot_profile_end
+ * synchronises those events and returns the summed device time of the timed
+ * sweep launches in *sweep_ms, their number in *timed_launches and the number of
+ * sweep launches seen in *launches.  Events are created at begin and destroyed
+ * at end.  Returns UOT_ERR_INVALID_ARG when no profile is open. */
+UOT_API uint64_t uot_kernel_launches(void);
+UOT_API uot_status uot_profile_begin(void);
+UOT_API uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* launches);
+
 /* Message describing the last error of the calling thread ("" if none). */
 UOT_API const char* uot_last_error(void);
 

@@ -357,39 +357,46 @@ int grid_for(int n) {
 
 cudaError_t launch_combine(const EpiParams& e, cudaStream_t st) {
   k_combine<<<grid_for(e.nq), kBlk, 0, st>>>(e);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rho1, DevState* s,
                            double* blk, cudaStream_t st) {
   k_ti_init<<<grid_for(n), kBlk, 0, st>>>(f0, ln_a, n, rho1, s, blk);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
                             int m, const DevState* s, int slot, cudaStream_t st) {
   k_finalize<<<grid_for(n + m), kBlk, 0, st>>>(ti, f_hat, g_hat, f, g, n, m, s, slot);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, DevState* s,
                                cudaStream_t st) {
   k_log_weights<<<grid_for(n), kBlk, 0, st>>>(w, n, lnw, l2w, s);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_dual(const DualParams& d, cudaStream_t st) {
   k_dual<<<grid_for(d.n + d.m), kBlk, 0, st>>>(d);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_epilogue(const GradParams& gp, cudaStream_t st) {
   k_grad<<<grid_for(gp.nq), kBlk, 0, st>>>(gp);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_mass(const float* w, int n, double* blk, DevState* s, int idx, cudaStream_t st) {
   k_mass<<<grid_for(n), kBlk, 0, st>>>(w, n, blk, s, idx);
+  note_launch();
   return cudaGetLastError();
 }
 

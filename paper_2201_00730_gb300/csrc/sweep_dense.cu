@@ -238,6 +238,7 @@ cudaError_t launch_dense_sweep(int axis, const float* C, int n, int m, const flo
     if (aligned) k_dense_cols<true><<<grid, kThreads, 0, st>>>(C, n, m, l2w_k, pot_k, shift_k, s, g.keys_per_split, part);
     else k_dense_cols<false><<<grid, kThreads, 0, st>>>(C, n, m, l2w_k, pot_k, shift_k, s, g.keys_per_split, part);
   }
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -239,6 +239,7 @@ cudaError_t run_small(const SideDesc& q, const SideDesc& k, const float* pot, co
   dim3 grid(g.row_blocks, g.splits);
   k_sweep_small<D, R, 8, MOM><<<grid, kThreads, 0, st>>>(q.pts, q.n, k.pts, k.n, k.l2w, pot, shift, s,
                                                         (float)sqrt(s), g.keys_per_split, part);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -260,6 +261,7 @@ cudaError_t run_generic(const SideDesc& q, const SideDesc& k, int dim, float p, 
   const size_t smem = sizeof(float) * kGenTile * (dim + 1);
   k_sweep_generic<DMAX, MOM><<<grid, kThreads, smem, st>>>(q.pts, q.n, k.pts, k.n, dim, p, k.l2w, pot,
                                                            shift, s, g.keys_per_split, part);
+  note_launch();
   return cudaGetLastError();
 }
 

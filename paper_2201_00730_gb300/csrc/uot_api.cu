@@ -8,8 +8,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "uot_internal.cuh"
 
@@ -17,6 +19,17 @@ namespace uot {
 
 namespace {
 thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+// Per-thread sweep profile: event pairs around each sweep launch.
+struct Profile {
+  bool open = false;
+  std::vector<cudaEvent_t> ev;  // 2 per timed launch, created lazily
+  size_t used = 0;              // events recorded
+  int64_t launches = 0;
+};
+thread_local Profile g_prof;
+constexpr size_t kMaxTimed = 65536;
 
 uot_status fail(uot_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 uot_status fail(uot_status s, const char* fmt, ...) {
@@ -155,7 +168,31 @@ uot_status prepare(Ctx& c) {
 // One softmin sweep: axis 0 -> queries are rows (x side), keys the y side;
 // axis 1 -> queries are columns (y side), keys the x side.  Returns the number
 // of key chunks (splits) written to the partial buffer.
+cudaEvent_t prof_event() {
+  if (g_prof.used >= 2 * kMaxTimed) return nullptr;
+  if (g_prof.used == g_prof.ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_prof.ev.push_back(e);
+  }
+  return g_prof.ev[g_prof.used++];
+}
+
+uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits);
+
 uot_status sweep(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits) {
+  if (!g_prof.open) return sweep_inner(c, axis, pot, shift, moments, splits);
+  ++g_prof.launches;
+  cudaEvent_t e0 = prof_event();
+  cudaEvent_t e1 = e0 ? prof_event() : nullptr;
+  if (e0 && !e1) --g_prof.used;
+  if (e1) UOT_CUDA(cudaEventRecord(e0, c.st));
+  uot_status v = sweep_inner(c, axis, pot, shift, moments, splits);
+  if (e1) UOT_CUDA(cudaEventRecord(e1, c.st));
+  return v;
+}
+
+uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits) {
   const uot_problem& p = c.p;
   float* part = axis == 0 ? c.part_r : c.part_c;
   if (p.cost_kind == UOT_COST_POINTS) {
@@ -254,6 +291,8 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
 }
 
 }  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int device_sm_count() {
   static std::mutex mu;
@@ -363,6 +402,35 @@ uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, flo
     gp.grad_w = gw; gp.grad_pts = gpts; gp.lnw_o = side == 0 ? c.ln_a : c.ln_b; gp.state = c.state;
     UOT_CUDA(launch_grad_epilogue(gp, c.st));
   }
+  return UOT_OK;
+}
+
+uint64_t uot_kernel_launches(void) { return g_launches.load(); }
+
+uot_status uot_profile_begin(void) {
+  g_prof.open = true;
+  g_prof.used = 0;
+  g_prof.launches = 0;
+  return UOT_OK;
+}
+
+uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* launches) {
+  if (!g_prof.open) return fail(UOT_ERR_INVALID_ARG, "no profile open on this thread");
+  g_prof.open = false;
+  double total = 0.0;
+  for (size_t k = 0; k + 1 < g_prof.used; k += 2) {
+    if (cudaEventSynchronize(g_prof.ev[k + 1]) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event sync");
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, g_prof.ev[k], g_prof.ev[k + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    total += ms;
+  }
+  if (sweep_ms) *sweep_ms = total;
+  if (timed_launches) *timed_launches = (int64_t)(g_prof.used / 2);
+  if (launches) *launches = g_prof.launches;
+  for (cudaEvent_t e : g_prof.ev) cudaEventDestroy(e);
+  g_prof.ev.clear();
+  g_prof.used = 0;
   return UOT_OK;
 }
 

@@ -49,6 +49,8 @@ struct SweepGeom {
 };
 
 int device_sm_count();
+// Counts one kernel launch (process-wide counter read by uot_kernel_launches).
+void note_launch();
 SweepGeom points_geom(int nq, int nk, int dim, bool moments);
 SweepGeom dense_row_geom(int nrows, int ncols);
 SweepGeom dense_col_geom(int nrows, int ncols);

@@ -72,6 +72,12 @@ def lib() -> C.CDLL:
         L.uot_dual_value.restype = C.c_int
         L.uot_grad.argtypes = [P, V, V, V, V, V, V, V, S, V]
         L.uot_grad.restype = C.c_int
+        L.uot_kernel_launches.argtypes = []
+        L.uot_kernel_launches.restype = C.c_uint64
+        L.uot_profile_begin.argtypes = []
+        L.uot_profile_begin.restype = C.c_int
+        L.uot_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.uot_profile_end.restype = C.c_int
         L.uot_last_error.argtypes = []
         L.uot_last_error.restype = C.c_char_p
         L.uot_version.argtypes = []
@@ -270,6 +276,28 @@ class UOTLoss(torch.autograd.Function):
         gr = grad(ctx.spec, ctx.f, ctx.g)
         s = gout.to(torch.float32)
         return (gr["x"] * s, gr["y"] * s, gr["a"] * s, gr["b"] * s, None, None, None, None, None, None)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libuot in this process so far."""
+    return int(lib().uot_kernel_launches())
+
+
+class SweepProfile:
+    """Context manager bracketing every sweep launch of this thread with CUDA events.
+
+    After exit: .sweep_ms (summed device time), .timed, .launches.
+    """
+
+    def __enter__(self):
+        _check(lib().uot_profile_begin())
+        return self
+
+    def __exit__(self, *exc):
+        ms, timed, n = C.c_double(), C.c_int64(), C.c_int64()
+        _check(lib().uot_profile_end(C.byref(ms), C.byref(timed), C.byref(n)))
+        self.sweep_ms, self.timed, self.launches = ms.value, timed.value, n.value
+        return False
 
 
 def version() -> str:
