@@ -117,6 +117,30 @@ UOT_API size_t uot_workspace_size(const uot_problem* prob);
 UOT_API uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, float* out,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* The same sweep as uot_softmin for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ *
+ * Some callers have no device allocator at hand (a plain C host program
+ * without a memory pool, a plug-in whose host framework forbids allocation
+ * after start-up, a real-time loop that must not call cudaMalloc).  This entry
+ * point takes no workspace: its scratch is a 16 MiB array compiled into the
+ * library, reserved on every GPU that loads the library's device code and held
+ * until the process exits.  The call itself performs no cudaMalloc, cudaFree
+ * or other allocation.
+ *  - Limit: problems whose uot_workspace_size() exceeds 16 MiB (with N = M
+ *    that happens at about 90000 points per side) are rejected with
+ *    UOT_ERR_UNSUPPORTED and a message; use uot_softmin for those.
+ *  - The first call on each device looks up the scratch's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the one scratch array, which keeps the last call's
+ *    contents (every call resets the parts it reads before reading them).
+ *    Calls whose GPU work overlaps in time (two host threads, or two streams
+ *    on the same device) race on the scratch and give wrong results: serialise
+ *    them.
+ * Arguments and results as for uot_softmin.  Asynchronous. */
+UOT_API uot_status uot_softmin_noalloc(const uot_problem* prob, int32_t axis, const float* pot, float* out,
+                                       void* stream);
+
 /* Plain (F-)Sinkhorn, Sec. 3:
  *   g_{t+1} = rho2/(rho2+eps) Smin_a^eps(C - f_t),  f_{t+1} = rho1/(rho1+eps) Smin_b^eps(C - g_{t+1}),
  * from f_0 = 0 (or f on entry when warm_start).  On return f, g hold (f_T, g_T).

@@ -294,6 +294,8 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 int device_sm_count() {
   static std::mutex mu;
   static int cache[64] = {0};

@@ -51,6 +51,8 @@ struct SweepGeom {
 int device_sm_count();
 // Counts one kernel launch (process-wide counter read by uot_kernel_launches).
 void note_launch();
+// Sets the calling thread's message returned by uot_last_error().
+void set_last_error(const char* msg);
 SweepGeom points_geom(int nq, int nk, int dim, bool moments);
 SweepGeom dense_row_geom(int nrows, int ncols);
 SweepGeom dense_col_geom(int nrows, int ncols);

@@ -65,6 +65,8 @@ def lib() -> C.CDLL:
         L.uot_workspace_size.restype = S
         L.uot_softmin.argtypes = [P, C.c_int32, V, V, V, S, V]
         L.uot_softmin.restype = C.c_int
+        L.uot_softmin_noalloc.argtypes = [P, C.c_int32, V, V, V]
+        L.uot_softmin_noalloc.restype = C.c_int
         for fn in (L.uot_sinkhorn, L.uot_ti_sinkhorn):
             fn.argtypes = [P, C.POINTER(Options), V, V, C.POINTER(Result), V, S, V]
             fn.restype = C.c_int
@@ -177,6 +179,19 @@ def softmin(spec: Spec, pot: torch.Tensor, axis: int, ws: torch.Tensor | None = 
     out = torch.empty(nq, dtype=torch.float32, device=spec.a.device)
     ws = spec.workspace() if ws is None else ws
     _check(lib().uot_softmin(C.byref(pr), axis, _ptr(pot), _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def softmin_noalloc(spec: Spec, pot: torch.Tensor, axis: int) -> torch.Tensor:
+    """uot_softmin without a workspace: the library's built-in 16 MiB scratch is used.
+
+    For callers that cannot allocate device memory; see include/uot.h.
+    """
+    pr = spec.struct()
+    nq, nk = (spec.n, spec.m) if axis == 0 else (spec.m, spec.n)
+    _dev_f32(pot, "pot", (nk,))
+    out = torch.empty(nq, dtype=torch.float32, device=spec.a.device)
+    _check(lib().uot_softmin_noalloc(C.byref(pr), axis, _ptr(pot), _ptr(out), _stream()))
     return out
 
 
