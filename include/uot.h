@@ -71,7 +71,10 @@ typedef struct {
   int32_t dim;         /* point dimension, 1..64 (points); ignored for dense          */
   int32_t cost_kind;   /* uot_cost_kind                                               */
   float p;             /* exponent p >= 1 of the points cost; p == 2 is the fast path */
-  int32_t reserved;
+  int32_t ordering;    /* points cost with dim <= 3 and p == 2 only: 0 = automatic, 1 = always put  */
+                       /* both clouds in Morton order and use the tiled sweep, 2 = never (results   */
+                       /* agree within rounding; ordering costs a few hundred us per call and pays  */
+                       /* off from about 1.5e9 cost entries per call, the automatic threshold)      */
   double eps, rho1, rho2;
   const float* x;      /* device, N x dim (points)        */
   const float* y;      /* device, M x dim (points)        */
@@ -128,8 +131,9 @@ UOT_API uot_status uot_softmin(const uot_problem* prob, int32_t axis, const floa
  * until the process exits.  The call itself performs no cudaMalloc, cudaFree
  * or other allocation.
  *  - Limit: problems whose uot_workspace_size() exceeds 16 MiB (with N = M
- *    that happens at about 90000 points per side) are rejected with
- *    UOT_ERR_UNSUPPORTED and a message; use uot_softmin for those.
+ *    and 3-D points that happens between 60000 and 70000 points per side)
+ *    are rejected with UOT_ERR_UNSUPPORTED and a message; use uot_softmin for
+ *    those.
  *  - The first call on each device looks up the scratch's device address with
  *    that device current; make that first call before any stream capture.
  *  - All calls share the one scratch array, which keeps the last call's

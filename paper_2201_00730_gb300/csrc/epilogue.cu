@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "epi_device.cuh"
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -79,75 +80,11 @@ __device__ Red4 block_reduce(Red4 v) {
 }
 
 __global__ void __launch_bounds__(kBlk) k_combine(EpiParams e) {
-  const int CH = 2 + e.moments;
-  const Slot& si = e.state->slot[e.slot_in];
-  const double Xin = e.out_is_f ? si.B : si.A;                      // key-side Smin^rho scalar
-  const double cS = e.rho_o / (e.rho_o + e.eps);                    // aprox factor
-  const double cX = e.eps / (e.eps + e.rho_o) * e.rho_o / (e.rho_o + e.rho_i);
-  const double base_old = e.out_is_f ? si.cf : si.cg;               // stored hat + shift = bar
-  const double cR = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i) *
-                    (e.out_is_f ? si.A : si.B);                       // residual constant (TI)
-  Red4 acc{-INFINITY, 0.0, 0.0, 0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nq; i += gridDim.x * blockDim.x) {
-    const double lse2 = merge_lse2(e.part, CH, e.nq, e.splits, i);
-    if (lse2 < 0.25 * (double)kZeroW) acc.bad = 1.0;  // every key had zero weight
-    const double S = -lse2 / e.s;  // Smin in cost units
-    double v;
-    if (e.mode == EPI_SOFTMIN) {
-      v = S;
-    } else if (e.mode == EPI_PLAIN) {
-      v = cS * S;
-      if (e.old_out) acc.r = fmax(acc.r, fabs((double)e.old_out[i] - v));
-    } else {
-      v = cS * S - cX * Xin;
-      const double lw = e.lnw_o[i];
-      if (lw != -INFINITY) lse_add(acc.m, acc.s, lw - v / e.rho_o, 1.0);
-      if (e.old_out) acc.r = fmax(acc.r, fabs((double)e.old_out[i] + base_old - v - cR));
-    }
-    if (!isfinite(v)) acc.bad = 1.0;
-    e.out[i] = (float)v;
-  }
-  const Red4 b = block_reduce(acc);
-  if (threadIdx.x == 0) {
-    double* o = e.blk + 4 * (size_t)blockIdx.x;
-    o[0] = b.m; o[1] = b.s; o[2] = b.r; o[3] = b.bad;
-  }
-  if (!last_block(&e.state->counter)) return;
-  Red4 t{-INFINITY, 0.0, 0.0, 0.0};
-  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-    const double* o = e.blk + 4 * (size_t)k;
-    lse_add(t.m, t.s, __ldcg(o), __ldcg(o + 1));
-    t.r = fmax(t.r, __ldcg(o + 2));
-    t.bad = fmax(t.bad, __ldcg(o + 3));
-  }
-  t = block_reduce(t);
-  if (threadIdx.x == 0) {
-    DevState* st = e.state;
-    int status = st->status;
-    if (t.bad != 0.0 || isnan(t.r)) status |= kStatusNonfinite;
-    if (e.mode == EPI_TI) {
-      const double lse = t.m + log(t.s);               // log <w, e^{-hat/rho_o}>
-      const double Xhat = -e.rho_o * lse;              // Smin_w^rho_o(hat)
-      const double k = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i);
-      const double c = k / (1.0 - k) * Xhat;           // closed-form translation
-      const double X = Xhat + c;                       // Smin(hat + c) = Smin(hat) + c
-      if (!isfinite(X)) status |= kStatusNonfinite;
-      Slot& so = st->slot[e.slot_out];
-      if (e.out_is_f) {
-        so.A = X; so.cf = c;
-        const double tau1 = e.rho_o / (e.rho_o + e.rho_i), tau2 = e.rho_i / (e.rho_o + e.rho_i);
-        so.lam = tau1 * so.B - tau2 * X;               // lambda* = tau1 Smin_b(gb) - tau2 Smin_a(fb)
-      } else {
-        so.B = X; so.cg = c;
-      }
-    }
-    if (e.old_out) {
-      st->resid = (float)t.r;
-      if (e.resid_hist) e.resid_hist[e.hist_index] = (float)t.r;
-    }
-    st->status = status;
-    st->counter = 0;
-  }
+  const epi::Consts c = epi::consts(e);
+  epi::Acc acc = epi::acc_empty();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nq; i += gridDim.x * blockDim.x) epi::row(e, c, i, acc);
+  const epi::Acc b = epi::block_reduce(acc);
+  epi::grid_tail(e, b, blockIdx.x, gridDim.x);
 }
 
 // slot 0 <- {A = Smin_a^rho1(f0) = -rho1 log sum_i a_i e^{-f0_i/rho1}, B = cf = cg = lam = 0}
@@ -185,17 +122,18 @@ __global__ void __launch_bounds__(kBlk) k_ti_init(const float* f0, const double*
 }
 
 __global__ void k_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
-                           int m, const DevState* st, int slot) {
+                           int m, const DevState* st, int slot, const int* pf, const int* pg) {
   const Slot& s = st->slot[slot];
   const double sf = ti ? s.cf + s.lam : 0.0;
   const double sg = ti ? s.cg - s.lam : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
     if (i < n) {
-      if (ti) f[i] = (float)((double)f_hat[i] + sf);
+      if (ti) f[pf ? pf[i] : i] = (float)((double)f_hat[i] + sf);
+      else if (pf || f_hat != f) f[pf ? pf[i] : i] = f_hat[i];
     } else {
       const int j = i - n;
-      if (ti) g[j] = (float)((double)g_hat[j] + sg);
-      else if (g_hat != g) g[j] = g_hat[j];
+      if (ti) g[pg ? pg[j] : j] = (float)((double)g_hat[j] + sg);
+      else if (pg || g_hat != g) g[pg ? pg[j] : j] = g_hat[j];
     }
   }
 }
@@ -301,8 +239,9 @@ __global__ void __launch_bounds__(kBlk) k_grad(GradParams gp) {
     const double S = -lse2 / gp.s;
     const double f = gp.pot_o[i];
     const double z = (f - S) / gp.eps;
+    const int io = gp.perm ? gp.perm[i] : i;
     if (gp.grad_w)
-      gp.grad_w[i] = (float)(gp.rho_o * (1.0 - exp(-f / gp.rho_o)) - gp.eps * (exp(z) - m_other));
+      gp.grad_w[io] = (float)(gp.rho_o * (1.0 - exp(-f / gp.rho_o)) - gp.eps * (exp(z) - m_other));
     if (gp.grad_pts) {
       const double lw = gp.lnw_o[i];
       const double pi1 = (lw == -INFINITY) ? 0.0 : exp(lw + z);
@@ -320,7 +259,7 @@ __global__ void __launch_bounds__(kBlk) k_grad(GradParams gp) {
           const float* b = gp.part + (size_t)k * CH * gp.nq;
           mo += b[(size_t)(2 + dd) * gp.nq + i] * ex2f(b[i] - M);
         }
-        gp.grad_pts[(size_t)i * gp.dim + dd] = (float)(pi1 * pts_scale * (double)mo / (double)sum);
+        gp.grad_pts[(size_t)io * gp.dim + dd] = (float)(pi1 * pts_scale * (double)mo / (double)sum);
       }
     }
   }
@@ -369,8 +308,9 @@ cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rh
 }
 
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
-                            int m, const DevState* s, int slot, cudaStream_t st) {
-  k_finalize<<<grid_for(n + m), kBlk, 0, st>>>(ti, f_hat, g_hat, f, g, n, m, s, slot);
+                            int m, const DevState* s, int slot, const int* perm_f, const int* perm_g,
+                            cudaStream_t st) {
+  k_finalize<<<grid_for(n + m), kBlk, 0, st>>>(ti, f_hat, g_hat, f, g, n, m, s, slot, perm_f, perm_g);
   note_launch();
   return cudaGetLastError();
 }

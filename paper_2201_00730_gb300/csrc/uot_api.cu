@@ -62,6 +62,7 @@ uot_status validate(const uot_problem* p) {
   if (!finite_pos(p->eps) || !finite_pos(p->rho1) || !finite_pos(p->rho2))
     return fail(UOT_ERR_INVALID_ARG, "eps, rho1, rho2 must be finite and > 0");
   if (!p->a || !p->b) return fail(UOT_ERR_INVALID_ARG, "weights a and b must be device pointers");
+  if (p->ordering < 0 || p->ordering > 2) return fail(UOT_ERR_INVALID_ARG, "ordering must be 0, 1 or 2");
   if (p->cost_kind == UOT_COST_POINTS) {
     if (p->dim < 1 || p->dim > 64) return fail(UOT_ERR_INVALID_ARG, "dim must be in 1..64 (got %d)", p->dim);
     if (!(p->p >= 1.0f) || !isfinite(p->p)) return fail(UOT_ERR_INVALID_ARG, "cost exponent p must be >= 1");
@@ -81,13 +82,18 @@ struct PartSizes { size_t rows, cols; };
 
 PartSizes part_sizes(const uot_problem& p) {
   PartSizes ps{0, 0};
+  auto upd = [](size_t& acc, size_t v) { if (v > acc) acc = v; };
   if (p.cost_kind == UOT_COST_POINTS) {
     for (int mom = 0; mom < 2; ++mom) {
       const int ch = 2 + (mom ? p.dim : 0);
       SweepGeom gr = points_geom(p.n, p.m, p.dim, mom);
       SweepGeom gc = points_geom(p.m, p.n, p.dim, mom);
-      ps.rows = ps.rows > (size_t)gr.splits * ch * p.n ? ps.rows : (size_t)gr.splits * ch * p.n;
-      ps.cols = ps.cols > (size_t)gc.splits * ch * p.m ? ps.cols : (size_t)gc.splits * ch * p.m;
+      upd(ps.rows, (size_t)gr.splits * ch * p.n);
+      upd(ps.cols, (size_t)gc.splits * ch * p.m);
+    }
+    if (tiled_path(p)) {
+      upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
+      upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
     }
   } else {
     SweepGeom gr = dense_row_geom(p.n, p.m);
@@ -99,7 +105,10 @@ PartSizes part_sizes(const uot_problem& p) {
 }
 
 struct WsLayout {
-  size_t state, ln_a, ln_b, l2_a, l2_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, total;
+  size_t state, ln_a, ln_b, l2_a, l2_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc;
+  // ordering of the tiled path (empty otherwise)
+  size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
+  size_t sort_tmp_bytes, total;
 };
 
 WsLayout ws_layout(const uot_problem& p) {
@@ -118,20 +127,58 @@ WsLayout ws_layout(const uot_problem& p) {
   L.part_r = take(sizeof(float) * ps.rows);
   L.part_c = take(sizeof(float) * ps.cols);
   L.blk = take(sizeof(double) * kMaxBlocks * 10);
+  L.rbc = take(sizeof(unsigned int) * kMaxBlocks);
+  if (tiled_path(p)) {
+    const int nmax = p.n > p.m ? p.n : p.m;
+    L.perm_x = take(sizeof(int) * p.n);
+    L.perm_y = take(sizeof(int) * p.m);
+    L.xs = take(sizeof(float) * p.n * p.dim);
+    L.ys = take(sizeof(float) * p.m * p.dim);
+    L.as = take(sizeof(float) * p.n);
+    L.bs = take(sizeof(float) * p.m);
+    L.fs = take(sizeof(float) * p.n);
+    L.gs = take(sizeof(float) * p.m);
+    L.cen_x = take(sizeof(float4) * ((p.n + kTileKeys - 1) / kTileKeys));
+    L.cen_y = take(sizeof(float4) * ((p.m + kTileKeys - 1) / kTileKeys));
+    L.blk_f = take(sizeof(float) * kMaxBlocks * 6);
+    L.box = take(sizeof(float) * 8);
+    L.code_in = take(sizeof(unsigned int) * nmax);
+    L.code_out = take(sizeof(unsigned int) * nmax);
+    L.idx_in = take(sizeof(int) * nmax);
+    L.sort_tmp_bytes = sort_temp_bytes(nmax);
+    L.sort_tmp = take(L.sort_tmp_bytes);
+  }
   L.total = off;
   return L;
 }
 
 struct Ctx {
-  uot_problem p;
+  uot_problem p;        // as given by the caller
   DevState* state;
   double *ln_a, *ln_b, *blk;
   float *l2_a, *l2_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;
+  unsigned int* rbc;  // per-row-block counters of the fused sweeps
   cudaStream_t st;
   double s;  // log2(e) / eps
+  // tiled path: clouds in Morton order (px..pb point at the sorted copies)
+  bool tiled;
+  const float *px, *py, *pa, *pb;
+  int *perm_x, *perm_y;
+  float4 *cen_x, *cen_y;
+  float *xs, *ys, *as, *bs, *fs, *gs;
+  OrderScratch osc;
 };
 
-uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* stream, Ctx* c) {
+// Putting the clouds in Morton order costs a few hundred microseconds per call
+// (bounding box, codes, radix sort, gathers); it pays off once the sweeps it
+// speeds up cover more than about 1.5e9 cost entries in total.
+bool worth_ordering(const uot_problem& p, double sweeps) {
+  if (!tiled_path(p) || p.ordering == 2) return false;
+  return p.ordering == 1 || (double)p.n * (double)p.m * sweeps > 1.5e9;
+}
+
+uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* stream, Ctx* c,
+                    double sweeps = 1.0) {
   uot_status v = validate(prob);
   if (v != UOT_OK) return v;
   if (!ws) return fail(UOT_ERR_WORKSPACE, "workspace is NULL");
@@ -152,22 +199,60 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->part_r = reinterpret_cast<float*>(b + L.part_r);
   c->part_c = reinterpret_cast<float*>(b + L.part_c);
   c->blk = reinterpret_cast<double*>(b + L.blk);
+  c->rbc = reinterpret_cast<unsigned int*>(b + L.rbc);
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
+  c->tiled = worth_ordering(*prob, sweeps);
+  c->px = prob->x; c->py = prob->y; c->pa = prob->a; c->pb = prob->b;
+  c->perm_x = c->perm_y = nullptr;
+  c->cen_x = c->cen_y = nullptr;
+  c->xs = c->ys = c->as = c->bs = c->fs = c->gs = nullptr;
+  if (c->tiled) {
+    c->perm_x = reinterpret_cast<int*>(b + L.perm_x);
+    c->perm_y = reinterpret_cast<int*>(b + L.perm_y);
+    c->xs = reinterpret_cast<float*>(b + L.xs);
+    c->ys = reinterpret_cast<float*>(b + L.ys);
+    c->as = reinterpret_cast<float*>(b + L.as);
+    c->bs = reinterpret_cast<float*>(b + L.bs);
+    c->fs = reinterpret_cast<float*>(b + L.fs);
+    c->gs = reinterpret_cast<float*>(b + L.gs);
+    c->cen_x = reinterpret_cast<float4*>(b + L.cen_x);
+    c->cen_y = reinterpret_cast<float4*>(b + L.cen_y);
+    c->osc.blk_f = reinterpret_cast<float*>(b + L.blk_f);
+    c->osc.box = reinterpret_cast<float*>(b + L.box);
+    c->osc.counter = &c->state->counter;
+    c->osc.code_in = reinterpret_cast<unsigned int*>(b + L.code_in);
+    c->osc.code_out = reinterpret_cast<unsigned int*>(b + L.code_out);
+    c->osc.idx_in = reinterpret_cast<int*>(b + L.idx_in);
+    c->osc.temp = b + L.sort_tmp;
+    c->osc.temp_bytes = L.sort_tmp_bytes;
+    c->px = c->xs; c->py = c->ys; c->pa = c->as; c->pb = c->bs;
+  }
   return UOT_OK;
 }
 
-// Common preamble: zero the state, log weights of both sides.
+// Common preamble: zero the state; on the tiled path put both clouds in Morton
+// order; log weights of both sides (in the order the sweeps use).
 uot_status prepare(Ctx& c) {
   UOT_CUDA(cudaMemsetAsync(c.state, 0, sizeof(DevState), c.st));
-  UOT_CUDA(launch_log_weights(c.p.a, c.p.n, c.ln_a, c.l2_a, c.state, c.st));
-  UOT_CUDA(launch_log_weights(c.p.b, c.p.m, c.ln_b, c.l2_b, c.state, c.st));
+  UOT_CUDA(cudaMemsetAsync(c.rbc, 0, sizeof(unsigned int) * kMaxBlocks, c.st));
+  if (c.tiled) {
+    UOT_CUDA(launch_order_points(c.p.x, c.p.a, c.p.n, c.p.dim, c.osc, c.perm_x, c.xs, c.as, c.cen_x, c.st));
+    UOT_CUDA(launch_order_points(c.p.y, c.p.b, c.p.m, c.p.dim, c.osc, c.perm_y, c.ys, c.bs, c.cen_y, c.st));
+  }
+  UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, c.state, c.st));
+  UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, c.state, c.st));
   return UOT_OK;
 }
 
-// One softmin sweep: axis 0 -> queries are rows (x side), keys the y side;
-// axis 1 -> queries are columns (y side), keys the x side.  Returns the number
-// of key chunks (splits) written to the partial buffer.
+// A caller-order vector of side x (axis 0) or y (axis 1) in the order the sweeps use.
+uot_status to_internal(Ctx& c, int side, const float* v, float* tmp, const float** out) {
+  if (!c.tiled) { *out = v; return UOT_OK; }
+  UOT_CUDA(launch_gather_vec(v, side == 0 ? c.perm_x : c.perm_y, side == 0 ? c.p.n : c.p.m, tmp, c.st));
+  *out = tmp;
+  return UOT_OK;
+}
+
 cudaEvent_t prof_event() {
   if (g_prof.used >= 2 * kMaxTimed) return nullptr;
   if (g_prof.used == g_prof.ev.size()) {
@@ -178,30 +263,56 @@ cudaEvent_t prof_event() {
   return g_prof.ev[g_prof.used++];
 }
 
-uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits);
+uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits,
+                       EpiParams* epi, bool* fused);
 
-uot_status sweep(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits) {
-  if (!g_prof.open) return sweep_inner(c, axis, pot, shift, moments, splits);
+// One softmin sweep.  With `epi` (the half-step to apply afterwards, its nq,
+// splits and part filled in here), the tiled path runs the epilogue inside the
+// sweep and sets *fused; otherwise the caller launches the combine kernel.
+uot_status sweep(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits,
+                 EpiParams* epi = nullptr, bool* fused = nullptr) {
+  bool fz = false;
+  if (!g_prof.open) {
+    uot_status v = sweep_inner(c, axis, pot, shift, moments, splits, epi, &fz);
+    if (fused) *fused = fz;
+    return v;
+  }
   ++g_prof.launches;
   cudaEvent_t e0 = prof_event();
   cudaEvent_t e1 = e0 ? prof_event() : nullptr;
   if (e0 && !e1) --g_prof.used;
   if (e1) UOT_CUDA(cudaEventRecord(e0, c.st));
-  uot_status v = sweep_inner(c, axis, pot, shift, moments, splits);
+  uot_status v = sweep_inner(c, axis, pot, shift, moments, splits, epi, &fz);
   if (e1) UOT_CUDA(cudaEventRecord(e1, c.st));
+  if (fused) *fused = fz;
   return v;
 }
 
-uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits) {
+uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, bool moments, int* splits,
+                       EpiParams* epi, bool* fused) {
   const uot_problem& p = c.p;
   float* part = axis == 0 ? c.part_r : c.part_c;
   if (p.cost_kind == UOT_COST_POINTS) {
-    SideDesc X{p.x, c.l2_a, c.ln_a, p.n}, Y{p.y, c.l2_b, c.ln_b, p.m};
+    SideDesc X{c.px, c.l2_a, c.ln_a, p.n}, Y{c.py, c.l2_b, c.ln_b, p.m};
     const SideDesc& q = axis == 0 ? X : Y;
     const SideDesc& k = axis == 0 ? Y : X;
-    SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
-    *splits = g.splits;
-    UOT_CUDA(launch_points_sweep(q, k, p.dim, p.p, pot, shift, c.s, moments, part, g, c.st));
+    if (c.tiled && !moments) {
+      SweepGeom g = tile_geom(q.n, k.n, p.dim);
+      *splits = g.splits;
+      if (epi) {
+        epi->nq = q.n; epi->splits = g.splits; epi->part = part; epi->rb_counter = c.rbc; epi->moments = 0;
+        epi->key_shift = shift;
+        *fused = true;
+      } else if (shift) {
+        return fail(UOT_ERR_UNSUPPORTED, "internal: shifted tiled sweep without epilogue");
+      }
+      UOT_CUDA(launch_tile_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, shift, c.s, part, g, epi,
+                                 c.st));
+    } else {
+      SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
+      *splits = g.splits;
+      UOT_CUDA(launch_points_sweep(q, k, p.dim, p.p, pot, shift, c.s, moments, part, g, c.st));
+    }
   } else {
     SweepGeom g = axis == 0 ? dense_row_geom(p.n, p.m) : dense_col_geom(p.n, p.m);
     *splits = g.splits;
@@ -222,10 +333,12 @@ uot_status read_flags(Ctx& c, int* status, float* resid) {
 
 uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float* f, float* g,
                  uot_result* res, void* ws, size_t ws_bytes, void* stream) {
-  Ctx c;
-  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
-  if (v != UOT_OK) return v;
+  uot_status v0 = validate(prob);
+  if (v0 != UOT_OK) return v0;
   if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");
+  Ctx c;
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c, 2.0 * opt->max_iter + 1.0);
+  if (v != UOT_OK) return v;
   if (!f || !g) return fail(UOT_ERR_INVALID_ARG, "f and g must be device pointers");
   if (opt->max_iter < 1) return fail(UOT_ERR_INVALID_ARG, "max_iter must be >= 1");
   if (opt->check_every < 1) return fail(UOT_ERR_INVALID_ARG, "check_every must be >= 1");
@@ -233,10 +346,13 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   const uot_problem& p = c.p;
   v = prepare(c);
   if (v != UOT_OK) return v;
-  if (!opt->warm_start) UOT_CUDA(cudaMemsetAsync(f, 0, sizeof(float) * p.n, c.st));
-  UOT_CUDA(cudaMemsetAsync(g, 0, sizeof(float) * p.m, c.st));
-  if (ti) UOT_CUDA(launch_ti_init(f, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
-  float* gbuf[2] = {g, c.g_alt};
+  // iteration state in the sweeps' order: f_hat and the two g buffers
+  float* fst = c.tiled ? c.fs : f;
+  float* gbuf[2] = {c.tiled ? c.gs : g, c.g_alt};
+  if (!opt->warm_start) UOT_CUDA(cudaMemsetAsync(fst, 0, sizeof(float) * p.n, c.st));
+  else if (c.tiled) UOT_CUDA(launch_gather_vec(f, c.perm_x, p.n, fst, c.st));
+  UOT_CUDA(cudaMemsetAsync(gbuf[0], 0, sizeof(float) * p.m, c.st));
+  if (ti) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
   const int mode = ti ? EPI_TI : EPI_PLAIN;
   int t = 0, status = 0;
   float r = NAN;
@@ -244,15 +360,17 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
     // g half-step of iteration t+1: column sweep over x with fb_t = f_hat + cf
     const int so = (t + 1) & 1, si = t & 1;
     int splits = 0;
-    v = sweep(c, 1, f, ti ? &c.state->slot[si].cf : nullptr, false, &splits);
-    if (v != UOT_OK) return v;
+    bool fused = false;
     EpiParams e{};
-    e.mode = mode; e.nq = p.m; e.splits = splits; e.moments = 0; e.s = c.s;
+    e.mode = mode; e.nq = p.m; e.moments = 0; e.s = c.s;
     e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1; e.out_is_f = 0; e.lnw_o = c.ln_b;
     e.old_out = (t >= 1) ? gbuf[si] : nullptr; e.out = gbuf[so];
     e.resid_hist = opt->residual_history; e.hist_index = t;
     e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
-    UOT_CUDA(launch_combine(e, c.st));
+    v = sweep(c, 1, fst, ti ? &c.state->slot[si].cf : nullptr, false, &splits, &e, &fused);
+    if (v != UOT_OK) return v;
+    e.splits = splits;
+    if (!fused) UOT_CUDA(launch_combine(e, c.st));
     const bool last = (t == opt->max_iter);
     if (t >= 1 && (last || (opt->tol > 0.0 && t % opt->check_every == 0))) {
       v = read_flags(c, &status, &r);
@@ -261,16 +379,17 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
       if (last || r <= opt->tol) break;
     }
     // f half-step of iteration t+1: row sweep over y with gb_{t+1} = g_hat + cg
-    v = sweep(c, 0, gbuf[so], ti ? &c.state->slot[so].cg : nullptr, false, &splits);
-    if (v != UOT_OK) return v;
     EpiParams ef = e;
-    ef.nq = p.n; ef.splits = splits; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
-    ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = f; ef.resid_hist = nullptr;
+    ef.nq = p.n; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
+    ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = fst; ef.resid_hist = nullptr;
     ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r;
-    UOT_CUDA(launch_combine(ef, c.st));
+    v = sweep(c, 0, gbuf[so], ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
+    if (v != UOT_OK) return v;
+    ef.splits = splits;
+    if (!fused) UOT_CUDA(launch_combine(ef, c.st));
     ++t;
   }
-  UOT_CUDA(launch_finalize(ti ? 1 : 0, f, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.st));
+  UOT_CUDA(launch_finalize(ti ? 1 : 0, fst, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y, c.st));
   Slot slot{};
   UOT_CUDA(cudaMemcpyAsync(&slot, &c.state->slot[t & 1], sizeof(Slot), cudaMemcpyDeviceToHost, c.st));
   UOT_CUDA(cudaStreamSynchronize(c.st));
@@ -330,15 +449,21 @@ uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, 
   if (!pot || !out) return fail(UOT_ERR_INVALID_ARG, "pot and out must be device pointers");
   v = prepare(c);
   if (v != UOT_OK) return v;
-  int splits = 0;
-  v = sweep(c, axis, pot, nullptr, false, &splits);
+  const float* pot_i = nullptr;  // the key side's potential in the sweeps' order
+  v = to_internal(c, 1 - axis, pot, axis == 0 ? c.g_tmp : c.f_tmp, &pot_i);
   if (v != UOT_OK) return v;
+  int splits = 0;
+  bool fused = false;
   EpiParams e{};
-  e.mode = EPI_SOFTMIN; e.nq = axis == 0 ? c.p.n : c.p.m; e.splits = splits; e.s = c.s;
+  e.perm_out = axis == 0 ? c.perm_x : c.perm_y;
+  e.mode = EPI_SOFTMIN; e.nq = axis == 0 ? c.p.n : c.p.m; e.s = c.s;
   e.eps = c.p.eps; e.rho_o = axis == 0 ? c.p.rho1 : c.p.rho2; e.rho_i = axis == 0 ? c.p.rho2 : c.p.rho1;
   e.out_is_f = axis == 0; e.lnw_o = axis == 0 ? c.ln_a : c.ln_b; e.out = out; e.state = c.state;
   e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk;
-  UOT_CUDA(launch_combine(e, c.st));
+  v = sweep(c, axis, pot_i, nullptr, false, &splits, &e, &fused);
+  if (v != UOT_OK) return v;
+  e.splits = splits;
+  if (!fused) UOT_CUDA(launch_combine(e, c.st));
   return UOT_OK;
 }
 
@@ -355,21 +480,26 @@ uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* opt, floa
 uot_status uot_dual_value(const uot_problem* prob, const float* f, const float* g, double* out,
                           int32_t want_primal, void* ws, size_t ws_bytes, void* stream) {
   Ctx c;
-  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c, want_primal ? 2.0 : 1.0);
   if (v != UOT_OK) return v;
   if (!f || !g || !out) return fail(UOT_ERR_INVALID_ARG, "f, g and out must be device pointers");
   v = prepare(c);
   if (v != UOT_OK) return v;
+  const float *fi = nullptr, *gi = nullptr;
+  v = to_internal(c, 0, f, c.f_tmp, &fi);
+  if (v != UOT_OK) return v;
+  v = to_internal(c, 1, g, c.g_tmp, &gi);
+  if (v != UOT_OK) return v;
   int sr = 0, sc = 0;
-  v = sweep(c, 0, g, nullptr, false, &sr);
+  v = sweep(c, 0, gi, nullptr, false, &sr);
   if (v != UOT_OK) return v;
   if (want_primal) {
-    v = sweep(c, 1, f, nullptr, false, &sc);
+    v = sweep(c, 1, fi, nullptr, false, &sc);
     if (v != UOT_OK) return v;
   }
   DualParams d{};
   d.n = c.p.n; d.m = c.p.m; d.splits_r = sr; d.splits_c = sc; d.s = c.s; d.eps = c.p.eps;
-  d.rho1 = c.p.rho1; d.rho2 = c.p.rho2; d.f = f; d.g = g; d.a = c.p.a; d.b = c.p.b;
+  d.rho1 = c.p.rho1; d.rho2 = c.p.rho2; d.f = fi; d.g = gi; d.a = c.pa; d.b = c.pb;
   d.ln_a = c.ln_a; d.ln_b = c.ln_b; d.part_r = c.part_r; d.part_c = want_primal ? c.part_c : nullptr;
   d.blk = c.blk; d.state = c.state; d.out = out; d.want_primal = want_primal;
   UOT_CUDA(launch_dual(d, c.st));
@@ -379,7 +509,7 @@ uot_status uot_dual_value(const uot_problem* prob, const float* f, const float* 
 uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, float* grad_a, float* grad_b,
                     float* grad_x, float* grad_y, void* ws, size_t ws_bytes, void* stream) {
   Ctx c;
-  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c);
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c, 2.0);
   if (v != UOT_OK) return v;
   if (!f || !g) return fail(UOT_ERR_INVALID_ARG, "f and g must be device pointers");
   if ((grad_x || grad_y) && c.p.cost_kind != UOT_COST_POINTS)
@@ -387,6 +517,11 @@ uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, flo
   v = prepare(c);
   if (v != UOT_OK) return v;
   const uot_problem& p = c.p;
+  const float *fi = nullptr, *gi = nullptr;
+  v = to_internal(c, 0, f, c.f_tmp, &fi);
+  if (v != UOT_OK) return v;
+  v = to_internal(c, 1, g, c.g_tmp, &gi);
+  if (v != UOT_OK) return v;
   for (int side = 0; side < 2; ++side) {
     float* gw = side == 0 ? grad_a : grad_b;
     float* gpts = side == 0 ? grad_x : grad_y;
@@ -394,14 +529,15 @@ uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, flo
     const bool mom = gpts != nullptr;
     int splits = 0;
     // side 0: rows (x side) against y with pot g; side 1: columns against x with pot f
-    v = sweep(c, side, side == 0 ? g : f, nullptr, mom, &splits);
+    v = sweep(c, side, side == 0 ? gi : fi, nullptr, mom, &splits);
     if (v != UOT_OK) return v;
     UOT_CUDA(launch_mass(side == 0 ? p.b : p.a, side == 0 ? p.m : p.n, c.blk, c.state, 0, c.st));
     GradParams gp{};
     gp.nq = side == 0 ? p.n : p.m; gp.splits = splits; gp.dim = p.dim; gp.moments = mom ? p.dim : 0;
     gp.s = c.s; gp.eps = p.eps; gp.rho_o = side == 0 ? p.rho1 : p.rho2; gp.p = p.p;
-    gp.pot_o = side == 0 ? f : g; gp.part = side == 0 ? c.part_r : c.part_c;
+    gp.pot_o = side == 0 ? fi : gi; gp.part = side == 0 ? c.part_r : c.part_c;
     gp.grad_w = gw; gp.grad_pts = gpts; gp.lnw_o = side == 0 ? c.ln_a : c.ln_b; gp.state = c.state;
+    gp.perm = side == 0 ? c.perm_x : c.perm_y;
     UOT_CUDA(launch_grad_epilogue(gp, c.st));
   }
   return UOT_OK;

@@ -59,8 +59,35 @@ SweepGeom dense_col_geom(int nrows, int ncols);
 int max_splits_for(const uot_problem& p);
 
 constexpr int kMaxBlocks = 4096;
+constexpr int kTileKeys = 128;  // keys per local-frame tile of the tiled sweep
+
+// True when the tiled (Morton-ordered, local-frame) sweep serves this problem.
+inline bool tiled_path(const uot_problem& p) {
+  return p.cost_kind == UOT_COST_POINTS && p.dim <= 3 && p.p == 2.0f;
+}
+
+// Scratch of the ordering step (bounding box, Morton codes, radix sort).
+struct OrderScratch {
+  float* blk_f;           // [kMaxBlocks * 6]
+  float* box;             // [6]
+  unsigned int* counter;  // last-block counter (zero between launches)
+  unsigned int* code_in;  // [max(n, m)]
+  unsigned int* code_out; // [max(n, m)]
+  int* idx_in;            // [max(n, m)]
+  void* temp;             // radix-sort temporary storage
+  size_t temp_bytes;
+};
+size_t sort_temp_bytes(int n);
+// Morton-order pts (n x dim) and w: perm[i] = source index of sorted point i;
+// pts_s / w_s = gathered copies; centers = bounding-box centre of every tile.
+cudaError_t launch_order_points(const float* pts, const float* w, int n, int dim, OrderScratch sc, int* perm,
+                                float* pts_s, float* w_s, float4* centers, cudaStream_t st);
+cudaError_t launch_gather_vec(const float* v, const int* perm, int n, float* out, cudaStream_t st);
+cudaError_t launch_scatter_rows(const float* v, const int* perm, int n, int dim, float* out, cudaStream_t st);
 
 // ---- kernels (launchers) --------------------------------------------------
+
+struct EpiParams;
 
 // Side description: the "query" side owns the output vector, the "key" side is
 // summed over.
@@ -77,6 +104,15 @@ struct SideDesc {
 cudaError_t launch_points_sweep(const SideDesc& q, const SideDesc& k, int dim, float p,
                                 const float* pot_k, const double* shift_k, double s,
                                 bool moments, float* part, const SweepGeom& g, cudaStream_t st);
+// Tiled sweep (sorted clouds, dim <= 3, p = 2); centers_k = tile centres of the key side.
+SweepGeom tile_geom(int nq, int nk, int dim);
+// With epi != nullptr the last CTA of each row block also runs the half-step
+// epilogue for its rows (no separate combine launch); epi->part must be `part`.
+// The sweep itself ignores shift_k: it is handed to the epilogue (epi->key_shift),
+// which applies it exactly, so a shift needs epi != nullptr.
+cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
+                              const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
+                              const struct EpiParams* epi, cudaStream_t st);
 // Dense cost: axis 0 = rows of C are queries, axis 1 = columns of C are queries.
 cudaError_t launch_dense_sweep(int axis, const float* C, int n, int m, const float* l2w_k,
                                const float* pot_k, const double* shift_k, double s, float* part,
@@ -100,6 +136,7 @@ struct EpiParams {
   const double* lnw_o;  // natural log weights of the output side
   const float* old_out; // previous value of the output vector (residual), nullable
   float* out;           // output vector
+  const int* perm_out;  // nullable: out[perm_out[i]] receives row i (scatter to caller order)
   float* resid_hist;    // residual history (device), nullable
   int hist_index;
   int slot_in;          // slot read (key-side scalars, residual baseline)
@@ -107,15 +144,19 @@ struct EpiParams {
   DevState* state;
   const float* part;
   double* blk;
+  unsigned int* rb_counter;  // per-row-block arrival counters (fused sweeps), zero between launches
+  const double* key_shift;   // nullable: constant added to the key potential that the sweep left out
 };
 cudaError_t launch_combine(const EpiParams& e, cudaStream_t st);
 
 // Initial TI scalars: slot 0 = {A = Smin_a^rho1(f0), B = 0, cf = cg = 0}.
 cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rho1, DevState* st_dev,
                            double* blk, cudaStream_t st);
-// Output map Phi (TI) or copy (plain) of iterate in slot `slot`.
+// Output map Phi (TI) or copy (plain) of iterate in slot `slot`; perm_f / perm_g
+// (nullable) scatter sorted rows back to the caller's order.
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
-                            int m, const DevState* st_dev, int slot, cudaStream_t st);
+                            int m, const DevState* st_dev, int slot, const int* perm_f, const int* perm_g,
+                            cudaStream_t st);
 // log weights (natural FP64 and log2 FP32) and validity flags.
 cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, DevState* st_dev,
                                cudaStream_t st);
@@ -146,6 +187,7 @@ struct GradParams {
   float* grad_w;         // d/d weights of this side, nullable
   float* grad_pts;       // d/d points of this side [nq x dim], nullable
   const double* lnw_o;   // natural log weights of this side
+  const int* perm;       // nullable: outputs of row i go to caller row perm[i]
   DevState* state;
 };
 cudaError_t launch_grad_epilogue(const GradParams& gp, cudaStream_t st);

@@ -34,7 +34,7 @@ class UOTError(RuntimeError):
 
 class Problem(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("dim", C.c_int32), ("cost_kind", C.c_int32),
-                ("p", C.c_float), ("reserved", C.c_int32),
+                ("p", C.c_float), ("ordering", C.c_int32),
                 ("eps", C.c_double), ("rho1", C.c_double), ("rho2", C.c_double),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("C", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p)]
 
@@ -126,6 +126,7 @@ class Spec:
     y: torch.Tensor | None = None
     C: torch.Tensor | None = None
     p: float = 2.0
+    ordering: int = 0   # 0 automatic, 1 always Morton-order (dim <= 3, p = 2), 2 never
 
     def __post_init__(self):
         if self.C is None and (self.x is None or self.y is None):
@@ -154,7 +155,7 @@ class Spec:
     def struct(self) -> Problem:
         dense = self.C is not None
         return Problem(self.n, self.m, 0 if dense else self.x.shape[1], COST_DENSE if dense else COST_POINTS,
-                       float(self.p), 0, float(self.eps), float(self.rho1), float(self.rho2),
+                       float(self.p), int(self.ordering), float(self.eps), float(self.rho1), float(self.rho2),
                        None if dense else self.x.data_ptr(), None if dense else self.y.data_ptr(),
                        self.C.data_ptr() if dense else None, self.a.data_ptr(), self.b.data_ptr())
 

@@ -71,7 +71,12 @@ def test_argument_errors_without_device_work(L):
     assert st == 1 and b"eps" in L.uot_last_error()
     ok = uot.Problem(4, 5, 1, 0, 2.0, 0, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
     st = L.uot_sinkhorn(C.byref(ok), None, None, None, None, None, 0, None)
+    assert st == 1 and b"options" in L.uot_last_error()
+    opt = uot.Options(10, 1, 0.0, 0, 0, None)
+    st = L.uot_sinkhorn(C.byref(ok), C.byref(opt), None, None, None, None, 0, None)
     assert st == 2  # no workspace
+    bad_order = uot.Problem(4, 5, 1, 0, 2.0, 3, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
+    assert L.uot_workspace_size(C.byref(bad_order)) == 0 and b"ordering" in L.uot_last_error()
     st = L.uot_softmin(C.byref(ok), 3, 256, 256, 256, 1 << 30, None)
     assert st == 1 and b"axis" in L.uot_last_error()
     dense_unaligned = uot.Problem(4, 5, 0, 1, 2.0, 0, 0.1, 1.0, 1.0, None, None, 260, 256, 256)

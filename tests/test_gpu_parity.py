@@ -28,12 +28,16 @@ def U():
     return uot
 
 
-def spec_of(U, p, dense=False):
+def spec_of(U, p, dense=False, ordering=0):
     dev = torch.device("cuda:0")
     t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
     if dense:
         return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, C=t(W.dense_cost_f32(p.x, p.y)), p=p.p)
-    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), p=p.p)
+    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), p=p.p, ordering=ordering)
+
+
+# the points cost with dim <= 3 and p = 2 has two kernels: Morton-ordered tiles (1) and direct (2)
+ORDERINGS = pytest.mark.parametrize("ordering", [1, 2], ids=["tiled", "direct"])
 
 
 def pot_tol(eps, ref):
@@ -73,10 +77,11 @@ SWEEP_CASES = [
 ]
 
 
+@ORDERINGS
 @pytest.mark.parametrize("n,m,d,eps,p,zf", SWEEP_CASES)
-def test_softmin_points(U, n, m, d, eps, p, zf):
+def test_softmin_points(U, n, m, d, eps, p, zf, ordering):
     pr = W.random_problem(n, m, d, seed=n + m + d, eps=eps, zero_frac=zf, p=p)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     rng = np.random.default_rng(7)
     g = (0.3 * rng.standard_normal(m)).astype(np.float32)
     f = (0.3 * rng.standard_normal(n)).astype(np.float32)
@@ -99,10 +104,11 @@ def test_softmin_dense(U, n, m, eps):
     assert_pot_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, pr.a, f, eps), eps, "dense cols")
 
 
-def test_softmin_shift_property(U):
+@ORDERINGS
+def test_softmin_shift_property(U, ordering):
     """Smin(h + tau) = Smin(h) + tau on the device (App. B)."""
     pr = W.random_problem(2000, 1500, 3, seed=3, eps=0.02)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     g = torch.zeros(1500, device="cuda")
     S0 = U.softmin(spec, g, 0).double()
     S1 = U.softmin(spec, g + 0.25, 0).double()
@@ -111,11 +117,12 @@ def test_softmin_shift_property(U):
 
 # ------------------------------------------------------------------ solvers
 
+@ORDERINGS
 @pytest.mark.parametrize("method", ["plain", "ti"])
-def test_config1_1000_iterations_match_golden(U, method):
+def test_config1_1000_iterations_match_golden(U, method, ordering):
     d = json.load(open(GOLDEN))
     pr = W.config1()
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     r = U.solve(spec, method, max_iter=1000, tol=0.0)
     assert r.iters == 1000
     key = "plain" if method == "plain" else "ti"
@@ -128,12 +135,13 @@ def test_config1_1000_iterations_match_golden(U, method):
 
 
 @pytest.mark.parametrize("method", ["plain", "ti"])
-@pytest.mark.parametrize("dense", [False, True])
-def test_iterates_match_oracle_ragged(U, method, dense):
+@pytest.mark.parametrize("kind", ["tiled", "direct", "dense"])
+def test_iterates_match_oracle_ragged(U, method, kind):
     """N != M, rho1 != rho2, unequal masses, zero weights: iterate-by-iterate parity."""
     pr = W.random_problem(611, 437, 2, seed=21, eps=0.05, rho1=0.3, rho2=2.0, mass_a=1.3, mass_b=0.6,
                           zero_frac=0.1)
-    spec = spec_of(U, pr, dense=dense)
+    dense = kind == "dense"
+    spec = spec_of(U, pr, dense=dense, ordering={"tiled": 1, "direct": 2, "dense": 0}[kind])
     C = O._t(W.dense_cost_f32(pr.x, pr.y)) if dense else O.cost_matrix(pr.x, pr.y)
     for T in (1, 7, 60):
         r = U.solve(spec, method, max_iter=T)
@@ -146,9 +154,10 @@ def test_iterates_match_oracle_ragged(U, method, dense):
             assert abs(r.lam - ref.lam) < 1e-4 * pr.eps
 
 
-def test_residual_history_and_early_stop(U):
+@ORDERINGS
+def test_residual_history_and_early_stop(U, ordering):
     pr = W.random_problem(400, 300, 1, seed=5, eps=0.05, rho1=1.0, rho2=0.5)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     C = O.cost_matrix(pr.x, pr.y)
     r = U.solve(spec, "ti", max_iter=30, history=True)
     h = r.history.cpu().double()
@@ -175,10 +184,11 @@ def test_ti_faster_than_plain_same_fixed_point(U):
     assert (ti.f - pl.f).abs().max().item() < 2e-4
 
 
-def test_mass_equality_after_translation(U):
+@ORDERINGS
+def test_mass_equality_after_translation(U, ordering):
     """(f, g) = Phi(fb, gb) has <a, e^{-f/rho1}> = <b, e^{-g/rho2}> at every iterate (Prop. 1)."""
     pr = W.random_problem(800, 900, 3, seed=2, eps=0.05, rho1=0.4, rho2=3.0, mass_a=2.0, mass_b=0.5)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     for T in (1, 3, 25):
         r = U.solve(spec, "ti", max_iter=T)
         f, g = r.f.double().cpu(), r.g.double().cpu()
@@ -210,10 +220,11 @@ def test_n1_and_degenerate_sizes(U):
     assert abs(U.dual_value(spec, r.f, r.g)[0].item() - val) < 1e-6 * abs(val)
 
 
-def test_warm_start_translation_recovery(U):
+@ORDERINGS
+def test_warm_start_translation_recovery(U, ordering):
     """TI from the optimum plus a constant returns to the optimum after one iteration (T2)."""
     pr = W.random_problem(500, 600, 2, seed=4, eps=0.05, rho1=0.8, rho2=0.8)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     r = U.solve(spec, "ti", max_iter=5000, tol=1e-7, check_every=5)
     r1 = U.solve(spec, "ti", max_iter=1, f0=r.f + 0.5)
     assert (r1.f - r.f).abs().max().item() < 1e-4 * pr.eps + 1e-6
@@ -222,10 +233,10 @@ def test_warm_start_translation_recovery(U):
 
 # --------------------------------------------------------- value, gradients
 
-@pytest.mark.parametrize("d,p", [(1, 2.0), (3, 2.0), (2, 1.5), (8, 2.0)])
-def test_dual_primal_and_envelope_grads(U, d, p):
+@pytest.mark.parametrize("d,p,ordering", [(1, 2.0, 1), (3, 2.0, 1), (3, 2.0, 2), (2, 1.5, 0), (8, 2.0, 0)])
+def test_dual_primal_and_envelope_grads(U, d, p, ordering):
     pr = W.random_problem(700, 500, d, seed=10 + d, eps=0.05, rho1=0.6, rho2=1.4, mass_a=1.1, mass_b=0.8, p=p)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering=ordering)
     r = U.solve(spec, "ti", max_iter=5000, tol=1e-7, check_every=5)
     f64, g64 = r.f.double().cpu(), r.g.double().cpu()
     C = O.cost_matrix(pr.x, pr.y, p)
