@@ -204,6 +204,45 @@ UOT_API uint64_t uot_kernel_launches(void);
 UOT_API uot_status uot_profile_begin(void);
 UOT_API uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* launches);
 
+/* A batch of independent problems with the points cost |x - y|^2 (p = 2) and
+ * dim <= 3, each with its own sizes, dimension and parameters.  Data of all
+ * problems is packed in shared device arrays; offsets are element offsets into
+ * those arrays.  f and g outputs use the offsets of a and b. */
+typedef struct {
+  int32_t count;          /* number of problems >= 1                                      */
+  int32_t reserved;
+  const int32_t* n;       /* host [count]: N_k >= 1                                        */
+  const int32_t* m;       /* host [count]: M_k >= 1                                        */
+  const int32_t* dim;     /* host [count]: 1..3                                            */
+  const double* eps;      /* host [count]                                                  */
+  const double* rho1;     /* host [count]                                                  */
+  const double* rho2;     /* host [count]                                                  */
+  const int64_t* x_off;   /* host [count]: first coordinate of problem k in x (N_k x dim_k) */
+  const int64_t* y_off;   /* host [count]: first coordinate of problem k in y              */
+  const int64_t* a_off;   /* host [count]: first weight of problem k in a (and f)          */
+  const int64_t* b_off;   /* host [count]: first weight of problem k in b (and g)          */
+  const float* x;         /* device, packed coordinates                                    */
+  const float* y;
+  const float* a;         /* device, packed weights                                        */
+  const float* b;
+} uot_batch;
+
+/* Workspace bytes for uot_sinkhorn_batched on `batch` (0 if invalid). */
+UOT_API size_t uot_batch_workspace_size(const uot_batch* batch);
+
+/* Plain (ti = 0) or translation-invariant (ti = 1) Sinkhorn on every problem of
+ * the batch at once (same updates, residual and stopping rule per problem as
+ * uot_sinkhorn / uot_ti_sinkhorn; opt->warm_start and residual_history are not
+ * supported and must be 0 / NULL).  Each half-step is one launch over all
+ * problems still running; problems stop individually when their residual is
+ * <= tol at a check, or at max_iter.  With a non-NULL stream, chunks of
+ * check_every iterations are captured once as a CUDA graph and replayed.
+ * results: host [count], filled before return.  Returns UOT_OK when every
+ * problem converged, UOT_NOT_CONVERGED when some stopped at max_iter, an
+ * error otherwise. */
+UOT_API uot_status uot_sinkhorn_batched(const uot_batch* batch, const uot_options* opt, int32_t ti, float* f,
+                                        float* g, uot_result* results, void* ws, size_t ws_bytes, void* stream);
+
 /* Message describing the last error of the calling thread ("" if none). */
 UOT_API const char* uot_last_error(void);
 

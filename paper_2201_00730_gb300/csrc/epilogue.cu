@@ -138,7 +138,7 @@ __global__ void k_finalize(int ti, const float* f_hat, const float* g_hat, float
   }
 }
 
-__global__ void k_log_weights(const float* w, int n, double* lnw, float* l2w, DevState* st) {
+__global__ void k_log_weights(const float* w, int n, double* lnw, float* l2w, int* flags) {
   int bad = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float v = w[i];
@@ -152,7 +152,7 @@ __global__ void k_log_weights(const float* w, int n, double* lnw, float* l2w, De
       l2w[i] = kZeroW;
     }
   }
-  if (bad) atomicOr(&st->status, kStatusBadWeights);
+  if (bad && flags) atomicOr(flags, kStatusBadWeights);
 }
 
 // ---- dual / primal objective ------------------------------------------------
@@ -315,9 +315,8 @@ cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, DevState* s,
-                               cudaStream_t st) {
-  k_log_weights<<<grid_for(n), kBlk, 0, st>>>(w, n, lnw, l2w, s);
+cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, int* flags, cudaStream_t st) {
+  k_log_weights<<<grid_for(n), kBlk, 0, st>>>(w, n, lnw, l2w, flags);
   note_launch();
   return cudaGetLastError();
 }

@@ -240,8 +240,8 @@ uot_status prepare(Ctx& c) {
     UOT_CUDA(launch_order_points(c.p.x, c.p.a, c.p.n, c.p.dim, c.osc, c.perm_x, c.xs, c.as, c.cen_x, c.st));
     UOT_CUDA(launch_order_points(c.p.y, c.p.b, c.p.m, c.p.dim, c.osc, c.perm_y, c.ys, c.bs, c.cen_y, c.st));
   }
-  UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, c.state, c.st));
-  UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, c.state, c.st));
+  UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, &c.state->status, c.st));
+  UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, &c.state->status, c.st));
   return UOT_OK;
 }
 

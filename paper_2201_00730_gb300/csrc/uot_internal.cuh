@@ -157,9 +157,9 @@ cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rh
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
                             int m, const DevState* st_dev, int slot, const int* perm_f, const int* perm_g,
                             cudaStream_t st);
-// log weights (natural FP64 and log2 FP32) and validity flags.
-cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, DevState* st_dev,
-                               cudaStream_t st);
+// log weights (natural FP64 and log2 FP32); negative / non-finite weights set
+// kStatusBadWeights in *flags (nullable).
+cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, int* flags, cudaStream_t st);
 
 // Dual value / primal value reductions from the row (and column) sweep partials.
 struct DualParams {

@@ -49,6 +49,14 @@ class Result(C.Structure):
                 ("residual", C.c_double), ("lambda_", C.c_double)]
 
 
+class Batch(C.Structure):
+    _fields_ = [("count", C.c_int32), ("reserved", C.c_int32),
+                ("n", C.c_void_p), ("m", C.c_void_p), ("dim", C.c_void_p),
+                ("eps", C.c_void_p), ("rho1", C.c_void_p), ("rho2", C.c_void_p),
+                ("x_off", C.c_void_p), ("y_off", C.c_void_p), ("a_off", C.c_void_p), ("b_off", C.c_void_p),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -74,6 +82,11 @@ def lib() -> C.CDLL:
         L.uot_dual_value.restype = C.c_int
         L.uot_grad.argtypes = [P, V, V, V, V, V, V, V, S, V]
         L.uot_grad.restype = C.c_int
+        L.uot_batch_workspace_size.argtypes = [C.POINTER(Batch)]
+        L.uot_batch_workspace_size.restype = S
+        L.uot_sinkhorn_batched.argtypes = [C.POINTER(Batch), C.POINTER(Options), C.c_int32, V, V,
+                                           C.POINTER(Result), V, S, V]
+        L.uot_sinkhorn_batched.restype = C.c_int
         L.uot_kernel_launches.argtypes = []
         L.uot_kernel_launches.restype = C.c_uint64
         L.uot_profile_begin.argtypes = []
@@ -314,6 +327,60 @@ class SweepProfile:
         _check(lib().uot_profile_end(C.byref(ms), C.byref(timed), C.byref(n)))
         self.sweep_ms, self.timed, self.launches = ms.value, timed.value, n.value
         return False
+
+
+@dataclass
+class BatchOut:
+    f: list            # per-problem f (device tensors, views into one packed buffer)
+    g: list
+    iters: list
+    converged: list
+    residual: list
+    lam: list
+    status: int
+
+
+def solve_batched(problems, method: str = "ti", max_iter: int = 20000, tol: float = 1e-6,
+                  check_every: int = 10, device="cuda:0") -> BatchOut:
+    """Solve many independent point-cloud problems in one batched call.
+
+    `problems`: sequence of objects with numpy/torch arrays x (n x d), y (m x d), a (n), b (m) and floats
+    eps, rho1, rho2 (d in 1..3, p = 2).  Inputs are packed into device arrays here (marshalling only).
+    """
+    import numpy as np
+    dev = torch.device(device)
+    cnt = len(problems)
+    n = np.array([p.x.shape[0] for p in problems], dtype=np.int32)
+    m = np.array([p.y.shape[0] for p in problems], dtype=np.int32)
+    d = np.array([p.x.shape[1] for p in problems], dtype=np.int32)
+    eps = np.array([p.eps for p in problems], dtype=np.float64)
+    r1 = np.array([p.rho1 for p in problems], dtype=np.float64)
+    r2 = np.array([p.rho2 for p in problems], dtype=np.float64)
+    xo = np.concatenate([[0], np.cumsum(n.astype(np.int64) * d)[:-1]]).astype(np.int64)
+    yo = np.concatenate([[0], np.cumsum(m.astype(np.int64) * d)[:-1]]).astype(np.int64)
+    ao = np.concatenate([[0], np.cumsum(n.astype(np.int64))[:-1]]).astype(np.int64)
+    bo = np.concatenate([[0], np.cumsum(m.astype(np.int64))[:-1]]).astype(np.int64)
+    cat = lambda vs: torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [np.asarray(v, dtype=np.float32).ravel() for v in vs]))).to(dev)
+    X, Y = cat([p.x for p in problems]), cat([p.y for p in problems])
+    A, B = cat([p.a for p in problems]), cat([p.b for p in problems])
+    host = [n, m, d, eps, r1, r2, xo, yo, ao, bo]
+    bt = Batch(cnt, 0, *[h.ctypes.data for h in host], X.data_ptr(), Y.data_ptr(), A.data_ptr(), B.data_ptr())
+    nbytes = lib().uot_batch_workspace_size(C.byref(bt))
+    if nbytes == 0:
+        raise UOTError(1, lib().uot_last_error().decode())
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    F = torch.empty(A.numel(), dtype=torch.float32, device=dev)
+    G = torch.empty(B.numel(), dtype=torch.float32, device=dev)
+    res = (Result * cnt)()
+    opt = Options(int(max_iter), int(check_every), float(tol), 0, 0, None)
+    st = lib().uot_sinkhorn_batched(C.byref(bt), C.byref(opt), 1 if method == "ti" else 0, _ptr(F), _ptr(G),
+                                    res, _ptr(ws), ws.numel(), _stream())
+    _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
+    fs = [F[ao[k]:ao[k] + n[k]] for k in range(cnt)]
+    gs = [G[bo[k]:bo[k] + m[k]] for k in range(cnt)]
+    return BatchOut(fs, gs, [r.iters for r in res], [bool(r.converged) for r in res],
+                    [r.residual for r in res], [r.lambda_ for r in res], st)
 
 
 def version() -> str:
