@@ -84,14 +84,25 @@ def log_weights(w) -> torch.Tensor:
     return out
 
 
+def log_dot_exp(w, z) -> torch.Tensor:
+    """log <w, exp(z)> = log sum_i w_i e^{z_i} over the last axis, with the weights kept outside the
+    exponential (so a zero weight has the derivative e^{z_i} / <w, e^z>, like any other) and the largest
+    exponent of a positive weight taken out first for range (it cancels exactly)."""
+    w = _t(w)
+    live = w > 0
+    zm = torch.where(live, z, torch.full_like(z, -math.inf))
+    m = zm.max(dim=-1, keepdim=True).values.detach()
+    return m.squeeze(-1) + torch.log((w * torch.exp(z - m)).sum(-1))
+
+
 def softmin(w, h, eps: float) -> torch.Tensor:
     """Smin_w^eps(h) = -eps log <w, exp(-h/eps)>, reduced over the last axis.
 
-    Definition of the softmin in Sec. 3 ("F-Sinkhorn"); evaluated as a
-    max-shifted log-sum-exp.
+    Definition of the softmin in Sec. 3 ("F-Sinkhorn"), written with the weights
+    outside the exponential as in the definition.
     """
     w, h = _t(w), _t(h)
-    return -eps * torch.logsumexp(log_weights(w) - h / eps, dim=-1)
+    return -eps * log_dot_exp(w, -h / eps)
 
 
 def smin_rows(C, b, g, eps: float) -> torch.Tensor:
@@ -123,8 +134,8 @@ def lambda_star(a, b, fb, gb, rho1: float, rho2: float) -> torch.Tensor:
     lambda* = rho1 rho2/(rho1+rho2) * log( <a, e^{-fb/rho1}> / <b, e^{-gb/rho2}> ),
     with both logs taken as stabilised log-sum-exps (Prop. 2, remark after it).
     """
-    la = torch.logsumexp(log_weights(a) - _t(fb) / rho1, dim=-1)
-    lb = torch.logsumexp(log_weights(b) - _t(gb) / rho2, dim=-1)
+    la = log_dot_exp(a, -_t(fb) / rho1)
+    lb = log_dot_exp(b, -_t(gb) / rho2)
     return rho1 * rho2 / (rho1 + rho2) * (la - lb)
 
 

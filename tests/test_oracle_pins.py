@@ -401,3 +401,22 @@ def test_unrolled_matches_envelope_when_converged():
     assert abs(val.item() - v2) < 1e-12
     for u, e in ((ga, ea), (gb, eb), (gx, ex), (gy, ey)):
         assert (u - e).abs().max() < 1e-9
+
+
+def test_unrolled_grads_with_zero_weights_vs_one_sided_differences():
+    """A zero weight keeps its derivative (the softmin is smooth in w_j at w_j = 0, Sec. 3 definition):
+    autograd of the oracle agrees with a forward difference there."""
+    p = W.random_problem(6, 5, 1, seed=14, eps=0.3, rho1=0.6, rho2=1.2, mass_a=1.0, mass_b=1.1, zero_frac=0.34)
+    x, y, a, b = (O._t(v) for v in (p.x, p.y, p.a, p.b))
+    T = 3
+    val, ga, gb, gx, gy = O.unrolled_grads(x, y, a, b, p.eps, p.rho1, p.rho2, T)
+    for w, g, name in ((a, ga, "a"), (b, gb, "b")):
+        zeros = (w == 0).nonzero().flatten()
+        assert zeros.numel() > 0
+        for k in zeros.tolist():
+            h = 1e-7
+            w2 = w.clone()
+            w2[k] = h
+            args = {"a": a, "b": b, name: w2}
+            fd = (O.truncated_ti_value(x, y, args["a"], args["b"], p.eps, p.rho1, p.rho2, T).item() - val.item()) / h
+            assert abs(fd - g[k].item()) < 1e-5 * max(1.0, abs(fd)), (name, k, fd, g[k].item())
