@@ -204,6 +204,22 @@ UOT_API uint64_t uot_kernel_launches(void);
 UOT_API uot_status uot_profile_begin(void);
 UOT_API uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* launches);
 
+/* Unrolled gradient of the truncated solve: with (f_T, g_T) = Phi(fb_T, gb_T)
+ * after T H-Sinkhorn iterations from fb_0 = 0 (as uot_ti_sinkhorn with
+ * max_iter = T, tol = 0), writes value[0] = F_eps(f_T, g_T) (device double) and
+ * the exact derivatives of that value with respect to a, b, x, y (outputs
+ * nullable), obtained by reverse mode through all T iterations: each half-step
+ * (softmin sweep, aprox, FP64 mass reduction and translation of the proof of
+ * Prop. 4, App. B) is differentiated, the softmins by one adjoint sweep each.
+ * Iterates are checkpointed every ckpt_every iterations and each segment is
+ * recomputed once during the reverse pass (memory O((N + M) (T/ckpt_every +
+ * ckpt_every (dim + 3)))).  Points cost with p = 2 only.  Workspace:
+ * uot_unrolled_workspace_size.  Synchronises the stream on return. */
+UOT_API size_t uot_unrolled_workspace_size(const uot_problem* prob, int32_t T, int32_t ckpt_every);
+UOT_API uot_status uot_grad_unrolled(const uot_problem* prob, int32_t T, int32_t ckpt_every, double* value,
+                                     float* grad_a, float* grad_b, float* grad_x, float* grad_y, void* ws,
+                                     size_t ws_bytes, void* stream);
+
 /* A batch of independent problems with the points cost |x - y|^2 (p = 2) and
  * dim <= 3, each with its own sizes, dimension and parameters.  Data of all
  * problems is packed in shared device arrays; offsets are element offsets into

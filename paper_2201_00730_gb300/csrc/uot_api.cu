@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -409,6 +410,257 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   return out;
 }
 
+
+// ---- unrolled backward -------------------------------------------------------
+// Extra workspace of uot_grad_unrolled after the regular layout of the problem.
+struct URLayout {
+  size_t base, ck_f, ck_slot, fbar, gbarn, Sp, Gp, ghat, S, G, fhat, rec, fst, g0, fbb, gbb, Sb, Spb, ffin, gfin,
+      fbT, gbT, ga, gb, gx, gy, val, mom, adj, sums, total;
+  int nck, K;
+};
+
+URLayout ur_layout(const uot_problem& p, int T, int K) {
+  URLayout L{};
+  L.K = K;
+  L.nck = (T + K - 1) / K;
+  size_t off = align256(ws_layout(p).total);
+  L.base = off;
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  const size_t N = p.n, M = p.m, D = p.dim;
+  L.ck_f = take(sizeof(float) * N * L.nck);
+  L.ck_slot = take(sizeof(Slot) * 2 * L.nck);
+  L.fbar = take(sizeof(float) * N * K);
+  L.gbarn = take(sizeof(float) * M * K);
+  L.Sp = take(sizeof(float) * M * K);
+  L.Gp = take(sizeof(float) * M * D * K);
+  L.ghat = take(sizeof(float) * M * K);
+  L.S = take(sizeof(float) * N * K);
+  L.G = take(sizeof(float) * N * D * K);
+  L.fhat = take(sizeof(float) * N * K);
+  L.rec = take(sizeof(double) * 8 * K);
+  L.fst = take(sizeof(float) * N);
+  L.g0 = take(sizeof(float) * M);
+  L.fbb = take(sizeof(float) * N);
+  L.gbb = take(sizeof(float) * M);
+  L.Sb = take(sizeof(float) * N);
+  L.Spb = take(sizeof(float) * M);
+  L.ffin = take(sizeof(float) * N);
+  L.gfin = take(sizeof(float) * M);
+  L.fbT = take(sizeof(float) * N);
+  L.gbT = take(sizeof(float) * M);
+  L.ga = take(sizeof(float) * N);
+  L.gb = take(sizeof(float) * M);
+  L.gx = take(sizeof(float) * N * D);
+  L.gy = take(sizeof(float) * M * D);
+  const size_t Q = N > M ? N : M;
+  L.val = take(sizeof(double) * Q);
+  L.mom = take(sizeof(double) * Q * D);
+  const SweepGeom a1 = adjoint_geom(p.m, p.n), a2 = adjoint_geom(p.n, p.m);
+  size_t ap = (size_t)a1.splits * (2 + D) * M;
+  if ((size_t)a2.splits * (2 + D) * N > ap) ap = (size_t)a2.splits * (2 + D) * N;
+  L.adj = take(sizeof(float) * ap);
+  L.sums = take(sizeof(double) * 8);
+  L.total = off;
+  return L;
+}
+
+uot_status ur_check(const uot_problem* prob, int T, int K) {
+  uot_status v = validate(prob);
+  if (v != UOT_OK) return v;
+  if (prob->cost_kind != UOT_COST_POINTS || prob->p != 2.0f)
+    return fail(UOT_ERR_UNSUPPORTED, "the unrolled backward covers the points cost with p = 2");
+  if (T < 1 || K < 1) return fail(UOT_ERR_INVALID_ARG, "need T >= 1 and ckpt_every >= 1");
+  return UOT_OK;
+}
+
+// One TI iteration t -> t+1 on the direct kernels.  With rec != nullptr the
+// iteration is recorded for the backward pass at segment index j.
+uot_status ur_iteration(Ctx& c, const URLayout& L, char* b, int t, float* fst, float* gbuf[2], bool rec, int j) {
+  const uot_problem& p = c.p;
+  const int si = t & 1, so = (t + 1) & 1;
+  const size_t N = p.n, M = p.m, D = p.dim;
+  const int mom = rec ? p.dim : 0;
+  const double gscale = (p.dim <= 3) ? 2.0 / sqrt(c.s) : 1.0;  // moment convention of the sweep kernels
+  float* fbar = reinterpret_cast<float*>(b + L.fbar) + N * j;
+  float* gbarn = reinterpret_cast<float*>(b + L.gbarn) + M * j;
+  float* Sp = reinterpret_cast<float*>(b + L.Sp) + M * j;
+  float* Gp = reinterpret_cast<float*>(b + L.Gp) + M * D * j;
+  float* ghat = reinterpret_cast<float*>(b + L.ghat) + M * j;
+  float* S = reinterpret_cast<float*>(b + L.S) + N * j;
+  float* G = reinterpret_cast<float*>(b + L.G) + N * D * j;
+  float* fhat = reinterpret_cast<float*>(b + L.fhat) + N * j;
+  double* recd = reinterpret_cast<double*>(b + L.rec) + 8 * j;
+  if (rec) UOT_CUDA(launch_add_scalar(fst, &c.state->slot[si].cf, p.n, fbar, c.st));
+  // g half-step
+  int splits = 0;
+  uot_status v = sweep(c, 1, fst, &c.state->slot[si].cf, rec, &splits);
+  if (v != UOT_OK) return v;
+  EpiParams e{};
+  e.nq = p.m; e.splits = splits; e.moments = mom; e.s = c.s; e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1;
+  e.out_is_f = 0; e.lnw_o = c.ln_b; e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c;
+  e.blk = c.blk;
+  if (rec) {
+    EpiParams es = e;
+    es.mode = EPI_SOFTMIN; es.out = Sp;
+    UOT_CUDA(launch_combine(es, c.st));
+    UOT_CUDA(launch_moments(c.part_c, p.m, p.dim, splits, gscale, Gp, c.st));
+  }
+  e.mode = EPI_TI; e.out = gbuf[so];
+  UOT_CUDA(launch_combine(e, c.st));
+  if (rec) {
+    UOT_CUDA(cudaMemcpyAsync(ghat, gbuf[so], sizeof(float) * M, cudaMemcpyDeviceToDevice, c.st));
+    UOT_CUDA(launch_add_scalar(gbuf[so], &c.state->slot[so].cg, p.m, gbarn, c.st));
+  }
+  // f half-step
+  v = sweep(c, 0, gbuf[so], &c.state->slot[so].cg, rec, &splits);
+  if (v != UOT_OK) return v;
+  EpiParams ef = e;
+  ef.nq = p.n; ef.splits = splits; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1; ef.lnw_o = c.ln_a;
+  ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r;
+  if (rec) {
+    EpiParams es = ef;
+    es.mode = EPI_SOFTMIN; es.out = S;
+    UOT_CUDA(launch_combine(es, c.st));
+    UOT_CUDA(launch_moments(c.part_r, p.n, p.dim, splits, gscale, G, c.st));
+  }
+  ef.mode = EPI_TI; ef.out = fst;
+  UOT_CUDA(launch_combine(ef, c.st));
+  if (rec) {
+    UOT_CUDA(cudaMemcpyAsync(fhat, fst, sizeof(float) * N, cudaMemcpyDeviceToDevice, c.st));
+    UOT_CUDA(launch_record_scalars(c.state, si, so, recd, c.st));
+  }
+  return UOT_OK;
+}
+
+uot_status grad_unrolled(const uot_problem* prob, int T, int K, double* value, float* grad_a, float* grad_b,
+                         float* grad_x, float* grad_y, void* ws, size_t ws_bytes, void* stream) {
+  uot_status v = ur_check(prob, T, K);
+  if (v != UOT_OK) return v;
+  uot_problem pd = *prob;
+  pd.ordering = 2;  // natural order and the direct kernels
+  const URLayout L = ur_layout(pd, T, K);
+  if (!ws) return fail(UOT_ERR_WORKSPACE, "workspace is NULL");
+  if (ws_bytes < L.total) return fail(UOT_ERR_WORKSPACE, "workspace too small: %zu given, %zu needed", ws_bytes, L.total);
+  if (!value) return fail(UOT_ERR_INVALID_ARG, "value must be a device pointer");
+  Ctx c;
+  v = make_ctx(&pd, ws, ws_bytes, stream, &c);
+  if (v != UOT_OK) return v;
+  v = prepare(c);
+  if (v != UOT_OK) return v;
+  char* b = static_cast<char*>(ws);
+  const uot_problem& p = c.p;
+  const size_t N = p.n, M = p.m, D = p.dim;
+  float* fst = reinterpret_cast<float*>(b + L.fst);
+  float* gbuf[2] = {reinterpret_cast<float*>(b + L.g0), c.g_alt};
+  float* ck_f = reinterpret_cast<float*>(b + L.ck_f);
+  Slot* ck_slot = reinterpret_cast<Slot*>(b + L.ck_slot);
+  double* sums = reinterpret_cast<double*>(b + L.sums);
+  float *fbb = reinterpret_cast<float*>(b + L.fbb), *gbb = reinterpret_cast<float*>(b + L.gbb);
+  float *Sb = reinterpret_cast<float*>(b + L.Sb), *Spb = reinterpret_cast<float*>(b + L.Spb);
+  float *ffin = reinterpret_cast<float*>(b + L.ffin), *gfin = reinterpret_cast<float*>(b + L.gfin);
+  float *fbT = reinterpret_cast<float*>(b + L.fbT), *gbT = reinterpret_cast<float*>(b + L.gbT);
+  float *ga = reinterpret_cast<float*>(b + L.ga), *gb = reinterpret_cast<float*>(b + L.gb);
+  float *gx = reinterpret_cast<float*>(b + L.gx), *gy = reinterpret_cast<float*>(b + L.gy);
+  double *val = reinterpret_cast<double*>(b + L.val), *mom = reinterpret_cast<double*>(b + L.mom);
+  float* adj = reinterpret_cast<float*>(b + L.adj);
+  unsigned int* ctr = &c.state->counter;
+
+  // forward with checkpoints of (f_hat, scalar slots) every K iterations
+  UOT_CUDA(cudaMemsetAsync(fst, 0, sizeof(float) * N, c.st));
+  UOT_CUDA(cudaMemsetAsync(gbuf[0], 0, sizeof(float) * M, c.st));
+  UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
+  for (int t = 0; t < T; ++t) {
+    if (t % K == 0) {
+      UOT_CUDA(cudaMemcpyAsync(ck_f + N * (t / K), fst, sizeof(float) * N, cudaMemcpyDeviceToDevice, c.st));
+      UOT_CUDA(cudaMemcpyAsync(ck_slot + 2 * (t / K), c.state->slot, sizeof(Slot) * 2, cudaMemcpyDeviceToDevice,
+                               c.st));
+    }
+    v = ur_iteration(c, L, b, t, fst, gbuf, false, 0);
+    if (v != UOT_OK) return v;
+  }
+  // output pair, value and the direct partials of F_eps
+  const int sT = T & 1;
+  UOT_CUDA(launch_finalize(1, fst, gbuf[sT], ffin, gfin, p.n, p.m, c.state, sT, nullptr, nullptr, c.st));
+  UOT_CUDA(launch_add_scalar(fst, &c.state->slot[sT].cf, p.n, fbT, c.st));
+  UOT_CUDA(launch_add_scalar(gbuf[sT], &c.state->slot[sT].cg, p.m, gbT, c.st));
+  int sr = 0, sc = 0;
+  v = sweep(c, 0, gfin, nullptr, false, &sr);
+  if (v != UOT_OK) return v;
+  DualParams d{};
+  d.n = p.n; d.m = p.m; d.splits_r = sr; d.splits_c = 0; d.s = c.s; d.eps = p.eps; d.rho1 = p.rho1;
+  d.rho2 = p.rho2; d.f = ffin; d.g = gfin; d.a = c.pa; d.b = c.pb; d.ln_a = c.ln_a; d.ln_b = c.ln_b;
+  d.part_r = c.part_r; d.part_c = nullptr; d.blk = c.blk; d.state = c.state; d.out = value; d.want_primal = 0;
+  UOT_CUDA(launch_dual(d, c.st));
+  const double tau1 = p.rho1 / (p.rho1 + p.rho2), tau2 = p.rho2 / (p.rho1 + p.rho2);
+  for (int side = 0; side < 2; ++side) {
+    v = sweep(c, side, side == 0 ? gfin : ffin, nullptr, true, side == 0 ? &sr : &sc);
+    if (v != UOT_OK) return v;
+    UOT_CUDA(launch_mass(side == 0 ? p.b : p.a, side == 0 ? p.m : p.n, c.blk, c.state, 0, c.st));
+    GradParams gp{};
+    gp.nq = side == 0 ? p.n : p.m; gp.splits = side == 0 ? sr : sc; gp.dim = p.dim; gp.moments = p.dim;
+    gp.s = c.s; gp.eps = p.eps; gp.rho_o = side == 0 ? p.rho1 : p.rho2; gp.p = p.p;
+    gp.pot_o = side == 0 ? ffin : gfin; gp.part = side == 0 ? c.part_r : c.part_c;
+    gp.grad_w = side == 0 ? ga : gb; gp.grad_pts = side == 0 ? gx : gy; gp.lnw_o = side == 0 ? c.ln_a : c.ln_b;
+    gp.perm = nullptr; gp.state = c.state;
+    UOT_CUDA(launch_grad_epilogue(gp, c.st));
+    UOT_CUDA(launch_final_side(side == 0 ? c.part_r : c.part_c, 2 + p.dim, gp.nq, gp.splits, c.s, p.eps, gp.rho_o,
+                               gp.pot_o, gp.lnw_o, side == 0 ? fbb : gbb, c.blk, ctr, sums + side, c.st));
+  }
+  // lambda = tau1 B(gb_T) - tau2 A(fb_T):  Abar_T = -tau2 lambda_bar,  Bbar_T = tau1 lambda_bar
+  UOT_CUDA(launch_final_lambda(p.n, fbT, c.ln_a, &c.state->slot[sT].A, p.rho1, -tau2, sums, sums + 1, fbb, ga, c.blk,
+                               ctr, sums + 2, c.st));
+  UOT_CUDA(launch_final_lambda(p.m, gbT, c.ln_b, &c.state->slot[sT].B, p.rho2, tau1, sums, sums + 1, gbb, gb, c.blk,
+                               ctr, nullptr, c.st));
+  // reverse sweep over segments, recomputing each from its checkpoint
+  const double eps = p.eps, r1 = p.rho1, r2 = p.rho2;
+  const double a1 = r1 / (r1 + eps), b1 = eps / (eps + r1) * r1 / (r1 + r2);
+  const double a2 = r2 / (r2 + eps), b2 = eps / (eps + r2) * r2 / (r1 + r2);
+  const double kf0 = eps / (eps + r1) * r2 / (r1 + r2), kg0 = eps / (eps + r2) * r1 / (r1 + r2);
+  const double kf = kf0 / (1.0 - kf0), kg = kg0 / (1.0 - kg0);
+  for (int sgi = L.nck - 1; sgi >= 0; --sgi) {
+    const int t0 = sgi * K, t1 = std::min(T, t0 + K);
+    UOT_CUDA(cudaMemcpyAsync(fst, ck_f + N * sgi, sizeof(float) * N, cudaMemcpyDeviceToDevice, c.st));
+    UOT_CUDA(cudaMemcpyAsync(c.state->slot, ck_slot + 2 * sgi, sizeof(Slot) * 2, cudaMemcpyDeviceToDevice, c.st));
+    for (int t = t0; t < t1; ++t) {
+      v = ur_iteration(c, L, b, t, fst, gbuf, true, t - t0);
+      if (v != UOT_OK) return v;
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      const int j = t - t0;
+      const float* fbar = reinterpret_cast<float*>(b + L.fbar) + N * j;
+      const float* gbarn = reinterpret_cast<float*>(b + L.gbarn) + M * j;
+      const float* Sp = reinterpret_cast<float*>(b + L.Sp) + M * j;
+      const float* Gp = reinterpret_cast<float*>(b + L.Gp) + M * D * j;
+      const float* ghat = reinterpret_cast<float*>(b + L.ghat) + M * j;
+      const float* S = reinterpret_cast<float*>(b + L.S) + N * j;
+      const float* G = reinterpret_cast<float*>(b + L.G) + N * D * j;
+      const float* fhat = reinterpret_cast<float*>(b + L.fhat) + N * j;
+      const double* rec = reinterpret_cast<double*>(b + L.rec) + 8 * j;
+      // f half-step of iteration t+1
+      UOT_CUDA(launch_bw_f1(p.n, p.dim, fbb, fhat, c.ln_a, rec + 3, sums + 2, kf, r1, a1, G, ga, gx, Sb, c.blk, ctr,
+                            sums + 3, c.st));
+      UOT_CUDA(launch_bw_smin_init(p.m, gbarn, c.ln_b, rec + 2, r2, -b1, sums + 3, gbb, gb, c.st));
+      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, c.st));
+      UOT_CUDA(launch_bw_adj(p.m, p.dim, val, mom, c.ln_b, eps, gbb, gb, gy, c.blk, ctr, sums + 4, c.st));
+      // g half-step of iteration t+1
+      UOT_CUDA(launch_bw_g1(p.m, p.dim, gbb, ghat, c.ln_b, rec + 1, sums + 4, kg, r2, a2, Gp, gb, gy, Spb, c.blk, ctr,
+                            sums + 5, c.st));
+      UOT_CUDA(launch_bw_fset(p.n, fbar, c.ln_a, rec + 0, r1, -b2, sums + 5, fbb, ga, c.st));
+      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, c.st));
+      UOT_CUDA(launch_bw_adj(p.n, p.dim, val, mom, c.ln_a, eps, fbb, ga, gx, c.blk, ctr, sums + 2, c.st));
+    }
+  }
+  if (grad_a) UOT_CUDA(cudaMemcpyAsync(grad_a, ga, sizeof(float) * N, cudaMemcpyDeviceToDevice, c.st));
+  if (grad_b) UOT_CUDA(cudaMemcpyAsync(grad_b, gb, sizeof(float) * M, cudaMemcpyDeviceToDevice, c.st));
+  if (grad_x) UOT_CUDA(cudaMemcpyAsync(grad_x, gx, sizeof(float) * N * D, cudaMemcpyDeviceToDevice, c.st));
+  if (grad_y) UOT_CUDA(cudaMemcpyAsync(grad_y, gy, sizeof(float) * M * D, cudaMemcpyDeviceToDevice, c.st));
+  int status = 0;
+  UOT_CUDA(cudaMemcpyAsync(&status, &c.state->status, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  UOT_CUDA(cudaStreamSynchronize(c.st));
+  if (status != 0) return fail(UOT_ERR_NONFINITE, "non-finite value met in the unrolled pass");
+  return UOT_OK;
+}
+
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -541,6 +793,18 @@ uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, flo
     UOT_CUDA(launch_grad_epilogue(gp, c.st));
   }
   return UOT_OK;
+}
+
+size_t uot_unrolled_workspace_size(const uot_problem* prob, int32_t T, int32_t ckpt_every) {
+  if (ur_check(prob, T, ckpt_every) != UOT_OK) return 0;
+  uot_problem pd = *prob;
+  pd.ordering = 2;
+  return ur_layout(pd, T, ckpt_every).total;
+}
+
+uot_status uot_grad_unrolled(const uot_problem* prob, int32_t T, int32_t ckpt_every, double* value, float* grad_a,
+                             float* grad_b, float* grad_x, float* grad_y, void* ws, size_t ws_bytes, void* stream) {
+  return grad_unrolled(prob, T, ckpt_every, value, grad_a, grad_b, grad_x, grad_y, ws, ws_bytes, stream);
 }
 
 uint64_t uot_kernel_launches(void) { return g_launches.load(); }

@@ -192,6 +192,34 @@ struct GradParams {
 };
 cudaError_t launch_grad_epilogue(const GradParams& gp, cudaStream_t st);
 
+// ---- unrolled backward (adjoint.cu, unrolled.cu) -----------------------------
+SweepGeom adjoint_geom(int nq, int nk);
+cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int dim, const float* pot_q,
+                           const float* h_k, const float* c_k, double s, float* part, double* val, double* mom,
+                           cudaStream_t st);
+cudaError_t launch_add_scalar(const float* u, const double* c, int n, float* v, cudaStream_t st);
+cudaError_t launch_moments(const float* part, int nq, int dim, int splits, double scale, float* G, cudaStream_t st);
+cudaError_t launch_final_side(const float* part, int CH, int nq, int splits, double s, double eps, double rho,
+                              const float* pot, const double* lnw, float* cot, double* blk, unsigned int* ctr,
+                              double* sum, cudaStream_t st);
+cudaError_t launch_final_lambda(int n, const float* u, const double* lnw, const double* X, double rho, double coef,
+                                const double* sum_f, const double* sum_g, float* cot, float* gw, double* blk,
+                                unsigned int* ctr, double* sum, cudaStream_t st);
+cudaError_t launch_bw_f1(int n, int dim, const float* fbb, const float* fhat, const double* lna, const double* Ahat,
+                         const double* sum_fbb, double kf, double rho1, double a1, const float* G, float* ga,
+                         float* gx, float* Sb, double* blk, unsigned int* ctr, double* sum_out, cudaStream_t st);
+cudaError_t launch_bw_smin_init(int n, const float* u, const double* lnw, const double* X, double rho, double coef,
+                                const double* sum_in, float* cot, float* gw, cudaStream_t st);
+cudaError_t launch_bw_adj(int n, int dim, const double* val, const double* mom, const double* lnw, double eps,
+                          float* cot, float* gw, float* gpts, double* blk, unsigned int* ctr, double* sum,
+                          cudaStream_t st);
+cudaError_t launch_bw_g1(int m, int dim, float* gbb, const float* ghat, const double* lnb, const double* Bhat,
+                         const double* sum_gbb, double kg, double rho2, double a2, const float* Gp, float* gb,
+                         float* gy, float* Spb, double* blk, unsigned int* ctr, double* sum_out, cudaStream_t st);
+cudaError_t launch_bw_fset(int n, const float* fb, const double* lna, const double* A, double rho1, double coef,
+                           const double* sum_in, float* fbb, float* ga, cudaStream_t st);
+cudaError_t launch_record_scalars(const DevState* s, int slot_t, int slot_t1, double* rec, cudaStream_t st);
+
 // Sum of weights in FP64 into state->dual[slot_idx].
 cudaError_t launch_mass(const float* w, int n, double* blk, DevState* st_dev, int idx, cudaStream_t st);
 

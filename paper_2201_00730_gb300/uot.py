@@ -82,6 +82,10 @@ def lib() -> C.CDLL:
         L.uot_dual_value.restype = C.c_int
         L.uot_grad.argtypes = [P, V, V, V, V, V, V, V, S, V]
         L.uot_grad.restype = C.c_int
+        L.uot_unrolled_workspace_size.argtypes = [P, C.c_int32, C.c_int32]
+        L.uot_unrolled_workspace_size.restype = S
+        L.uot_grad_unrolled.argtypes = [P, C.c_int32, C.c_int32, V, V, V, V, V, V, S, V]
+        L.uot_grad_unrolled.restype = C.c_int
         L.uot_batch_workspace_size.argtypes = [C.POINTER(Batch)]
         L.uot_batch_workspace_size.restype = S
         L.uot_sinkhorn_batched.argtypes = [C.POINTER(Batch), C.POINTER(Options), C.c_int32, V, V,
@@ -281,6 +285,24 @@ def grad(spec: Spec, f: torch.Tensor, g: torch.Tensor, wrt=("a", "b", "x", "y"),
     _check(lib().uot_grad(C.byref(pr), _ptr(f), _ptr(g), _ptr(out.get("a")), _ptr(out.get("b")),
                           _ptr(out.get("x")), _ptr(out.get("y")), _ptr(ws), ws.numel(), _stream()))
     return out
+
+
+def grad_unrolled(spec: Spec, T: int = 200, ckpt_every: int = 20):
+    """Value F_eps(f_T, g_T) after T TI iterations from zero and its exact (unrolled) gradient
+    with respect to a, b, x, y.  Returns (value (FP64 tensor [1]), dict of gradients)."""
+    pr = spec.struct()
+    nbytes = lib().uot_unrolled_workspace_size(C.byref(pr), int(T), int(ckpt_every))
+    if nbytes == 0:
+        raise UOTError(1, lib().uot_last_error().decode())
+    dev = spec.a.device
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    val = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {"a": torch.empty(spec.n, dtype=torch.float32, device=dev),
+           "b": torch.empty(spec.m, dtype=torch.float32, device=dev),
+           "x": torch.empty_like(spec.x), "y": torch.empty_like(spec.y)}
+    _check(lib().uot_grad_unrolled(C.byref(pr), int(T), int(ckpt_every), _ptr(val), _ptr(out["a"]),
+                                   _ptr(out["b"]), _ptr(out["x"]), _ptr(out["y"]), _ptr(ws), ws.numel(), _stream()))
+    return val, out
 
 
 class UOTLoss(torch.autograd.Function):
