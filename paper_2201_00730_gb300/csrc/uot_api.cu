@@ -96,6 +96,10 @@ PartSizes part_sizes(const uot_problem& p) {
       upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
       upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
     }
+    if (mma_path(p)) {
+      upd(ps.rows, (size_t)mma_geom(p.n, p.m).splits * 2 * p.n);
+      upd(ps.cols, (size_t)mma_geom(p.m, p.n).splits * 2 * p.m);
+    }
   } else {
     SweepGeom gr = dense_row_geom(p.n, p.m);
     SweepGeom gc = dense_col_geom(p.n, p.m);
@@ -106,7 +110,7 @@ PartSizes part_sizes(const uot_problem& p) {
 }
 
 struct WsLayout {
-  size_t state, ln_a, ln_b, l2_a, l2_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc;
+  size_t state, ln_a, ln_b, l2_a, l2_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc, center;
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
   size_t sort_tmp_bytes, total;
@@ -129,6 +133,7 @@ WsLayout ws_layout(const uot_problem& p) {
   L.part_c = take(sizeof(float) * ps.cols);
   L.blk = take(sizeof(double) * kMaxBlocks * 10);
   L.rbc = take(sizeof(unsigned int) * kMaxBlocks);
+  L.center = take(sizeof(float) * 64);
   if (tiled_path(p)) {
     const int nmax = p.n > p.m ? p.n : p.m;
     L.perm_x = take(sizeof(int) * p.n);
@@ -159,6 +164,7 @@ struct Ctx {
   double *ln_a, *ln_b, *blk;
   float *l2_a, *l2_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;
   unsigned int* rbc;  // per-row-block counters of the fused sweeps
+  float* center;      // common centre of the clouds (tensor-core path)
   cudaStream_t st;
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
@@ -201,6 +207,7 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->part_c = reinterpret_cast<float*>(b + L.part_c);
   c->blk = reinterpret_cast<double*>(b + L.blk);
   c->rbc = reinterpret_cast<unsigned int*>(b + L.rbc);
+  c->center = reinterpret_cast<float*>(b + L.center);
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
@@ -241,6 +248,7 @@ uot_status prepare(Ctx& c) {
     UOT_CUDA(launch_order_points(c.p.x, c.p.a, c.p.n, c.p.dim, c.osc, c.perm_x, c.xs, c.as, c.cen_x, c.st));
     UOT_CUDA(launch_order_points(c.p.y, c.p.b, c.p.m, c.p.dim, c.osc, c.perm_y, c.ys, c.bs, c.cen_y, c.st));
   }
+  if (mma_path(c.p)) UOT_CUDA(launch_center(c.p.x, c.p.n, c.p.y, c.p.m, c.p.dim, c.center, c.st));
   UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, &c.state->status, c.st));
   UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, &c.state->status, c.st));
   return UOT_OK;
@@ -309,6 +317,10 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       }
       UOT_CUDA(launch_tile_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, shift, c.s, part, g, epi,
                                  c.st));
+    } else if (mma_path(p) && !moments) {
+      SweepGeom g = mma_geom(q.n, k.n);
+      *splits = g.splits;
+      UOT_CUDA(launch_mma_sweep(q, k, p.dim, c.center, pot, shift, c.s, part, g, c.st));
     } else {
       SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
       *splits = g.splits;

@@ -61,6 +61,13 @@ int max_splits_for(const uot_problem& p);
 constexpr int kMaxBlocks = 4096;
 constexpr int kTileKeys = 128;  // keys per local-frame tile of the tiled sweep
 
+// True when the tensor-core sweep (3xTF32 cross term) serves this problem.
+inline bool mma_path(const uot_problem& p) {
+  return p.cost_kind == UOT_COST_POINTS && p.dim >= 32 && p.p == 2.0f;
+}
+SweepGeom mma_geom(int nq, int nk);
+cudaError_t launch_center(const float* x, int n, const float* y, int m, int dim, float* center, cudaStream_t st);
+
 // True when the tiled (Morton-ordered, local-frame) sweep serves this problem.
 inline bool tiled_path(const uot_problem& p) {
   return p.cost_kind == UOT_COST_POINTS && p.dim <= 3 && p.p == 2.0f;
@@ -113,6 +120,9 @@ SweepGeom tile_geom(int nq, int nk, int dim);
 cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
                               const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
                               const struct EpiParams* epi, cudaStream_t st);
+// Tensor-core sweep (dim >= 32, p = 2): centre = common centre of the clouds (dim floats).
+cudaError_t launch_mma_sweep(const SideDesc& q, const SideDesc& k, int dim, const float* center, const float* pot_k,
+                             const double* shift_k, double s, float* part, const SweepGeom& g, cudaStream_t st);
 // Dense cost: axis 0 = rows of C are queries, axis 1 = columns of C are queries.
 cudaError_t launch_dense_sweep(int axis, const float* C, int n, int m, const float* l2w_k,
                                const float* pot_k, const double* shift_k, double s, float* part,

@@ -1,0 +1,73 @@
+"""Tensor-core sweep (dim >= 32: 3xTF32 cross term) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import uot as O
+from paper_2201_00730_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def U():
+    from paper_2201_00730_gb300 import build, uot
+    build.build()
+    return uot
+
+
+def gauss_problem(n, m, d, seed, eps, rho, ma=1.0, mb=2.0, shift=0.0):
+    rx, ry = np.random.default_rng(seed), np.random.default_rng(seed + 1)
+    sd = np.sqrt(1.0 / (2 * d))
+    p = W.random_problem(n, m, d, seed=seed, eps=eps, rho1=rho, rho2=rho, mass_a=ma, mass_b=mb)
+    p.x = (sd * rx.standard_normal((n, d)) + shift).astype(np.float32)
+    p.y = (sd * ry.standard_normal((m, d)) + shift).astype(np.float32)
+    return p
+
+
+def spec_of(U, p):
+    dev = torch.device("cuda:0")
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y))
+
+
+def assert_close(got, ref, eps, what):
+    ref = torch.as_tensor(ref, dtype=torch.float64)
+    err = (got.double().cpu() - ref).abs()
+    tol = 1e-4 * eps + 2 * 2.0 ** -23 * ref.abs()
+    assert bool((err <= tol).all()), (what, err.max().item(), 1e-4 * eps)
+
+
+@pytest.mark.parametrize("n,m,d,eps,shift", [
+    (300, 517, 32, 0.05, 0.0), (1000, 700, 64, 0.05, 0.0), (129, 257, 48, 0.1, 0.0), (400, 300, 40, 0.05, 3.0),
+])
+def test_softmin_mma(U, n, m, d, eps, shift):
+    p = gauss_problem(n, m, d, seed=d + n, eps=eps, rho=0.5, shift=shift)
+    spec = spec_of(U, p)
+    rng = np.random.default_rng(3)
+    g = (0.2 * rng.standard_normal(m)).astype(np.float32)
+    f = (0.2 * rng.standard_normal(n)).astype(np.float32)
+    C = O.cost_matrix(p.x, p.y)
+    assert_close(U.softmin(spec, torch.from_numpy(g).cuda(), 0), O.smin_rows(C, p.b, g, eps), eps, "rows")
+    assert_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, p.a, f, eps), eps, "cols")
+
+
+def test_d64_solve_and_grads_match_oracle(U):
+    """Config-3 shape at reduced size: N = M = 1024, D = 64, eps = 5e-2, rho = 0.5, masses 1 / 2."""
+    p = gauss_problem(1024, 1024, 64, seed=1003, eps=5e-2, rho=0.5)
+    spec = spec_of(U, p)
+    r = U.solve(spec, "ti", max_iter=5000, tol=1e-7, check_every=5)
+    assert r.converged
+    C = O.cost_matrix(p.x, p.y)
+    ref = O.ti_sinkhorn(C, p.a, p.b, p.eps, p.rho1, p.rho2, 20000, tol=1e-12, check_every=10)
+    # converged to r <= 1e-7: distance to the fixed point is bounded by r / (1 - rate)
+    assert (r.f.double().cpu() - ref.f).abs().max().item() < 2e-5
+    val = U.dual_value(spec, r.f, r.g)[0].item()
+    ref_val = O.dual_value(C, p.a, p.b, ref.f, ref.g, p.eps, p.rho1, p.rho2).item()
+    assert abs(val - ref_val) < 1e-6 * abs(ref_val)
+    gr = U.grad(spec, r.f, r.g)
+    ea, eb, ex, ey = O.envelope_grads(p.x, p.y, p.a, p.b, r.f.double().cpu(), r.g.double().cpu(),
+                                      p.eps, p.rho1, p.rho2)
+    for k, e in (("a", ea), ("b", eb), ("x", ex), ("y", ey)):
+        rel = ((gr[k].double().cpu() - e).norm() / e.norm()).item()
+        assert rel < 1e-4, (k, rel)
