@@ -90,7 +90,15 @@ typedef struct {
   double tol;                /* >= 0 fixed-point residual tolerance in cost units; 0 = run     */
                              /* exactly max_iter iterations                                      */
   int32_t warm_start;        /* nonzero: f holds the initial potential on entry                 */
-  int32_t reserved;
+  int32_t lse_reference;     /* tiled sweeps of uot_sinkhorn / uot_ti_sinkhorn (Morton-ordered   */
+                             /* clouds): each row's log-sum-exp of the previous iteration may    */
+                             /* serve as the fixed exponent reference of the next one, which     */
+                             /* removes the running max from the inner loop.  0 = automatic     */
+                             /* (once the largest change between two iterations is below 24     */
+                             /* in log2 units), 1 = never, 2 = from the second iteration on.    */
+                             /* Rows that land outside a +-60 window around their reference are */
+                             /* recomputed exactly, so every setting gives the same result       */
+                             /* within rounding; only the time differs.  Other paths ignore it. */
   float* residual_history;   /* device, nullable, >= max_iter+1 floats: entry t is the residual */
                              /* of iterate t (t = 1..iters); entry 0 is unused                   */
 } uot_options;
@@ -100,7 +108,7 @@ typedef struct {
   int32_t iters;       /* index T of the returned iterate                                   */
   int32_t converged;   /* 1 if residual <= tol                                              */
   int32_t status;      /* uot_status of the solve                                           */
-  int32_t reserved;
+  int32_t lse_misses;  /* rows recomputed after their fixed reference missed (lse_reference) */
   double residual;     /* fixed-point residual of the returned (f, g), see below            */
   double lambda;       /* TI: lambda*(fb_T, gb_T) of Prop. 2; plain: 0                      */
 } uot_result;

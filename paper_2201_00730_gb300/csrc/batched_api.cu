@@ -168,8 +168,8 @@ uot_status uot_sinkhorn_batched(const uot_batch* b, const uot_options* opt, int3
   BCUDA(cudaMemsetAsync(g, 0, sizeof(float) * L.nb, st));
   BCUDA(cudaMemsetAsync(d_g1, 0, sizeof(float) * L.nb, st));
   int* d_flags = reinterpret_cast<int*>(d_ctr + 4);
-  BCUDA(launch_log_weights(b->a, (int)L.na, d_lna, d_l2a, d_flags, st));
-  BCUDA(launch_log_weights(b->b, (int)L.nb, d_lnb, d_l2b, d_flags, st));
+  BCUDA(launch_log_weights(b->a, (int)L.na, d_lna, d_l2a, nullptr, d_flags, st));
+  BCUDA(launch_log_weights(b->b, (int)L.nb, d_lnb, d_l2b, nullptr, d_flags, st));
   BCUDA(launch_batch_init(d_probs, d_st, b->a, count, ti ? 1 : 0, d_ctr + 2, st));
 
   BHalf h{};
@@ -247,7 +247,7 @@ uot_status uot_sinkhorn_batched(const uot_batch* b, const uot_options* opt, int3
     r.iters = s.conv_iter;
     r.converged = s.status == 1;
     r.status = s.status == 1 ? UOT_OK : (s.status == 3 ? UOT_NOT_CONVERGED : UOT_ERR_NONFINITE);
-    r.reserved = 0;
+    r.lse_misses = 0;
     r.residual = s.resid;
     r.lambda = ti ? s.slot[s.conv_iter & 1].lam : 0.0;
     if (s.status != 1) all_conv = false;

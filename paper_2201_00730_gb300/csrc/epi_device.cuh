@@ -6,14 +6,25 @@
 //   softmin : out_i = S_i
 //   plain   : out_i = rho_o/(rho_o+eps) S_i                          (aprox for rho KL, Sec. 3)
 //   TI      : out_i = rho_o/(rho_o+eps) S_i - eps/(eps+rho_o) rho_o/(rho_o+rho_i) X_in
-//             with FP64 accumulation of log sum_i w_i e^{-out_i/rho_o}   (proof of Prop. 4, App. B)
-// and the residual against the previous vector.  Grid-level results are
-// reduced by the last block to arrive (no block ever waits on another).
+//             with the mass sum_i w_i e^{-out_i/rho_o}                      (proof of Prop. 4, App. B)
+// and the residual against the previous vector.  The per-row arithmetic runs
+// on float pairs (ffloat.cuh: FP64 is slow here), the mass terms through a
+// table-driven exp2, summed per block against an integer power-of-two
+// reference; blocks combine in FP64.  Grid-level results are reduced by the
+// last block to arrive (no block ever waits on another).
+//
+// With e.lse_buf the raw log-sum-exp of every row (log2 units, before the key
+// shift) is kept between launches of the same side, and the largest change
+// since the previous launch decides whether the next launch of that side may
+// take the stored value as its fixed exponent reference (see the tiled sweep).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <climits>
+
+#include "ffloat.cuh"
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -25,121 +36,169 @@ __device__ __forceinline__ float ex2f(float x) {
   return y;
 }
 
-// log2 sum_k 2^(pm_k) ps_k over the key chunks of query i (FP32, max taken out),
-// in one pass over groups of 8 chunks whose 16 loads are all issued up front.
-__device__ __forceinline__ double merge_lse2(const float* part, int CH, int nq, int splits, int i) {
-  float M = kInitMax, S = 0.f;
+// Merge of the key-chunk partials of R query rows at once (all loads of a group
+// of 8 chunks issued before any use): per row the pair (M, log2 S) with
+// log-sum-exp = M + log2 S in log2 units.
+template <int R>
+__device__ __forceinline__ void merge_rows(const float* part, int CH, int nq, int splits, const int (&idx)[R],
+                                           float (&Mo)[R], float (&Lo)[R]) {
   const size_t stride = (size_t)CH * nq;
-  for (int k0 = 0; k0 < splits; k0 += 8) {
-    float mv[8], sv[8];
+  float M[R], S[R];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int k = k0 + u;
-      if (k < splits) {
-        const float* b = part + (size_t)k * stride;
-        mv[u] = __ldcg(b + i);
-        sv[u] = __ldcg(b + (size_t)nq + i);
-      } else {
-        mv[u] = kInitMax;
-        sv[u] = 0.f;
+  for (int r = 0; r < R; ++r) { M[r] = kInitMax; S[r] = 0.f; }
+  for (int k0 = 0; k0 < splits; k0 += 8) {
+    float mv[R][8], sv[R][8];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
+        if (k < splits && idx[r] >= 0) {
+          const float* b = part + (size_t)k * stride;
+          mv[r][u] = __ldcg(b + idx[r]);
+          sv[r][u] = __ldcg(b + (size_t)nq + idx[r]);
+        } else {
+          mv[r][u] = kInitMax;
+          sv[r][u] = 0.f;
+        }
       }
     }
-    float cm = M;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cm = fmaxf(cm, mv[u]);
-    float acc = S * ex2f(M - cm);
+    for (int r = 0; r < R; ++r) {
+      float cm = M[r];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc = fmaf(sv[u], ex2f(mv[u] - cm), acc);
-    S = acc;
-    M = cm;
+      for (int u = 0; u < 8; ++u) cm = fmaxf(cm, mv[r][u]);
+      float a = S[r] * ex2f(M[r] - cm);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a = fmaf(sv[r][u], ex2f(mv[r][u] - cm), a);
+      S[r] = a;
+      M[r] = cm;
+    }
   }
-  return (double)M + (double)log2f(S);
+#pragma unroll
+  for (int r = 0; r < R; ++r) { Mo[r] = M[r]; Lo[r] = log2f(S[r]); }
 }
 
-struct Acc {
-  double m, s;  // log-sum-exp pair: sum = s * e^m (m = -inf: empty)
-  double r;     // residual max
-  double bad;   // non-finite flag
-};
-
-__device__ __forceinline__ Acc acc_empty() { return Acc{-INFINITY, 0.0, 0.0, 0.0}; }
-
-__device__ __forceinline__ void lse_add(double& m, double& s, double m2, double s2) {
-  if (m2 == -INFINITY) return;
-  if (m == -INFINITY) { m = m2; s = s2; return; }
-  if (m2 > m) { s = s * exp(m - m2) + s2; m = m2; }
-  else { s += s2 * exp(m2 - m); }
-}
-
+// Per-launch constants of the half-step as float pairs, made once per block
+// (thread 0, FP64) and read from shared memory by the rows.
 struct Consts {
-  double Xin, cS, cX, base_old, cR, inv_s, inv_rho, key_shift;
+  ffl::ff U;    // 1/s = eps ln 2 (log2 units -> cost units)
+  ffl::ff KS;   // constant shift of the key potential left out by the sweep
+  ffl::ff CS;   // aprox factor rho_o/(rho_o+eps)
+  ffl::ff CXX;  // TI: eps/(eps+rho_o) rho_o/(rho_o+rho_i) * key-side Smin scalar
+  ffl::ff K1;   // TI residual: stored hat + shift - (the part of the next step fixed by the other side)
+  ffl::ff RL;   // log2(e)/rho_o (mass exponent)
+  int lse_ready;
 };
 
-__device__ __forceinline__ Consts consts(const EpiParams& e) {
+__device__ inline Consts make_consts(const EpiParams& e) {
   const Slot& si = e.state->slot[e.slot_in];
+  const double Xin = e.out_is_f ? si.B : si.A;                      // key-side Smin^rho scalar
+  const double cS = e.rho_o / (e.rho_o + e.eps);                    // aprox factor
+  const double cX = e.eps / (e.eps + e.rho_o) * e.rho_o / (e.rho_o + e.rho_i);
+  const double base_old = e.out_is_f ? si.cf : si.cg;               // stored hat + shift = bar
+  const double cR = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i) * (e.out_is_f ? si.A : si.B);
   Consts c;
-  c.Xin = e.out_is_f ? si.B : si.A;                                   // key-side Smin^rho scalar
-  c.cS = e.rho_o / (e.rho_o + e.eps);                                 // aprox factor
-  c.cX = e.eps / (e.eps + e.rho_o) * e.rho_o / (e.rho_o + e.rho_i);
-  c.base_old = e.out_is_f ? si.cf : si.cg;                            // stored hat + shift = bar
-  c.cR = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i) * (e.out_is_f ? si.A : si.B);
-  c.inv_s = 1.0 / e.s;
-  c.inv_rho = 1.0 / e.rho_o;
-  c.key_shift = e.key_shift ? *e.key_shift : 0.0;
+  c.U = ffl::from_double(1.0 / e.s);
+  c.KS = ffl::from_double(e.key_shift ? *e.key_shift : 0.0);
+  c.CS = ffl::from_double(cS);
+  c.CXX = ffl::from_double(cX * Xin);
+  c.K1 = ffl::from_double(base_old - cR);
+  c.RL = ffl::from_double(kLog2e / e.rho_o);
+  c.lse_ready = e.lse_buf ? e.state->lse_ready[e.out_is_f] : 0;
   return c;
 }
 
-// Half-step of one query row.
-__device__ __forceinline__ void row(const EpiParams& e, const Consts& c, int i, Acc& acc) {
-  const double lse2 = merge_lse2(e.part, 2 + e.moments, e.nq, e.splits, i);
-  if (lse2 < 0.25 * (double)kZeroW) acc.bad = 1.0;  // every key had zero weight
+// Block-wide constants: thread 0 computes, everyone reads (one barrier).
+__device__ __forceinline__ const Consts& block_consts(const EpiParams& e) {
+  __shared__ Consts sc;
+  if (threadIdx.x == 0) sc = make_consts(e);
+  __syncthreads();
+  return sc;
+}
+
+// Row inputs read ahead of the merge.
+struct Pre {
+  float lwh, lwl;  // log2 w of the output side as a float pair (TI mass term)
+  float old;       // previous output (residual)
+  float prev;      // previous log-sum-exp of the row (fixed-reference bookkeeping)
+};
+
+__device__ __forceinline__ Pre prefetch(const EpiParams& e, int i) {
+  Pre p;
+  const bool ti = e.mode == EPI_TI && i >= 0;
+  p.lwh = ti ? e.l2w_o[i] : 0.f;
+  p.lwl = ti ? e.l2lo_o[i] : 0.f;
+  p.old = (e.old_out && i >= 0) ? e.old_out[i] : 0.f;
+  p.prev = (e.lse_buf && i >= 0) ? e.lse_buf[i] : 0.f;
+  return p;
+}
+
+// Thread-level accumulator of the rows: TI mass sum_i 2^(y_i) kept as
+// 2^ref * (sum.hi + sum.lo) with an integer ref (rescaling is exact).
+struct RowAcc {
+  int ref;       // INT_MIN: no term yet
+  ffl::ff sum;
+  float r;       // residual max
+  float gap;     // max |lse - previous lse|
+  int bad;
+};
+
+__device__ __forceinline__ RowAcc rowacc_empty() { return RowAcc{INT_MIN, ffl::ff{0.f, 0.f}, 0.f, 0.f, 0}; }
+
+// a * 2^-k for k >= 0; below 2^-100 of the reference a term no longer matters
+// (every sum holds a term of at least half its reference).
+__device__ __forceinline__ ffl::ff scale2(ffl::ff a, int k) {
+  if (k > 100) return ffl::ff{0.f, 0.f};
+  const float sc = ffl::pow2f(-k);
+  return ffl::ff{a.hi * sc, a.lo * sc};
+}
+
+// Half-step of one query row from its merged log-sum-exp M + L (log2 units).
+__device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int i, float M, float L, const Pre& p,
+                                       RowAcc& a) {
+  using namespace ffl;
+  const ff lse = two_sum(M, L);
+  if (!(lse.hi > 0.25f * kZeroW)) a.bad = 1;  // every key had zero weight (or NaN)
+  if (e.lse_buf) {
+    const float d = fabsf(lse.hi - p.prev);
+    if (!c.lse_ready || !(d <= 1e30f) || !(lse.hi > 0.25f * kZeroW)) a.gap = INFINITY;
+    else a.gap = fmaxf(a.gap, d);
+    e.lse_buf[i] = lse.hi;
+  }
   // Smin in cost units; a shift tau of the key potential moves it by -tau exactly
-  const double S = -lse2 * c.inv_s - c.key_shift;
-  double v;
-  if (e.mode == EPI_SOFTMIN) {
-    v = S;
-  } else if (e.mode == EPI_PLAIN) {
-    v = c.cS * S;
-    if (e.old_out) acc.r = fmax(acc.r, fabs((double)e.old_out[i] - v));
-  } else {
-    v = c.cS * S - c.cX * c.Xin;
-    const double lw = e.lnw_o[i];
-    if (lw != -INFINITY) lse_add(acc.m, acc.s, lw - v * c.inv_rho, 1.0);
-    if (e.old_out) acc.r = fmax(acc.r, fabs((double)e.old_out[i] + c.base_old - v - c.cR));
+  const ff S = neg(add(mul(lse, c.U), c.KS));
+  ff v = S;
+  if (e.mode != EPI_SOFTMIN) v = mul(S, c.CS);
+  if (e.mode == EPI_TI) v = add(v, neg(c.CXX));
+  const float vo = v.hi + v.lo;
+  if (!isfinite(vo)) a.bad = 1;
+  e.out[e.perm_out ? e.perm_out[i] : i] = vo;
+  if (e.old_out) {
+    const ff d = (e.mode == EPI_TI) ? add(add(c.K1, p.old), neg(v)) : add(neg(v), p.old);
+    a.r = fmaxf(a.r, fabsf(d.hi + d.lo));
   }
-  if (!isfinite(v)) acc.bad = 1.0;
-  e.out[e.perm_out ? e.perm_out[i] : i] = (float)v;
-}
-
-__device__ __forceinline__ double shfl_d(double v, int off) {
-  return __shfl_xor_sync(0xffffffffu, v, off);
-}
-
-// Block reduction: max of m first, one exp per thread, then sums (no exp per tree level).
-__device__ inline Acc block_reduce(Acc v) {
-  __shared__ double sm[32], ss[32], sr[32], sb[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  double M = v.m;
-  for (int off = 16; off > 0; off >>= 1) M = fmax(M, shfl_d(M, off));
-  double s = (v.m == -INFINITY) ? 0.0 : v.s * exp(v.m - M);
-  double r = v.r, b = v.bad;
-  for (int off = 16; off > 0; off >>= 1) {
-    s += shfl_d(s, off);
-    r = fmax(r, shfl_d(r, off));
-    b = fmax(b, shfl_d(b, off));
-  }
-  if (lane == 0) { sm[warp] = M; ss[warp] = s; sr[warp] = r; sb[warp] = b; }
-  __syncthreads();
-  Acc out = acc_empty();
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < nw; ++w) {
-      lse_add(out.m, out.s, sm[w], ss[w]);
-      out.r = fmax(out.r, sr[w]);
-      out.bad = fmax(out.bad, sb[w]);
+  if (e.mode == EPI_TI && p.lwh > 0.5f * kZeroW) {
+    // mass term w_i e^{-v/rho_o} = 2^y, y = log2 w_i - v log2(e)/rho_o
+    const ff y = add(ff{p.lwh, p.lwl}, neg(mul(v, c.RL)));
+    if (!(fabsf(y.hi) < 1e9f)) {
+      a.bad = 1;
+      return;
     }
+    const int yr = (int)ceilf(y.hi);
+    if (a.ref == INT_MIN) a.ref = yr;
+    else if (yr > a.ref) { a.sum = scale2(a.sum, yr - a.ref); a.ref = yr; }
+    a.sum = add(a.sum, exp2(add(y, (float)(-a.ref))));
   }
-  __syncthreads();
-  return out;  // valid in thread 0
+}
+
+// The old per-row interface (merge + half-step), used by the combine kernel.
+__device__ __forceinline__ void row(const EpiParams& e, const Consts& c, int i, RowAcc& a) {
+  const Pre p = prefetch(e, i);
+  int idx[1] = {i};
+  float M[1], L[1];
+  merge_rows<1>(e.part, 2 + e.moments, e.nq, e.splits, idx, M, L);
+  row_ff(e, c, i, M[0], L[0], p, a);
 }
 
 __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
@@ -152,54 +211,118 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int 
   return last;
 }
 
+// Partial of one block (and of the grid, once reduced): the TI mass as
+// 2^ref * (hi + lo), residual and lse-change maxima, non-finite flag.
+struct Part {
+  int ref, bad;
+  float hi, lo, r, gap;
+};
+
+__device__ __forceinline__ Part part_merge(Part a, const Part& b) {
+  if (b.ref != INT_MIN) {
+    if (a.ref == INT_MIN) { a.ref = b.ref; a.hi = b.hi; a.lo = b.lo; }
+    else if (b.ref > a.ref) {
+      const ffl::ff s = ffl::add(scale2(ffl::ff{a.hi, a.lo}, b.ref - a.ref), ffl::ff{b.hi, b.lo});
+      a.ref = b.ref; a.hi = s.hi; a.lo = s.lo;
+    } else {
+      const ffl::ff s = ffl::add(ffl::ff{a.hi, a.lo}, scale2(ffl::ff{b.hi, b.lo}, a.ref - b.ref));
+      a.hi = s.hi; a.lo = s.lo;
+    }
+  }
+  a.bad = max(a.bad, b.bad);
+  a.r = fmaxf(a.r, b.r);
+  a.gap = fmaxf(a.gap, b.gap);
+  return a;
+}
+
+__device__ __forceinline__ Part part_shfl(const Part& p, int off) {
+  Part o;
+  o.ref = __shfl_xor_sync(0xffffffffu, p.ref, off);
+  o.bad = __shfl_xor_sync(0xffffffffu, p.bad, off);
+  o.hi = __shfl_xor_sync(0xffffffffu, p.hi, off);
+  o.lo = __shfl_xor_sync(0xffffffffu, p.lo, off);
+  o.r = __shfl_xor_sync(0xffffffffu, p.r, off);
+  o.gap = __shfl_xor_sync(0xffffffffu, p.gap, off);
+  return o;
+}
+
+__device__ __forceinline__ Part warp_reduce(Part p) {
+  for (int off = 16; off > 0; off >>= 1) p = part_merge(p, part_shfl(p, off));
+  return p;
+}
+
 // Thread 0 of the last block: scalars of the half-step, residual, status.
-__device__ inline void finalize(const EpiParams& e, const Acc& t) {
+__device__ inline void finalize(const EpiParams& e, const Part& t) {
   DevState* st = e.state;
   int status = st->status;
-  if (t.bad != 0.0 || isnan(t.r)) status |= kStatusNonfinite;
+  if (t.bad != 0 || isnan(t.r)) status |= kStatusNonfinite;
   if (e.mode == EPI_TI) {
-    const double lse = t.m + log(t.s);               // log <w, e^{-hat/rho_o}>
+    // log <w, e^{-hat/rho_o}> (empty sum: -inf)
+    const double lse = (t.ref == INT_MIN || !(t.hi > 0.f)) ? -INFINITY
+                                                          : (double)t.ref * ffl::kLn2d + ffl::log(ffl::ff{t.hi, t.lo});
     const double Xhat = -e.rho_o * lse;              // Smin_w^rho_o(hat)
-    const double k = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i);
-    const double c = k / (1.0 - k) * Xhat;           // closed-form translation
+    const double c = e.fin_kk * Xhat;                // closed-form translation k/(1-k) Xhat
     const double X = Xhat + c;                       // Smin(hat + c) = Smin(hat) + c
     if (!isfinite(X)) status |= kStatusNonfinite;
     Slot& so = st->slot[e.slot_out];
     if (e.out_is_f) {
       so.A = X; so.cf = c;
-      const double tau1 = e.rho_o / (e.rho_o + e.rho_i), tau2 = e.rho_i / (e.rho_o + e.rho_i);
-      so.lam = tau1 * so.B - tau2 * X;               // lambda* = tau1 Smin_b(gb) - tau2 Smin_a(fb)
+      so.lam = e.fin_tau1 * so.B - e.fin_tau2 * X;   // lambda* = tau1 Smin_b(gb) - tau2 Smin_a(fb)
     } else {
       so.B = X; so.cg = c;
     }
   }
   if (e.old_out) {
-    st->resid = (float)t.r;
-    if (e.resid_hist) e.resid_hist[e.hist_index] = (float)t.r;
+    st->resid = t.r;
+    if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+  }
+  if (e.lse_buf) {
+    // policy 2: always use the stored reference; 0: only after a small change
+    const int side = e.out_is_f;
+    st->lse_ok[side] = (e.lse_policy == 2) || (e.lse_policy == 0 && t.gap <= (float)kLseGate);
+    st->lse_ready[side] = 1;
   }
   st->status = status;
 }
 
 // Grid-level tail: block partial -> blk[slot]; the last of `nblocks` arrivals
-// reduces all partials and finalises.
-__device__ inline void grid_tail(const EpiParams& e, const Acc& mine, int slot, int nblocks) {
-  if (threadIdx.x == 0) {
-    double* o = e.blk + 4 * (size_t)slot;
-    o[0] = mine.m; o[1] = mine.s; o[2] = mine.r; o[3] = mine.bad;
-  }
+// reduces all partials in its first warp (exact power-of-two rescaling, no
+// exponentials) and finalises.
+__device__ inline void grid_tail(const EpiParams& e, const Part& mine, int slot, int nblocks) {
+  Part* bp = reinterpret_cast<Part*>(e.blk);
+  if (threadIdx.x == 0) bp[slot] = mine;
   if (!arrive_last(&e.state->counter, (unsigned)nblocks)) return;
-  Acc t = acc_empty();
-  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
-    const double* o = e.blk + 4 * (size_t)k;
-    lse_add(t.m, t.s, __ldcg(o), __ldcg(o + 1));
-    t.r = fmax(t.r, __ldcg(o + 2));
-    t.bad = fmax(t.bad, __ldcg(o + 3));
+  if (threadIdx.x >= 32) return;
+  Part t{INT_MIN, 0, 0.f, 0.f, 0.f, 0.f};
+  for (int k = threadIdx.x; k < nblocks; k += 32) {
+    const Part* o = bp + k;
+    Part q;
+    q.ref = __ldcg(&o->ref); q.bad = __ldcg(&o->bad); q.hi = __ldcg(&o->hi); q.lo = __ldcg(&o->lo);
+    q.r = __ldcg(&o->r); q.gap = __ldcg(&o->gap);
+    t = part_merge(t, q);
   }
-  t = block_reduce(t);
+  t = warp_reduce(t);
   if (threadIdx.x == 0) {
     finalize(e, t);
     e.state->counter = 0;
   }
+}
+
+// Block reduction of the thread accumulators, then the grid-level tail.
+__device__ inline void block_finish(const EpiParams& e, const RowAcc& a, int slot, int nblocks) {
+  __shared__ Part sp[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  Part p{a.ref, a.bad, a.sum.hi, a.sum.lo, a.r, a.gap};
+  p = warp_reduce(p);
+  if (lane == 0) sp[warp] = p;
+  __syncthreads();
+  if (warp == 0) {
+    Part q = (lane < nw) ? sp[lane] : Part{INT_MIN, 0, 0.f, 0.f, 0.f, 0.f};
+    q = warp_reduce(q);
+    if (lane == 0) sp[0] = q;
+  }
+  __syncthreads();
+  grid_tail(e, sp[0], slot, nblocks);
 }
 
 }  // namespace epi

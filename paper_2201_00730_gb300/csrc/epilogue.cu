@@ -80,11 +80,10 @@ __device__ Red4 block_reduce(Red4 v) {
 }
 
 __global__ void __launch_bounds__(kBlk) k_combine(EpiParams e) {
-  const epi::Consts c = epi::consts(e);
-  epi::Acc acc = epi::acc_empty();
+  const epi::Consts& c = epi::block_consts(e);
+  epi::RowAcc acc = epi::rowacc_empty();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nq; i += gridDim.x * blockDim.x) epi::row(e, c, i, acc);
-  const epi::Acc b = epi::block_reduce(acc);
-  epi::grid_tail(e, b, blockIdx.x, gridDim.x);
+  epi::block_finish(e, acc, blockIdx.x, gridDim.x);
 }
 
 // slot 0 <- {A = Smin_a^rho1(f0) = -rho1 log sum_i a_i e^{-f0_i/rho1}, B = cf = cg = lam = 0}
@@ -138,18 +137,22 @@ __global__ void k_finalize(int ti, const float* f_hat, const float* g_hat, float
   }
 }
 
-__global__ void k_log_weights(const float* w, int n, double* lnw, float* l2w, int* flags) {
+__global__ void k_log_weights(const float* w, int n, double* lnw, float* l2w, float* l2lo, int* flags) {
   int bad = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float v = w[i];
     if (!(v >= 0.f) || !isfinite(v)) bad = 1;
     if (v > 0.f) {
       const double l = log((double)v);
+      const double l2 = l * kLog2e;
+      const float hi = (float)l2;
       lnw[i] = l;
-      l2w[i] = (float)(l * kLog2e);
+      l2w[i] = hi;
+      if (l2lo) l2lo[i] = (float)(l2 - (double)hi);
     } else {
       lnw[i] = -INFINITY;
       l2w[i] = kZeroW;
+      if (l2lo) l2lo[i] = 0.f;
     }
   }
   if (bad && flags) atomicOr(flags, kStatusBadWeights);
@@ -294,7 +297,9 @@ int grid_for(int n) {
 
 }  // namespace
 
-cudaError_t launch_combine(const EpiParams& e, cudaStream_t st) {
+cudaError_t launch_combine(const EpiParams& e0, cudaStream_t st) {
+  EpiParams e = e0;
+  epi_finish_params(e);
   k_combine<<<grid_for(e.nq), kBlk, 0, st>>>(e);
   note_launch();
   return cudaGetLastError();
@@ -315,8 +320,16 @@ cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, int* flags, cudaStream_t st) {
-  k_log_weights<<<grid_for(n), kBlk, 0, st>>>(w, n, lnw, l2w, flags);
+void epi_finish_params(EpiParams& e) {
+  const double k = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i);
+  e.fin_kk = k / (1.0 - k);
+  e.fin_tau1 = e.rho_o / (e.rho_o + e.rho_i);
+  e.fin_tau2 = e.rho_i / (e.rho_o + e.rho_i);
+}
+
+cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, float* l2lo, int* flags,
+                               cudaStream_t st) {
+  k_log_weights<<<grid_for(n), kBlk, 0, st>>>(w, n, lnw, l2w, l2lo, flags);
   note_launch();
   return cudaGetLastError();
 }

@@ -17,6 +17,16 @@
 // FADD2 / FMUL2: one issue slot for two lanes), one MUFU ex2 per entry, and a
 // running max per group of 8 keys.  Output: per (query, key chunk) partials
 // (max, sum of 2^(t - max)), merged by the combine kernel.
+//
+// Fixed-reference mode (fused epilogue with a stored reference, decided per
+// launch on the device): inside a Sinkhorn solve a row's log-sum-exp moves
+// little between two iterations, so the previous launch's value m_i can stand
+// in for the running max.  The sum of 2^(t_ij - m_i) then needs no max and no
+// rescaling: per key pair one FADD2 (tile constant R_i - m_i), dim FFMA2, two
+// ex2 and one FADD2.  The result is exact as long as |lse_i - m_i| stays inside
+// a window far from FP32 over- and underflow; the epilogue checks every row and
+// recomputes the rows outside it from scratch (warp per row, running max), so
+// a poor reference costs time, never accuracy.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -68,6 +78,38 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
   return d;
 }
 
+// Softmin partial of one query row over all keys in the direct form, one warp
+// with a running max per lane; the lanes' pairs are combined on every lane.
+template <int D>
+__device__ void exact_row(const float* __restrict__ xq, const float* __restrict__ kp, int nk,
+                          const float* __restrict__ l2w, const float* __restrict__ pot, float sf, int lane,
+                          float& Mo, float& So) {
+  float x[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) x[d] = xq[d];
+  float Mx = kInitMax, Sx = 0.f;
+  for (int j = lane; j < nk; j += 32) {
+    float r2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) { const float dd = x[d] - kp[(size_t)j * D + d]; r2 = fmaf(dd, dd, r2); }
+    const float lw = l2w[j];
+    if (lw <= 0.5f * kZeroW) continue;
+    const float t = fmaf(-sf, r2, fmaf(sf, pot ? pot[j] : 0.f, lw));
+    const float mn = fmaxf(Mx, t);
+    Sx = Sx * ex2f(Mx - mn) + ex2f(t - mn);
+    Mx = mn;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float M2 = __shfl_xor_sync(0xffffffffu, Mx, off);
+    const float S2 = __shfl_xor_sync(0xffffffffu, Sx, off);
+    const float mn = fmaxf(Mx, M2);
+    Sx = Sx * ex2f(Mx - mn) + S2 * ex2f(M2 - mn);
+    Mx = mn;
+  }
+  Mo = Mx;
+  So = Sx;
+}
+
 // R = 2 is limited to 64 registers so that 4 CTAs (32 warps) share an SM; on
 // GB300 that hides the ex2 / FMA latency chains better than more registers.
 template <int D, int R, bool EPI>
@@ -85,8 +127,12 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
   const float sf = (float)s;
   const float s2 = (float)(2.0 * s);
 
+  bool use_ref = false;
+  if constexpr (EPI) use_ref = e.lse_buf != nullptr && e.state->lse_ok[e.out_is_f] != 0;
+
   float xq[R][3];
   float M[R], acc[R];
+  u64 ar[R];  // fixed-reference sums, M[r] holding the reference
   const int ibase = blockIdx.x * (kThreads * R) + threadIdx.x;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -94,7 +140,11 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
 #pragma unroll
     for (int d = 0; d < 3; ++d) xq[r][d] = (i < nq && d < D) ? q[(size_t)i * D + d] : 0.f;
     M[r] = kInitMax;
+    if constexpr (EPI) {
+      if (use_ref) M[r] = (i < nq) ? e.lse_buf[i] : 0.f;
+    }
     acc[r] = 0.f;
+    ar[r] = pk(0.f, 0.f);
   }
 
   for (int jt = j0; jt < j1; jt += kStageKeys) {
@@ -159,6 +209,32 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
       }
       const ulonglong2* A = sA + lt * kPairsPerTile;
       const ulonglong2* B = sB + lt * kPairsPerTile;
+      if (use_ref) {
+        // exponent t_ij - m_i = H_j + q'_i . Y_j + (R_i - m_i)
+        u64 cc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { const float c0 = Rr[r] - M[r]; cc[r] = pk(c0, c0); }
+#pragma unroll 2
+        for (int pp = 0; pp < kPairsPerTile; pp += 4) {
+          ulonglong2 a[4], b[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) { a[k] = A[pp + k]; b[k] = B[pp + k]; }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              u64 v = add2(b[k].y, cc[r]);
+              if (D > 2) v = fma2(X[r][2], b[k].x, v);
+              if (D > 1) v = fma2(X[r][1], a[k].y, v);
+              v = fma2(X[r][0], a[k].x, v);
+              float w0, w1;
+              upk(v, w0, w1);
+              ar[r] = add2(ar[r], pk(ex2f(w0), ex2f(w1)));
+            }
+          }
+        }
+        continue;
+      }
 #pragma unroll 2
       for (int pp = 0; pp < kPairsPerTile; pp += 4) {
         ulonglong2 a[4], b[4];
@@ -210,7 +286,13 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
     if (i < nq) {
       float* base = part + (size_t)split * 2 * nq;
       base[i] = M[r];
-      base[(size_t)nq + i] = acc[r];
+      if (use_ref) {
+        float a0, a1;
+        upk(ar[r], a0, a1);
+        base[(size_t)nq + i] = a0 + a1;
+      } else {
+        base[(size_t)nq + i] = acc[r];
+      }
     }
   }
   if constexpr (EPI) {
@@ -218,13 +300,68 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
     // and applies the half-step; the last row block finishes the scalars.
     if (!epi::arrive_last(&e.rb_counter[blockIdx.x], gridDim.y)) return;
     if (threadIdx.x == 0) e.rb_counter[blockIdx.x] = 0;
-    const epi::Consts c = epi::consts(e);
-    epi::Acc ea = epi::acc_empty();
-    const int r0 = blockIdx.x * (kThreads * R);
-    const int r1 = min(nq, r0 + kThreads * R);
-    for (int i = r0 + threadIdx.x; i < r1; i += kThreads) epi::row(e, c, i, ea);
-    const epi::Acc b = epi::block_reduce(ea);
-    epi::grid_tail(e, b, blockIdx.x, gridDim.x);
+    const int r1 = min(nq, blockIdx.x * (kThreads * R) + kThreads * R);
+    int idx[R];
+    epi::Pre pre[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = ibase + r * kThreads;
+      idx[r] = (i < r1) ? i : -1;
+      pre[r] = epi::prefetch(e, idx[r]);
+    }
+    float Mg[R], Lg[R];
+    epi::merge_rows<R>(part, 2, nq, gridDim.y, idx, Mg, Lg);
+    if (use_ref) {
+      // rows whose log-sum-exp left the window around the reference are listed,
+      // recomputed (one warp each) into chunk 0 of their partials, and merged again
+      __shared__ int s_nbad;
+      int* s_bad = reinterpret_cast<int*>(sA);  // kThreads * R ints fit in sA
+      static_assert(sizeof(int) * kThreads * 4 <= sizeof(ulonglong2) * kPairsPerStage, "bad-row list size");
+      if (threadIdx.x == 0) s_nbad = 0;
+      __syncthreads();
+      bool redo[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        redo[r] = false;
+        if (idx[r] >= 0 && !(fabsf((Mg[r] + Lg[r]) - M[r]) <= (float)kLseWindow)) {
+          redo[r] = true;
+          s_bad[atomicAdd(&s_nbad, 1)] = idx[r];
+        }
+      }
+      __syncthreads();
+      const int nbad = s_nbad;
+      if (nbad > 0) {
+        const int lane = threadIdx.x & 31;
+        for (int k = threadIdx.x >> 5; k < nbad; k += kThreads / 32) {
+          const int i = s_bad[k];
+          float Mx, Sx;
+          exact_row<D>(q + (size_t)i * D, kp, nk, l2w, pot, sf, lane, Mx, Sx);
+          for (int sp = lane; sp < (int)gridDim.y; sp += 32) {
+            float* base = part + (size_t)sp * 2 * nq;
+            base[i] = sp == 0 ? Mx : kInitMax;
+            base[(size_t)nq + i] = sp == 0 ? Sx : 0.f;
+          }
+        }
+        if (threadIdx.x == 0) atomicAdd(&e.state->lse_miss, (unsigned)nbad);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (redo[r]) {
+            int one[1] = {idx[r]};
+            float m1[1], l1[1];
+            epi::merge_rows<1>(part, 2, nq, gridDim.y, one, m1, l1);
+            Mg[r] = m1[0];
+            Lg[r] = l1[0];
+          }
+        }
+      }
+    }
+    const epi::Consts& c = epi::block_consts(e);
+    epi::RowAcc ea = epi::rowacc_empty();
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (idx[r] >= 0) epi::row_ff(e, c, idx[r], Mg[r], Lg[r], pre[r], ea);
+    epi::block_finish(e, ea, blockIdx.x, gridDim.x);
   }
 }
 
@@ -259,8 +396,10 @@ cudaError_t run(const SideDesc& q, const SideDesc& k, const float4* centers, con
                 double s, float* part, const SweepGeom& g, const EpiParams* epi, cudaStream_t st) {
   dim3 grid(g.row_blocks, g.splits);
   if (epi) {
+    EpiParams e = *epi;
+    epi_finish_params(e);
     k_sweep_tiles<D, R, true><<<grid, kThreads, 0, st>>>(q.pts, q.n, k.pts, k.n, centers, k.l2w, pot, shift, s,
-                                                         g.keys_per_split, part, *epi);
+                                                         g.keys_per_split, part, e);
   } else {
     EpiParams none{};
     k_sweep_tiles<D, R, false><<<grid, kThreads, 0, st>>>(q.pts, q.n, k.pts, k.n, centers, k.l2w, pot, shift, s,

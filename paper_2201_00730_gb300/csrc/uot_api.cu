@@ -110,7 +110,7 @@ PartSizes part_sizes(const uot_problem& p) {
 }
 
 struct WsLayout {
-  size_t state, ln_a, ln_b, l2_a, l2_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc, center;
+  size_t state, ln_a, ln_b, l2_a, l2_b, lo_a, lo_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc, center;
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
   size_t sort_tmp_bytes, total;
@@ -125,6 +125,8 @@ WsLayout ws_layout(const uot_problem& p) {
   L.ln_b = take(sizeof(double) * p.m);
   L.l2_a = take(sizeof(float) * p.n);
   L.l2_b = take(sizeof(float) * p.m);
+  L.lo_a = take(sizeof(float) * p.n);
+  L.lo_b = take(sizeof(float) * p.m);
   L.g_alt = take(sizeof(float) * p.m);
   L.f_tmp = take(sizeof(float) * p.n);
   L.g_tmp = take(sizeof(float) * p.m);
@@ -162,7 +164,7 @@ struct Ctx {
   uot_problem p;        // as given by the caller
   DevState* state;
   double *ln_a, *ln_b, *blk;
-  float *l2_a, *l2_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;
+  float *l2_a, *l2_b, *lo_a, *lo_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;  // lo_*: log2 w - l2_*
   unsigned int* rbc;  // per-row-block counters of the fused sweeps
   float* center;      // common centre of the clouds (tensor-core path)
   cudaStream_t st;
@@ -200,6 +202,8 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->ln_b = reinterpret_cast<double*>(b + L.ln_b);
   c->l2_a = reinterpret_cast<float*>(b + L.l2_a);
   c->l2_b = reinterpret_cast<float*>(b + L.l2_b);
+  c->lo_a = reinterpret_cast<float*>(b + L.lo_a);
+  c->lo_b = reinterpret_cast<float*>(b + L.lo_b);
   c->g_alt = reinterpret_cast<float*>(b + L.g_alt);
   c->f_tmp = reinterpret_cast<float*>(b + L.f_tmp);
   c->g_tmp = reinterpret_cast<float*>(b + L.g_tmp);
@@ -249,8 +253,8 @@ uot_status prepare(Ctx& c) {
     UOT_CUDA(launch_order_points(c.p.y, c.p.b, c.p.m, c.p.dim, c.osc, c.perm_y, c.ys, c.bs, c.cen_y, c.st));
   }
   if (mma_path(c.p)) UOT_CUDA(launch_center(c.p.x, c.p.n, c.p.y, c.p.m, c.p.dim, c.center, c.st));
-  UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, &c.state->status, c.st));
-  UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, &c.state->status, c.st));
+  UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, c.lo_a, &c.state->status, c.st));
+  UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, c.lo_b, &c.state->status, c.st));
   return UOT_OK;
 }
 
@@ -356,7 +360,13 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   if (opt->max_iter < 1) return fail(UOT_ERR_INVALID_ARG, "max_iter must be >= 1");
   if (opt->check_every < 1) return fail(UOT_ERR_INVALID_ARG, "check_every must be >= 1");
   if (!(opt->tol >= 0.0) || !isfinite(opt->tol)) return fail(UOT_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (opt->lse_reference < 0 || opt->lse_reference > 2)
+    return fail(UOT_ERR_INVALID_ARG, "lse_reference must be 0, 1 or 2");
   const uot_problem& p = c.p;
+  // fixed-reference sweeps (tiled path): the row log-sum-exps live in the
+  // temporaries, which a solve does not otherwise use
+  float* lse_g = (c.tiled && opt->lse_reference != 1) ? c.g_tmp : nullptr;
+  float* lse_f = (c.tiled && opt->lse_reference != 1) ? c.f_tmp : nullptr;
   v = prepare(c);
   if (v != UOT_OK) return v;
   // iteration state in the sweeps' order: f_hat and the two g buffers
@@ -377,9 +387,11 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
     EpiParams e{};
     e.mode = mode; e.nq = p.m; e.moments = 0; e.s = c.s;
     e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1; e.out_is_f = 0; e.lnw_o = c.ln_b;
+    e.l2w_o = c.l2_b; e.l2lo_o = c.lo_b;
     e.old_out = (t >= 1) ? gbuf[si] : nullptr; e.out = gbuf[so];
     e.resid_hist = opt->residual_history; e.hist_index = t;
     e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
+    e.lse_buf = lse_g; e.lse_policy = opt->lse_reference;
     v = sweep(c, 1, fst, ti ? &c.state->slot[si].cf : nullptr, false, &splits, &e, &fused);
     if (v != UOT_OK) return v;
     e.splits = splits;
@@ -395,7 +407,8 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
     EpiParams ef = e;
     ef.nq = p.n; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
     ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = fst; ef.resid_hist = nullptr;
-    ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r;
+    ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
+    ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r; ef.lse_buf = lse_f;
     v = sweep(c, 0, gbuf[so], ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
     if (v != UOT_OK) return v;
     ef.splits = splits;
@@ -404,7 +417,9 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   }
   UOT_CUDA(launch_finalize(ti ? 1 : 0, fst, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y, c.st));
   Slot slot{};
+  unsigned int misses = 0;
   UOT_CUDA(cudaMemcpyAsync(&slot, &c.state->slot[t & 1], sizeof(Slot), cudaMemcpyDeviceToHost, c.st));
+  UOT_CUDA(cudaMemcpyAsync(&misses, &c.state->lse_miss, sizeof(misses), cudaMemcpyDeviceToHost, c.st));
   UOT_CUDA(cudaStreamSynchronize(c.st));
   uot_status out = UOT_OK;
   const bool converged = !isnan(r) && r <= opt->tol;
@@ -415,7 +430,7 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
     res->iters = t;
     res->converged = converged ? 1 : 0;
     res->status = out;
-    res->reserved = 0;
+    res->lse_misses = (int32_t)(misses > 0x7fffffffu ? 0x7fffffffu : misses);
     res->residual = r;
     res->lambda = ti ? slot.lam : 0.0;
   }
@@ -510,6 +525,7 @@ uot_status ur_iteration(Ctx& c, const URLayout& L, char* b, int t, float* fst, f
   EpiParams e{};
   e.nq = p.m; e.splits = splits; e.moments = mom; e.s = c.s; e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1;
   e.out_is_f = 0; e.lnw_o = c.ln_b; e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c;
+  e.l2w_o = c.l2_b; e.l2lo_o = c.lo_b;
   e.blk = c.blk;
   if (rec) {
     EpiParams es = e;
@@ -528,6 +544,7 @@ uot_status ur_iteration(Ctx& c, const URLayout& L, char* b, int t, float* fst, f
   if (v != UOT_OK) return v;
   EpiParams ef = e;
   ef.nq = p.n; ef.splits = splits; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1; ef.lnw_o = c.ln_a;
+  ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
   ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r;
   if (rec) {
     EpiParams es = ef;
@@ -723,6 +740,7 @@ uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, 
   e.mode = EPI_SOFTMIN; e.nq = axis == 0 ? c.p.n : c.p.m; e.s = c.s;
   e.eps = c.p.eps; e.rho_o = axis == 0 ? c.p.rho1 : c.p.rho2; e.rho_i = axis == 0 ? c.p.rho2 : c.p.rho1;
   e.out_is_f = axis == 0; e.lnw_o = axis == 0 ? c.ln_a : c.ln_b; e.out = out; e.state = c.state;
+  e.l2w_o = axis == 0 ? c.l2_a : c.l2_b; e.l2lo_o = axis == 0 ? c.lo_a : c.lo_b;
   e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk;
   v = sweep(c, axis, pot_i, nullptr, false, &splits, &e, &fused);
   if (v != UOT_OK) return v;

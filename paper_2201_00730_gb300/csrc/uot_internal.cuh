@@ -33,7 +33,18 @@ struct DevState {
   float pad0;
   double dual[4];        // uot_dual_value scratch results
   double pad[4];
+  // fixed-reference log-sum-exp (tiled sweeps of a solve), indexed by out_is_f
+  int lse_ready[2];      // the side's buffer holds the previous launch's row values
+  int lse_ok[2];         // the next launch of the side takes them as exponent reference
+  unsigned int lse_miss; // rows recomputed because the reference was too far off
+  int pad1;
 };
+
+// Largest change of a row's log-sum-exp (log2 units) between two launches of a
+// side after which the next launch uses the stored values as reference, and
+// the window |lse2 - reference| within which the fixed-reference sum is kept.
+constexpr double kLseGate = 24.0;
+constexpr double kLseWindow = 60.0;
 
 constexpr int kStatusNonfinite = 1;
 constexpr int kStatusBadWeights = 2;
@@ -156,7 +167,15 @@ struct EpiParams {
   double* blk;
   unsigned int* rb_counter;  // per-row-block arrival counters (fused sweeps), zero between launches
   const double* key_shift;   // nullable: constant added to the key potential that the sweep left out
+  double fin_kk, fin_tau1, fin_tau2;  // TI translation k/(1-k) and the lambda* weights (host-computed)
+  float* lse_buf;       // nullable: per-row log-sum-exp kept between launches of this side (tiled sweeps)
+  int lse_policy;       // 0: reference after a small change, 2: whenever one is stored
+  const float* l2w_o;   // TI: log2 weights of the output side as float pairs (hi, lo)
+  const float* l2lo_o;
 };
+// Fills the constants of an EpiParams that depend only on eps and the rhos
+// (call after setting eps, rho_o, rho_i).
+void epi_finish_params(EpiParams& e);
 cudaError_t launch_combine(const EpiParams& e, cudaStream_t st);
 
 // Initial TI scalars: slot 0 = {A = Smin_a^rho1(f0), B = 0, cf = cg = 0}.
@@ -167,9 +186,11 @@ cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rh
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
                             int m, const DevState* st_dev, int slot, const int* perm_f, const int* perm_g,
                             cudaStream_t st);
-// log weights (natural FP64 and log2 FP32); negative / non-finite weights set
-// kStatusBadWeights in *flags (nullable).
-cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, int* flags, cudaStream_t st);
+// log weights (natural FP64, log2 FP32 and, if l2lo is not null, the FP32
+// remainder log2 w - l2w); negative / non-finite weights set kStatusBadWeights
+// in *flags (nullable).
+cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, float* l2lo, int* flags,
+                               cudaStream_t st);
 
 // Dual value / primal value reductions from the row (and column) sweep partials.
 struct DualParams {

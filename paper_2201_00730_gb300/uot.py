@@ -41,11 +41,11 @@ class Problem(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double),
-                ("warm_start", C.c_int32), ("reserved", C.c_int32), ("residual_history", C.c_void_p)]
+                ("warm_start", C.c_int32), ("lse_reference", C.c_int32), ("residual_history", C.c_void_p)]
 
 
 class Result(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("status", C.c_int32), ("lse_misses", C.c_int32),
                 ("residual", C.c_double), ("lambda_", C.c_double)]
 
 
@@ -223,15 +223,21 @@ class SolveOut:
     residual: float
     lam: float
     history: torch.Tensor | None = None
+    lse_misses: int = 0
+
+
+LSE_REFERENCE = {"auto": 0, "off": 1, "eager": 2}
 
 
 def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0, check_every: int = 10,
           f0: torch.Tensor | None = None, history: bool = False, ws: torch.Tensor | None = None,
-          f: torch.Tensor | None = None, g: torch.Tensor | None = None) -> SolveOut:
+          f: torch.Tensor | None = None, g: torch.Tensor | None = None, lse_reference: str = "auto") -> SolveOut:
     """Plain ('plain') or translation-invariant ('ti') Sinkhorn on the device.
 
     Returns the translated potentials (f, g), the iteration count and the
-    fixed-point residual of the returned pair.
+    fixed-point residual of the returned pair.  `lse_reference` ('auto', 'off',
+    'eager') controls the fixed-reference sweeps of the tiled path (same result
+    within rounding, different speed).
     """
     pr = spec.struct()
     dev = spec.a.device
@@ -240,8 +246,10 @@ def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0
     if f0 is not None:
         f.copy_(f0)
     hist = torch.full((max_iter + 1,), float("nan"), dtype=torch.float32, device=dev) if history else None
-    opt = Options(int(max_iter), int(check_every), float(tol), 1 if f0 is not None else 0, 0,
-                  None if hist is None else hist.data_ptr())
+    if lse_reference not in LSE_REFERENCE:
+        raise ValueError("lse_reference must be 'auto', 'off' or 'eager'")
+    opt = Options(int(max_iter), int(check_every), float(tol), 1 if f0 is not None else 0,
+                  LSE_REFERENCE[lse_reference], None if hist is None else hist.data_ptr())
     res = Result()
     ws = spec.workspace() if ws is None else ws
     fn = lib().uot_ti_sinkhorn if method == "ti" else lib().uot_sinkhorn
@@ -249,7 +257,7 @@ def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0
         raise ValueError("method must be 'ti' or 'plain'")
     st = fn(C.byref(pr), C.byref(opt), _ptr(f), _ptr(g), C.byref(res), _ptr(ws), ws.numel(), _stream())
     _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
-    return SolveOut(f, g, res.iters, bool(res.converged), st, res.residual, res.lambda_, hist)
+    return SolveOut(f, g, res.iters, bool(res.converged), st, res.residual, res.lambda_, hist, res.lse_misses)
 
 
 def dual_value(spec: Spec, f: torch.Tensor, g: torch.Tensor, primal: bool = False,

@@ -1,0 +1,30 @@
+"""Float-pair helpers of the epilogues (csrc/ffloat.cuh) against FP64 on the GPU.
+
+The half-step epilogues compute the mass terms of the TI update through a
+table-driven exp2 on float pairs; its relative error must stay far below the
+1e-9 the translation of Prop. 2 needs.  Products and sums of pairs must agree
+with FP64 to ~2^-44.
+"""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+def test_ffloat_accuracy(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "ffloat_check")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "paper_2201_00730_gb300", "csrc"),
+                    os.path.join(HERE, "cuda", "ffloat_check.cu"), "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    vals = dict(zip(out[0::2], map(float, out[1::2])))
+    assert vals["exp2"] < 1e-11, vals
+    assert vals["mul"] < 2.0 ** -43, vals
+    assert vals["add"] < 2.0 ** -43, vals
