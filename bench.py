@@ -282,7 +282,8 @@ def run_gpu(args):
     peak_ex2 = sms * EX2_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     achieved = NM / (sweep_us * 1e-6) / 1e9
     src_hash = kernel_source_hash("paper_2201_00730_gb300/csrc/sweep_tiles.cu",
-                                  "paper_2201_00730_gb300/csrc/epi_device.cuh")
+                                  "paper_2201_00730_gb300/csrc/epi_device.cuh",
+                                  "paper_2201_00730_gb300/csrc/ffloat.cuh")
     roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak_ex2, 2),
                 "unit": "G ex2/s (MUFU exp pipe)", "frac": round(achieved / peak_ex2, 4),
                 "traffic": profiled_traffic("sweep_tiles_d3", src_hash),

@@ -139,7 +139,7 @@ UOT_API uot_status uot_softmin(const uot_problem* prob, int32_t axis, const floa
  * until the process exits.  The call itself performs no cudaMalloc, cudaFree
  * or other allocation.
  *  - Limit: problems whose uot_workspace_size() exceeds 16 MiB (with N = M
- *    and 3-D points that happens between 60000 and 70000 points per side)
+ *    and 3-D points on a 152-SM GB300 that happens above 51200 points per side)
  *    are rejected with UOT_ERR_UNSUPPORTED and a message; use uot_softmin for
  *    those.
  *  - The first call on each device looks up the scratch's device address with

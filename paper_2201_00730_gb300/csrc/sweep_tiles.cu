@@ -415,8 +415,10 @@ SweepGeom tile_geom(int nq, int nk, int dim) {
   SweepGeom g{};
   g.threads = kThreads;
   const int sms = device_sm_count();
-  // 4 rows per thread for large query sets, 2 otherwise (more CTAs to balance)
-  const int R = (nq >= 2 * sms * kThreads * 4) ? 4 : 2;
+  // 4 rows per thread (half the shared-memory loads per entry, 2 CTAs of 128
+  // registers per SM) once there are a few row blocks; 2 rows (4 CTAs of 64
+  // registers per SM) for small query sets, where more CTAs balance better
+  const int R = (nq >= 4096) ? 4 : 2;
   g.rows = R;
   const int rows_per_cta = kThreads * R;
   g.row_blocks = (nq + rows_per_cta - 1) / rows_per_cta;
