@@ -56,7 +56,7 @@ typedef enum {
   UOT_ERR_WORKSPACE = 2,    /* workspace missing, too small or misaligned       */
   UOT_ERR_CUDA = 3,         /* a CUDA runtime call failed (see uot_last_error)  */
   UOT_ERR_NONFINITE = 4,    /* NaN/Inf met on the device, or invalid weights    */
-  UOT_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait gave up          */
+  UOT_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up               */
   UOT_NOT_CONVERGED = 6,    /* max_iter reached above tol; outputs are valid    */
   UOT_ERR_UNSUPPORTED = 7   /* valid request this build does not implement      */
 } uot_status;
@@ -72,9 +72,12 @@ typedef struct {
   int32_t cost_kind;   /* uot_cost_kind                                               */
   float p;             /* exponent p >= 1 of the points cost; p == 2 is the fast path */
   int32_t ordering;    /* points cost with dim <= 3 and p == 2 only: 0 = automatic, 1 = always put  */
-                       /* both clouds in Morton order and use the tiled sweep, 2 = never (results   */
-                       /* agree within rounding; ordering costs a few hundred us per call and pays  */
-                       /* off from about 1.5e9 cost entries per call, the automatic threshold)      */
+                       /* both clouds in Morton order and use the tiled CUDA-core sweeps, 2 = never, */
+                       /* 3 = Morton order with the solver's half-steps from the second iteration   */
+                       /* on the tensor-core sweep (tcgen05; correct, currently slower than 1).     */
+                       /* Results agree within rounding; ordering costs a few hundred us per call   */
+                       /* and pays off from about 1.5e9 cost entries per call, the automatic        */
+                       /* threshold.                                                                */
   double eps, rho1, rho2;
   const float* x;      /* device, N x dim (points)        */
   const float* y;      /* device, M x dim (points)        */

@@ -109,13 +109,28 @@ __device__ inline Consts make_consts(const EpiParams& e) {
   return c;
 }
 
-// Block-wide constants: thread 0 computes, everyone reads (one barrier).
-__device__ __forceinline__ const Consts& block_consts(const EpiParams& e) {
+// The threads that run an epilogue together: the whole block (barrier 0), or
+// a group of whole warps that synchronises on its own named barrier (the
+// consumer warps of a warp-specialised sweep).  tid is the thread's index in
+// the group, n the group's size (a multiple of 32).
+struct Grp {
+  int tid, n, bar;
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+  }
+};
+
+__device__ __forceinline__ Grp whole_block() { return Grp{(int)threadIdx.x, (int)blockDim.x, 0}; }
+
+// Group-wide constants: the group's thread 0 computes, everyone reads (one barrier).
+__device__ __forceinline__ const Consts& block_consts(const EpiParams& e, const Grp& g) {
   __shared__ Consts sc;
-  if (threadIdx.x == 0) sc = make_consts(e);
-  __syncthreads();
+  if (g.tid == 0) sc = make_consts(e);
+  g.sync();
   return sc;
 }
+__device__ __forceinline__ const Consts& block_consts(const EpiParams& e) { return block_consts(e, whole_block()); }
 
 // Row inputs read ahead of the merge.
 struct Pre {
@@ -201,14 +216,17 @@ __device__ __forceinline__ void row(const EpiParams& e, const Consts& c, int i, 
   row_ff(e, c, i, M[0], L[0], p, a);
 }
 
-__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total, const Grp& g) {
   __shared__ bool last;
   __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == total - 1);
-  __syncthreads();
+  g.sync();
+  if (g.tid == 0) last = (atomicAdd(counter, 1u) == total - 1);
+  g.sync();
   if (last) __threadfence();
   return last;
+}
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
+  return arrive_last(counter, total, whole_block());
 }
 
 // Partial of one block (and of the grid, once reduced): the TI mass as
@@ -288,13 +306,13 @@ __device__ inline void finalize(const EpiParams& e, const Part& t) {
 // Grid-level tail: block partial -> blk[slot]; the last of `nblocks` arrivals
 // reduces all partials in its first warp (exact power-of-two rescaling, no
 // exponentials) and finalises.
-__device__ inline void grid_tail(const EpiParams& e, const Part& mine, int slot, int nblocks) {
+__device__ inline void grid_tail(const EpiParams& e, const Part& mine, int slot, int nblocks, const Grp& g) {
   Part* bp = reinterpret_cast<Part*>(e.blk);
-  if (threadIdx.x == 0) bp[slot] = mine;
-  if (!arrive_last(&e.state->counter, (unsigned)nblocks)) return;
-  if (threadIdx.x >= 32) return;
+  if (g.tid == 0) bp[slot] = mine;
+  if (!arrive_last(&e.state->counter, (unsigned)nblocks, g)) return;
+  if (g.tid >= 32) return;
   Part t{INT_MIN, 0, 0.f, 0.f, 0.f, 0.f};
-  for (int k = threadIdx.x; k < nblocks; k += 32) {
+  for (int k = g.tid; k < nblocks; k += 32) {
     const Part* o = bp + k;
     Part q;
     q.ref = __ldcg(&o->ref); q.bad = __ldcg(&o->bad); q.hi = __ldcg(&o->hi); q.lo = __ldcg(&o->lo);
@@ -302,27 +320,30 @@ __device__ inline void grid_tail(const EpiParams& e, const Part& mine, int slot,
     t = part_merge(t, q);
   }
   t = warp_reduce(t);
-  if (threadIdx.x == 0) {
+  if (g.tid == 0) {
     finalize(e, t);
     e.state->counter = 0;
   }
 }
 
 // Block reduction of the thread accumulators, then the grid-level tail.
-__device__ inline void block_finish(const EpiParams& e, const RowAcc& a, int slot, int nblocks) {
+__device__ inline void block_finish(const EpiParams& e, const RowAcc& a, int slot, int nblocks, const Grp& g) {
   __shared__ Part sp[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int lane = g.tid & 31, warp = g.tid >> 5, nw = g.n >> 5;
   Part p{a.ref, a.bad, a.sum.hi, a.sum.lo, a.r, a.gap};
   p = warp_reduce(p);
   if (lane == 0) sp[warp] = p;
-  __syncthreads();
+  g.sync();
   if (warp == 0) {
     Part q = (lane < nw) ? sp[lane] : Part{INT_MIN, 0, 0.f, 0.f, 0.f, 0.f};
     q = warp_reduce(q);
     if (lane == 0) sp[0] = q;
   }
-  __syncthreads();
-  grid_tail(e, sp[0], slot, nblocks);
+  g.sync();
+  grid_tail(e, sp[0], slot, nblocks, g);
+}
+__device__ inline void block_finish(const EpiParams& e, const RowAcc& a, int slot, int nblocks) {
+  block_finish(e, a, slot, nblocks, whole_block());
 }
 
 }  // namespace epi

@@ -63,7 +63,7 @@ uot_status validate(const uot_problem* p) {
   if (!finite_pos(p->eps) || !finite_pos(p->rho1) || !finite_pos(p->rho2))
     return fail(UOT_ERR_INVALID_ARG, "eps, rho1, rho2 must be finite and > 0");
   if (!p->a || !p->b) return fail(UOT_ERR_INVALID_ARG, "weights a and b must be device pointers");
-  if (p->ordering < 0 || p->ordering > 2) return fail(UOT_ERR_INVALID_ARG, "ordering must be 0, 1 or 2");
+  if (p->ordering < 0 || p->ordering > 3) return fail(UOT_ERR_INVALID_ARG, "ordering must be 0, 1, 2 or 3");
   if (p->cost_kind == UOT_COST_POINTS) {
     if (p->dim < 1 || p->dim > 64) return fail(UOT_ERR_INVALID_ARG, "dim must be in 1..64 (got %d)", p->dim);
     if (!(p->p >= 1.0f) || !isfinite(p->p)) return fail(UOT_ERR_INVALID_ARG, "cost exponent p must be >= 1");
@@ -95,6 +95,8 @@ PartSizes part_sizes(const uot_problem& p) {
     if (tiled_path(p)) {
       upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
       upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
+      upd(ps.rows, (size_t)tc_geom(p.n, p.m, p.dim).splits * 2 * p.n);
+      upd(ps.cols, (size_t)tc_geom(p.m, p.n, p.dim).splits * 2 * p.m);
     }
     if (mma_path(p)) {
       upd(ps.rows, (size_t)mma_geom(p.n, p.m).splits * 2 * p.n);
@@ -171,6 +173,7 @@ struct Ctx {
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
   bool tiled;
+  bool tc;  // the solver's tiled sweeps run on the tensor cores (ordering == 3)
   const float *px, *py, *pa, *pb;
   int *perm_x, *perm_y;
   float4 *cen_x, *cen_y;
@@ -183,7 +186,7 @@ struct Ctx {
 // speeds up cover more than about 1.5e9 cost entries in total.
 bool worth_ordering(const uot_problem& p, double sweeps) {
   if (!tiled_path(p) || p.ordering == 2) return false;
-  return p.ordering == 1 || (double)p.n * (double)p.m * sweeps > 1.5e9;
+  return p.ordering == 1 || p.ordering == 3 || (double)p.n * (double)p.m * sweeps > 1.5e9;
 }
 
 uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* stream, Ctx* c,
@@ -215,6 +218,7 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
+  c->tc = c->tiled && prob->ordering == 3;
   c->px = prob->x; c->py = prob->y; c->pa = prob->a; c->pb = prob->b;
   c->perm_x = c->perm_y = nullptr;
   c->cen_x = c->cen_y = nullptr;
@@ -309,7 +313,14 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
     SideDesc X{c.px, c.l2_a, c.ln_a, p.n}, Y{c.py, c.l2_b, c.ln_b, p.m};
     const SideDesc& q = axis == 0 ? X : Y;
     const SideDesc& k = axis == 0 ? Y : X;
-    if (c.tiled && !moments) {
+    if (c.tiled && !moments && epi && epi->allow_tc && epi->lse_buf && c.tc && tc_sweep_fits(q.n)) {
+      SweepGeom g = tc_geom(q.n, k.n, p.dim);
+      *splits = g.splits;
+      epi->nq = q.n; epi->splits = g.splits; epi->part = part; epi->rb_counter = c.rbc; epi->moments = 0;
+      epi->key_shift = shift;
+      *fused = true;
+      UOT_CUDA(launch_tc_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, c.s, part, g, *epi, c.st));
+    } else if (c.tiled && !moments) {
       SweepGeom g = tile_geom(q.n, k.n, p.dim);
       *splits = g.splits;
       if (epi) {
@@ -363,10 +374,11 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   if (opt->lse_reference < 0 || opt->lse_reference > 2)
     return fail(UOT_ERR_INVALID_ARG, "lse_reference must be 0, 1 or 2");
   const uot_problem& p = c.p;
-  // fixed-reference sweeps (tiled path): the row log-sum-exps live in the
-  // temporaries, which a solve does not otherwise use
-  float* lse_g = (c.tiled && opt->lse_reference != 1) ? c.g_tmp : nullptr;
-  float* lse_f = (c.tiled && opt->lse_reference != 1) ? c.f_tmp : nullptr;
+  // tiled path: every row's log-sum-exp is kept between the sweeps of a side
+  // (the temporaries, which a solve does not otherwise use), for the fixed
+  // reference (lse_reference != 1) and the tensor-core sweeps' exponent shift
+  float* lse_g = c.tiled ? c.g_tmp : nullptr;
+  float* lse_f = c.tiled ? c.f_tmp : nullptr;
   v = prepare(c);
   if (v != UOT_OK) return v;
   // iteration state in the sweeps' order: f_hat and the two g buffers
@@ -391,7 +403,7 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
     e.old_out = (t >= 1) ? gbuf[si] : nullptr; e.out = gbuf[so];
     e.resid_hist = opt->residual_history; e.hist_index = t;
     e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
-    e.lse_buf = lse_g; e.lse_policy = opt->lse_reference;
+    e.lse_buf = lse_g; e.lse_policy = opt->lse_reference; e.allow_tc = t >= 1;
     v = sweep(c, 1, fst, ti ? &c.state->slot[si].cf : nullptr, false, &splits, &e, &fused);
     if (v != UOT_OK) return v;
     e.splits = splits;
@@ -423,7 +435,8 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   UOT_CUDA(cudaStreamSynchronize(c.st));
   uot_status out = UOT_OK;
   const bool converged = !isnan(r) && r <= opt->tol;
-  if (status & kStatusBadWeights) out = fail(UOT_ERR_NONFINITE, "negative, NaN or infinite weights");
+  if (status & kStatusTimeout) out = fail(UOT_ERR_TIMEOUT, "a bounded device-side wait gave up (tensor-core sweep)");
+  else if (status & kStatusBadWeights) out = fail(UOT_ERR_NONFINITE, "negative, NaN or infinite weights");
   else if (status != 0 || isnan(r)) out = fail(UOT_ERR_NONFINITE, "non-finite value met during the iteration");
   else if (opt->tol > 0.0 && !converged) out = UOT_NOT_CONVERGED;
   if (res) {

@@ -48,6 +48,7 @@ constexpr double kLseWindow = 60.0;
 
 constexpr int kStatusNonfinite = 1;
 constexpr int kStatusBadWeights = 2;
+constexpr int kStatusTimeout = 4;  // a bounded device-side wait gave up
 
 // ---- launch geometry -----------------------------------------------------
 
@@ -131,6 +132,16 @@ SweepGeom tile_geom(int nq, int nk, int dim);
 cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
                               const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
                               const struct EpiParams* epi, cudaStream_t st);
+// Tensor-core tiled sweep (sorted clouds, dim <= 3, p = 2) with the fused
+// half-step epilogue; centers_k = 128-point tile centres of the key side.
+// Needs ceil(nq / 128) <= kMaxBlocks.
+bool tc_sweep_fits(int nq);
+SweepGeom tc_geom(int nq, int nk, int dim);
+// Requires epi.lse_buf holding every row's previous log-sum-exp (the solver's
+// second and later sweeps of a side).
+cudaError_t launch_tc_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
+                            const float* pot_k, double s, float* part, const SweepGeom& g,
+                            const struct EpiParams& epi, cudaStream_t st);
 // Tensor-core sweep (dim >= 32, p = 2): centre = common centre of the clouds (dim floats).
 cudaError_t launch_mma_sweep(const SideDesc& q, const SideDesc& k, int dim, const float* center, const float* pot_k,
                              const double* shift_k, double s, float* part, const SweepGeom& g, cudaStream_t st);
@@ -172,6 +183,7 @@ struct EpiParams {
   int lse_policy;       // 0: reference after a small change, 2: whenever one is stored
   const float* l2w_o;   // TI: log2 weights of the output side as float pairs (hi, lo)
   const float* l2lo_o;
+  int allow_tc;         // host hint: lse_buf holds this side's previous row values (tensor-core sweep allowed)
 };
 // Fills the constants of an EpiParams that depend only on eps and the rhos
 // (call after setting eps, rho_o, rho_i).

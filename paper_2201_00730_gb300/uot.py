@@ -143,7 +143,7 @@ class Spec:
     y: torch.Tensor | None = None
     C: torch.Tensor | None = None
     p: float = 2.0
-    ordering: int = 0   # 0 automatic, 1 always Morton-order (dim <= 3, p = 2), 2 never
+    ordering: int = 0   # 0 automatic, 1 Morton tiles (dim <= 3, p = 2), 2 never, 3 Morton tiles + tensor-core half-steps
 
     def __post_init__(self):
         if self.C is None and (self.x is None or self.y is None):

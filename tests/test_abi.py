@@ -78,7 +78,7 @@ def test_argument_errors_without_device_work(L):
     bad_ref = uot.Options(10, 1, 0.0, 0, 3, None)
     st = L.uot_ti_sinkhorn(C.byref(ok), C.byref(bad_ref), 256, 256, None, 1 << 30, 1 << 40, None)
     assert st == 1 and b"lse_reference" in L.uot_last_error()
-    bad_order = uot.Problem(4, 5, 1, 0, 2.0, 3, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
+    bad_order = uot.Problem(4, 5, 1, 0, 2.0, 4, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
     assert L.uot_workspace_size(C.byref(bad_order)) == 0 and b"ordering" in L.uot_last_error()
     st = L.uot_softmin(C.byref(ok), 3, 256, 256, 256, 1 << 30, None)
     assert st == 1 and b"axis" in L.uot_last_error()

@@ -22,10 +22,14 @@ def U():
     return uot
 
 
-def spec_of(U, p):
+def spec_of(U, p, ordering=1):
     dev = torch.device("cuda:0")
     t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
-    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), p=p.p, ordering=1)
+    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), p=p.p, ordering=ordering)
+
+
+# Morton tiles on CUDA cores (1) and with the solver's half-steps on the tensor cores (3)
+TILED = pytest.mark.parametrize("ordering", [1, 3], ids=["cc", "tc"])
 
 
 def assert_pot_close(got, ref, eps, what=""):
@@ -36,12 +40,13 @@ def assert_pot_close(got, ref, eps, what=""):
     assert not bool((err > tol).any()), f"{what}: max err {err.max().item():.3e} (eps={eps})"
 
 
+@TILED
 @pytest.mark.parametrize("policy", ["off", "auto", "eager"])
 @pytest.mark.parametrize("method", ["plain", "ti"])
-def test_iterates_match_oracle_every_policy(U, method, policy):
+def test_iterates_match_oracle_every_policy(U, method, policy, ordering):
     pr = W.random_problem(1611, 1437, 3, seed=33, eps=0.02, rho1=0.3, rho2=2.0, mass_a=1.3, mass_b=0.6,
                           zero_frac=0.1)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering)
     C = O.cost_matrix(pr.x, pr.y)
     for T in (1, 2, 9, 80):
         r = U.solve(spec, method, max_iter=T, lse_reference=policy)
@@ -54,14 +59,15 @@ def test_iterates_match_oracle_every_policy(U, method, policy):
             assert abs(r.lam - ref.lam) < 1e-4 * pr.eps
 
 
-def test_eager_reference_misses_are_recomputed(U):
+@TILED
+def test_eager_reference_misses_are_recomputed(U, ordering):
     """Strong damping (rho = eps = 0.01: aprox halves every half-step) and a warm
     start with one spike (+5 on one point) make the potentials fall by several
     units per iteration, i.e. hundreds of log2 units in every row's log-sum-exp,
     far beyond the window: the eager setting must recompute rows, and still
     match the oracle."""
     pr = W.random_problem(900, 1100, 2, seed=8, eps=1e-2, rho1=1e-2, rho2=1e-2, mass_a=1.0, mass_b=1.7)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering)
     C = O.cost_matrix(pr.x, pr.y)
     f0 = np.zeros(900, dtype=np.float32)
     f0[0] = 5.0
@@ -78,9 +84,10 @@ def test_eager_reference_misses_are_recomputed(U):
     assert misses["plain"] > 0, misses
 
 
-def test_policies_converge_to_the_same_fixed_point(U):
+@TILED
+def test_policies_converge_to_the_same_fixed_point(U, ordering):
     pr = W.random_problem(3000, 2500, 3, seed=4, eps=5e-3, rho1=1.0, rho2=1.0, mass_a=1.0, mass_b=0.7)
-    spec = spec_of(U, pr)
+    spec = spec_of(U, pr, ordering)
     out = {p: U.solve(spec, "ti", max_iter=5000, tol=1e-6, lse_reference=p) for p in ("off", "auto", "eager")}
     for p, r in out.items():
         assert r.converged, p
