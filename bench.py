@@ -337,6 +337,7 @@ def run_gpu(args):
         out["time_to_tol"] = time_to_tol(U, W, dev, args)
         out["roofline_dense"] = dense_roofline(U, W, dev, p)
         out["batched"] = batched_leg(U, W)
+        out["workloads"] = workload_legs(U, W, dev)
     if rank == 0 and world == 1 and not args.no_extras:
         rate, dt, it, ns = oracle_sample_rate(p)
         out["cpu_baseline"] = {"value": round(rate, 5), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -395,6 +396,89 @@ def batched_leg(U, W):
             "iters_median": float(np.median(it)), "iters_max": int(it.max()),
             "entries_per_s_G": round(entries / dt / 1e9, 1),
             "note": "wall time of the whole call (host set-up, graph capture and replays included)"}
+
+
+def workload_legs(U, W, dev):
+    """The other workloads of the method, one timed run each (CUDA events):
+    1-D N = M = 256 (latency-bound: microseconds per iteration, residual recorded
+    every iteration), D = 64 Gaussians N = M = 8192 (tensor-core sweep; TI to
+    1e-6, envelope and unrolled T = 200 gradients), 3-D uniform N = M = 262144
+    (TI to 1e-6 capped at 600 iterations, envelope gradient), and the row / column
+    softmin entry point on the 20000-point clouds."""
+    import torch
+    t = lambda v: torch.from_numpy(v).to(dev)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = ev()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) * 1e-3
+
+    # 1-D, 1000 iterations each, residual history on the device (no host syncs)
+    p1 = W.config1()
+    s1 = U.Spec(t(p1.a), t(p1.b), p1.eps, p1.rho1, p1.rho2, x=t(p1.x), y=t(p1.y))
+    w1 = s1.workspace()
+    leg = {}
+    for method in ("ti", "plain"):
+        U.solve(s1, method, max_iter=50, ws=w1, history=True)
+        r, dt = timed(lambda: U.solve(s1, method, max_iter=1000, ws=w1, history=True))
+        leg[method] = {"us_per_iteration": round(dt / 1000 * 1e6, 2), "residual_at_1000": float(r.residual)}
+        r2, dt2 = timed(lambda: U.solve(s1, method, max_iter=20000, tol=TOL, check_every=10, ws=w1))
+        leg[method].update({"iters_to_1e-6": r2.iters, "seconds_to_1e-6": round(dt2, 4)})
+    out["config1_1d_256"] = leg
+
+    # D = 64 Gaussians
+    p3 = W.config3()
+    s3 = U.Spec(t(p3.a), t(p3.b), p3.eps, p3.rho1, p3.rho2, x=t(p3.x), y=t(p3.y))
+    w3 = s3.workspace()
+    U.solve(s3, "ti", max_iter=5, ws=w3)
+    with U.SweepProfile() as prof:
+        r3, dt3 = timed(lambda: U.solve(s3, "ti", max_iter=MAX_ITER, tol=TOL, check_every=10, ws=w3))
+    _, dtg = timed(lambda: U.grad(s3, r3.f, r3.g, ws=w3))
+    leg = {"ti_iters_to_1e-6": r3.iters, "ti_seconds": round(dt3, 4),
+           "sweep_G_entries_per_s": round(p3.n * p3.m / (prof.sweep_ms / max(1, prof.timed) * 1e-3) / 1e9, 1),
+           "envelope_grads_seconds": round(dtg, 4)}
+    try:
+        _, dtu = timed(lambda: U.grad_unrolled(s3, T=200, ckpt_every=20))
+        leg["unrolled_T200_K20_seconds"] = round(dtu, 3)
+    except Exception as ex:  # reported, not fatal for the bench line
+        leg["unrolled_T200_K20_error"] = str(ex)[:200]
+    out["config3_d64_8192"] = leg
+
+    # 3-D uniform, N = M = 262144
+    p5 = W.config5()
+    s5 = U.Spec(t(p5.a), t(p5.b), p5.eps, p5.rho1, p5.rho2, x=t(p5.x), y=t(p5.y))
+    w5 = s5.workspace()
+    U.solve(s5, "ti", max_iter=3, ws=w5)
+    r5, dt5 = timed(lambda: U.solve(s5, "ti", max_iter=600, tol=TOL, check_every=10, ws=w5))
+    _, dtg5 = timed(lambda: U.grad(s5, r5.f, r5.g, ws=w5))
+    nm5 = float(p5.n) * p5.m
+    out["config5_3d_262144"] = {"ti_iters": r5.iters, "converged": bool(r5.converged), "residual": float(r5.residual),
+                                "ti_seconds": round(dt5, 3),
+                                "G_entries_per_s": round(nm5 * (2 * r5.iters + 1) / dt5 / 1e9, 1),
+                                "envelope_grads_seconds": round(dtg5, 3)}
+
+    # row / column softmin entry point (running max; ordering forced on)
+    p2 = W.config2(1.0)
+    s2 = U.Spec(t(p2.a), t(p2.b), p2.eps, p2.rho1, p2.rho2, x=t(p2.x), y=t(p2.y), ordering=1)
+    w2 = s2.workspace()
+    leg = {}
+    for axis, name in ((0, "rows"), (1, "columns")):
+        pot = torch.zeros(p2.m if axis == 0 else p2.n, device=dev)
+        U.softmin(s2, pot, axis, w2)
+        with U.SweepProfile() as prof:
+            for _ in range(10):
+                U.softmin(s2, pot, axis, w2)
+        torch.cuda.synchronize()
+        leg[name] = round(p2.n * p2.m / (prof.sweep_ms / max(1, prof.timed) * 1e-3) / 1e9, 1)
+    leg["note"] = "G-entries/s of uot_softmin (sort included in the call, sweep timed alone)"
+    out["softmin_entry_point_20000"] = leg
+    return out
 
 
 def dense_cost_on_device(p, dev):
