@@ -101,6 +101,8 @@ PartSizes part_sizes(const uot_problem& p) {
     if (mma_path(p)) {
       upd(ps.rows, (size_t)mma_geom(p.n, p.m).splits * 2 * p.n);
       upd(ps.cols, (size_t)mma_geom(p.m, p.n).splits * 2 * p.m);
+      upd(ps.rows, (size_t)flash_geom(p.n, p.m).splits * (2 + p.dim) * p.n);
+      upd(ps.cols, (size_t)flash_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
     }
   } else {
     SweepGeom gr = dense_row_geom(p.n, p.m);
@@ -336,6 +338,12 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       SweepGeom g = mma_geom(q.n, k.n);
       *splits = g.splits;
       UOT_CUDA(launch_mma_sweep(q, k, p.dim, c.center, pot, shift, c.s, part, g, c.st));
+    } else if (mma_path(p)) {
+      // gradient sweep with moments: dC/dx = 2 (x - y)
+      SweepGeom g = flash_geom(q.n, k.n);
+      *splits = g.splits;
+      UOT_CUDA(launch_flash_sweep(q.pts, q.n, k.pts, k.n, p.dim, c.center, k.l2w, pot, shift, nullptr, nullptr,
+                                  nullptr, c.s, 2.0f, part, g, c.st));
     } else {
       SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
       *splits = g.splits;
@@ -498,6 +506,11 @@ URLayout ur_layout(const uot_problem& p, int T, int K) {
   const SweepGeom a1 = adjoint_geom(p.m, p.n), a2 = adjoint_geom(p.n, p.m);
   size_t ap = (size_t)a1.splits * (2 + D) * M;
   if ((size_t)a2.splits * (2 + D) * N > ap) ap = (size_t)a2.splits * (2 + D) * N;
+  if (mma_path(p)) {
+    const SweepGeom b1 = flash_geom(p.m, p.n), b2 = flash_geom(p.n, p.m);
+    if ((size_t)b1.splits * (2 + D) * M > ap) ap = (size_t)b1.splits * (2 + D) * M;
+    if ((size_t)b2.splits * (2 + D) * N > ap) ap = (size_t)b2.splits * (2 + D) * N;
+  }
   L.adj = take(sizeof(float) * ap);
   L.sums = take(sizeof(double) * 8);
   L.total = off;
@@ -657,6 +670,7 @@ uot_status grad_unrolled(const uot_problem* prob, int T, int K, double* value, f
   const double eps = p.eps, r1 = p.rho1, r2 = p.rho2;
   const double a1 = r1 / (r1 + eps), b1 = eps / (eps + r1) * r1 / (r1 + r2);
   const double a2 = r2 / (r2 + eps), b2 = eps / (eps + r2) * r2 / (r1 + r2);
+  const float* ctr_c = mma_path(c.p) ? c.center : nullptr;  // tensor-core adjoint sweeps for dim >= 32
   const double kf0 = eps / (eps + r1) * r2 / (r1 + r2), kg0 = eps / (eps + r2) * r1 / (r1 + r2);
   const double kf = kf0 / (1.0 - kf0), kg = kg0 / (1.0 - kg0);
   for (int sgi = L.nck - 1; sgi >= 0; --sgi) {
@@ -682,13 +696,13 @@ uot_status grad_unrolled(const uot_problem* prob, int T, int K, double* value, f
       UOT_CUDA(launch_bw_f1(p.n, p.dim, fbb, fhat, c.ln_a, rec + 3, sums + 2, kf, r1, a1, G, ga, gx, Sb, c.blk, ctr,
                             sums + 3, c.st));
       UOT_CUDA(launch_bw_smin_init(p.m, gbarn, c.ln_b, rec + 2, r2, -b1, sums + 3, gbb, gb, c.st));
-      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, c.st));
+      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, ctr_c, c.st));
       UOT_CUDA(launch_bw_adj(p.m, p.dim, val, mom, c.ln_b, eps, gbb, gb, gy, c.blk, ctr, sums + 4, c.st));
       // g half-step of iteration t+1
       UOT_CUDA(launch_bw_g1(p.m, p.dim, gbb, ghat, c.ln_b, rec + 1, sums + 4, kg, r2, a2, Gp, gb, gy, Spb, c.blk, ctr,
                             sums + 5, c.st));
       UOT_CUDA(launch_bw_fset(p.n, fbar, c.ln_a, rec + 0, r1, -b2, sums + 5, fbb, ga, c.st));
-      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, c.st));
+      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, ctr_c, c.st));
       UOT_CUDA(launch_bw_adj(p.n, p.dim, val, mom, c.ln_a, eps, fbb, ga, gx, c.blk, ctr, sums + 2, c.st));
     }
   }

@@ -142,6 +142,16 @@ SweepGeom tc_geom(int nq, int nk, int dim);
 cudaError_t launch_tc_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
                             const float* pot_k, double s, float* part, const SweepGeom& g,
                             const struct EpiParams& epi, cudaStream_t st);
+// Tensor-core sweep with moments (dim >= 32, p = 2): partials [splits][2 + dim][nq]
+// (max, sum of mult_j 2^(t - max), momscale * the moments of (x_i - y_j)).
+// Forward gradient sweep: l2w, pot, shift of the keys, zrow = hk = mk = null,
+// momscale = 2.  Adjoint sweep: zrow = the query potential, hk = the keys' h,
+// mk = the keys' signed cotangents, momscale = 1.
+SweepGeom flash_geom(int nq, int nk);
+cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
+                               const float* l2w, const float* pot, const double* shift, const float* zrow,
+                               const float* hk, const float* mk, double s, float momscale, float* part,
+                               const SweepGeom& g, cudaStream_t st);
 // Tensor-core sweep (dim >= 32, p = 2): centre = common centre of the clouds (dim floats).
 cudaError_t launch_mma_sweep(const SideDesc& q, const SideDesc& k, int dim, const float* center, const float* pot_k,
                              const double* shift_k, double s, float* part, const SweepGeom& g, cudaStream_t st);
@@ -237,9 +247,10 @@ cudaError_t launch_grad_epilogue(const GradParams& gp, cudaStream_t st);
 
 // ---- unrolled backward (adjoint.cu, unrolled.cu) -----------------------------
 SweepGeom adjoint_geom(int nq, int nk);
+// center != null (dim >= 32): the sweep runs on the tensor cores (flash sweep).
 cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int dim, const float* pot_q,
                            const float* h_k, const float* c_k, double s, float* part, double* val, double* mom,
-                           cudaStream_t st);
+                           const float* center, cudaStream_t st);
 cudaError_t launch_add_scalar(const float* u, const double* c, int n, float* v, cudaStream_t st);
 cudaError_t launch_moments(const float* part, int nq, int dim, int splits, double scale, float* G, cudaStream_t st);
 cudaError_t launch_final_side(const float* part, int CH, int nq, int splits, double s, double eps, double rho,

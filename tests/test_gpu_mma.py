@@ -71,3 +71,18 @@ def test_d64_solve_and_grads_match_oracle(U):
     for k, e in (("a", ea), ("b", eb), ("x", ex), ("y", ey)):
         rel = ((gr[k].double().cpu() - e).norm() / e.norm()).item()
         assert rel < 1e-4, (k, rel)
+
+
+@pytest.mark.parametrize("n,m,d,T,K", [(96, 80, 48, 12, 5), (130, 110, 64, 20, 20)])
+def test_unrolled_high_dim_matches_autograd(U, n, m, d, T, K):
+    """Unrolled backward with the tensor-core moment and adjoint sweeps (dim >= 32) against FP64
+    autograd of the oracle's truncated TI solve."""
+    p = gauss_problem(n, m, d, seed=d + T, eps=0.1, rho=0.5)
+    spec = spec_of(U, p)
+    val, g = U.grad_unrolled(spec, T=T, ckpt_every=K)
+    rv, ga, gb, gx, gy = O.unrolled_grads(p.x, p.y, p.a, p.b, p.eps, p.rho1, p.rho2, T)
+    assert abs(val.item() - rv.item()) < 1e-6 * abs(rv.item())
+    for k, ref in (("a", ga), ("b", gb), ("x", gx), ("y", gy)):
+        ref = torch.as_tensor(ref, dtype=torch.float64)
+        rel = ((g[k].double().cpu() - ref).norm() / ref.norm()).item()
+        assert rel < 1e-4, (k, rel)
