@@ -80,7 +80,8 @@ __device__ __forceinline__ void merge_rows(const float* part, int CH, int nq, in
 }
 
 // Per-launch constants of the half-step as float pairs, made once per block
-// (thread 0, FP64) and read from shared memory by the rows.
+// (thread 0, FP32 only: the FP64 parts come precomputed from the host and the
+// state's float-pair copies) and read from shared memory by the rows.
 struct Consts {
   ffl::ff U;    // 1/s = eps ln 2 (log2 units -> cost units)
   ffl::ff KS;   // constant shift of the key potential left out by the sweep
@@ -89,23 +90,26 @@ struct Consts {
   ffl::ff K1;   // TI residual: stored hat + shift - (the part of the next step fixed by the other side)
   ffl::ff RL;   // log2(e)/rho_o (mass exponent)
   int lse_ready;
+  const ffl::Exp2Table* tab;  // exp2 table (global, or a shared-memory copy)
 };
 
+__device__ __forceinline__ ffl::ff pair(const float (&v)[2]) { return ffl::ff{v[0], v[1]}; }
+
 __device__ inline Consts make_consts(const EpiParams& e) {
+  using namespace ffl;
   const Slot& si = e.state->slot[e.slot_in];
-  const double Xin = e.out_is_f ? si.B : si.A;                      // key-side Smin^rho scalar
-  const double cS = e.rho_o / (e.rho_o + e.eps);                    // aprox factor
-  const double cX = e.eps / (e.eps + e.rho_o) * e.rho_o / (e.rho_o + e.rho_i);
-  const double base_old = e.out_is_f ? si.cf : si.cg;               // stored hat + shift = bar
-  const double cR = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i) * (e.out_is_f ? si.A : si.B);
+  const ff Xin = pair(e.out_is_f ? si.Bf : si.Af);    // key-side Smin^rho scalar
+  const ff base_old = pair(e.out_is_f ? si.cff : si.cgf);  // stored hat + shift = bar
+  const ff own = pair(e.out_is_f ? si.Af : si.Bf);
   Consts c;
-  c.U = ffl::from_double(1.0 / e.s);
-  c.KS = ffl::from_double(e.key_shift ? *e.key_shift : 0.0);
-  c.CS = ffl::from_double(cS);
-  c.CXX = ffl::from_double(cX * Xin);
-  c.K1 = ffl::from_double(base_old - cR);
-  c.RL = ffl::from_double(kLog2e / e.rho_o);
+  c.U = pair(e.U2);
+  c.KS = e.key_shift ? pair(e.out_is_f ? si.cgf : si.cff) : ff{0.f, 0.f};
+  c.CS = pair(e.CS2);
+  c.CXX = mul(pair(e.CX2), Xin);
+  c.K1 = add(base_old, neg(mul(pair(e.CR2), own)));
+  c.RL = pair(e.RL2);
   c.lse_ready = e.lse_buf ? e.state->lse_ready[e.out_is_f] : 0;
+  c.tab = &kExp2Tab;
   return c;
 }
 
@@ -203,7 +207,7 @@ __device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int 
     const int yr = (int)ceilf(y.hi);
     if (a.ref == INT_MIN) a.ref = yr;
     else if (yr > a.ref) { a.sum = scale2(a.sum, yr - a.ref); a.ref = yr; }
-    a.sum = add(a.sum, exp2(add(y, (float)(-a.ref))));
+    a.sum = add(a.sum, exp2(add(y, (float)(-a.ref)), *c.tab));
   }
 }
 
@@ -264,35 +268,71 @@ __device__ __forceinline__ Part part_shfl(const Part& p, int off) {
   return o;
 }
 
-__device__ __forceinline__ Part warp_reduce(Part p) {
-  for (int off = 16; off > 0; off >>= 1) p = part_merge(p, part_shfl(p, off));
-  return p;
+// Warp-wide reduction of the partials, the result on every lane: the largest
+// reference by an integer reduction, each lane's sum rescaled to it (exact
+// powers of two), a butterfly of float-pair sums (commutative, so every lane
+// ends with the same pair), and the maxima and flag by integer reductions
+// (r and gap are >= +0, so their bit patterns order like their values).
+__device__ __forceinline__ Part warp_reduce(const Part& p) {
+  const int R = __reduce_max_sync(0xffffffffu, p.ref);
+  ffl::ff s{0.f, 0.f};
+  if (p.ref != INT_MIN) s = scale2(ffl::ff{p.hi, p.lo}, R - p.ref);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const ffl::ff o{__shfl_xor_sync(0xffffffffu, s.hi, off), __shfl_xor_sync(0xffffffffu, s.lo, off)};
+    s = ffl::add(s, o);
+  }
+  Part q;
+  q.ref = R;
+  q.hi = s.hi;
+  q.lo = s.lo;
+  q.bad = __reduce_or_sync(0xffffffffu, (unsigned)p.bad) ? 1 : 0;
+  q.r = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(p.r)));
+  q.gap = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(p.gap)));
+  return q;
 }
 
 // Thread 0 of the last block: scalars of the half-step, residual, status.
-__device__ inline void finalize(const EpiParams& e, const Part& t) {
+// Float-pair arithmetic throughout; the FP64 copies of the slot are written
+// last (skipped with e.ff_only) so that nothing waits on the FP64 pipe.
+__device__ inline void finalize(const EpiParams& e, const Part& t, const ffl::Exp2Table& tab = ffl::kExp2Tab) {
+  using namespace ffl;
   DevState* st = e.state;
   int status = st->status;
   if (t.bad != 0 || isnan(t.r)) status |= kStatusNonfinite;
   if (e.mode == EPI_TI) {
-    // log <w, e^{-hat/rho_o}> (empty sum: -inf)
-    const double lse = (t.ref == INT_MIN || !(t.hi > 0.f)) ? -INFINITY
-                                                          : (double)t.ref * ffl::kLn2d + ffl::log(ffl::ff{t.hi, t.lo});
-    const double Xhat = -e.rho_o * lse;              // Smin_w^rho_o(hat)
-    const double c = e.fin_kk * Xhat;                // closed-form translation k/(1-k) Xhat
-    const double X = Xhat + c;                       // Smin(hat + c) = Smin(hat) + c
-    if (!isfinite(X)) status |= kStatusNonfinite;
+    // log <w, e^{-hat/rho_o}> = ref ln 2 + ln(hi + lo) (empty sum: -inf)
+    const bool empty = t.ref == INT_MIN || !(t.hi > 0.f);
+    const ff lse = empty ? ff{-INFINITY, 0.f} : add(mul(kLn2ff, from_int(t.ref)), log_ff(ff{t.hi, t.lo}, tab));
+    const ff Xhat = mul(lse, pair(e.NR2));           // Smin_w^rho_o(hat) = -rho_o lse
+    const ff c = mul(Xhat, pair(e.KK2));             // closed-form translation k/(1-k) Xhat
+    const ff X = add(Xhat, c);                       // Smin(hat + c) = Smin(hat) + c
+    if (!isfinite(X.hi) || !isfinite(X.lo)) status |= kStatusNonfinite;
     Slot& so = st->slot[e.slot_out];
+    ff lam{0.f, 0.f};
     if (e.out_is_f) {
-      so.A = X; so.cf = c;
-      so.lam = e.fin_tau1 * so.B - e.fin_tau2 * X;   // lambda* = tau1 Smin_b(gb) - tau2 Smin_a(fb)
+      so.Af[0] = X.hi; so.Af[1] = X.lo; so.cff[0] = c.hi; so.cff[1] = c.lo;
+      // lambda* = tau1 Smin_b(gb) - tau2 Smin_a(fb)
+      lam = add(mul(pair(e.T12), pair(so.Bf)), neg(mul(pair(e.T22), X)));
+      so.lamf[0] = lam.hi; so.lamf[1] = lam.lo;
     } else {
-      so.B = X; so.cg = c;
+      so.Bf[0] = X.hi; so.Bf[1] = X.lo; so.cgf[0] = c.hi; so.cgf[1] = c.lo;
     }
-  }
-  if (e.old_out) {
-    st->resid = t.r;
-    if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+    if (e.old_out) {
+      st->resid = t.r;
+      if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+    }
+    st->status = status;
+    if (!e.ff_only) {
+      if (e.out_is_f) { so.A = to_double(X); so.cf = to_double(c); so.lam = to_double(lam); }
+      else { so.B = to_double(X); so.cg = to_double(c); }
+    }
+  } else {
+    if (e.old_out) {
+      st->resid = t.r;
+      if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+    }
+    st->status = status;
   }
   if (e.lse_buf) {
     // policy 2: always use the stored reference; 0: only after a small change
@@ -300,7 +340,15 @@ __device__ inline void finalize(const EpiParams& e, const Part& t) {
     st->lse_ok[side] = (e.lse_policy == 2) || (e.lse_policy == 0 && t.gap <= (float)kLseGate);
     st->lse_ready[side] = 1;
   }
-  st->status = status;
+}
+
+// The FP64 copies of a slot from its float pairs.
+__device__ inline void slot_doubles(Slot& s) {
+  s.A = ffl::to_double(pair(s.Af));
+  s.B = ffl::to_double(pair(s.Bf));
+  s.cf = ffl::to_double(pair(s.cff));
+  s.cg = ffl::to_double(pair(s.cgf));
+  s.lam = ffl::to_double(pair(s.lamf));
 }
 
 // Grid-level tail: block partial -> blk[slot]; the last of `nblocks` arrivals

@@ -111,9 +111,12 @@ __global__ void __launch_bounds__(kBlk) k_ti_init(const float* f0, const double*
   t = block_reduce(t);
   if (threadIdx.x == 0) {
     const double A = -rho1 * (t.m + log(t.s));
+    const float Ah = (float)A, Al = (float)(A - (double)Ah);
     for (int q = 0; q < 2; ++q) {
-      st->slot[q].A = A; st->slot[q].B = 0.0; st->slot[q].cf = 0.0;
-      st->slot[q].cg = 0.0; st->slot[q].lam = 0.0;
+      Slot& o = st->slot[q];
+      o.A = A; o.B = 0.0; o.cf = 0.0; o.cg = 0.0; o.lam = 0.0;
+      o.Af[0] = Ah; o.Af[1] = Al;
+      o.Bf[0] = o.Bf[1] = o.cff[0] = o.cff[1] = o.cgf[0] = o.cgf[1] = o.lamf[0] = o.lamf[1] = 0.f;
     }
     if (!isfinite(A) || t.bad != 0.0) st->status |= kStatusNonfinite;
     st->counter = 0;
@@ -320,11 +323,24 @@ cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, floa
   return cudaGetLastError();
 }
 
+namespace {
+void split2(double d, float* o) {
+  o[0] = (float)d;
+  o[1] = (float)(d - (double)o[0]);
+}
+}  // namespace
+
 void epi_finish_params(EpiParams& e) {
   const double k = e.eps / (e.eps + e.rho_o) * e.rho_i / (e.rho_o + e.rho_i);
-  e.fin_kk = k / (1.0 - k);
-  e.fin_tau1 = e.rho_o / (e.rho_o + e.rho_i);
-  e.fin_tau2 = e.rho_i / (e.rho_o + e.rho_i);
+  split2(1.0 / e.s, e.U2);
+  split2(e.rho_o / (e.rho_o + e.eps), e.CS2);
+  split2(e.eps / (e.eps + e.rho_o) * e.rho_o / (e.rho_o + e.rho_i), e.CX2);
+  split2(k, e.CR2);
+  split2(kLog2e / e.rho_o, e.RL2);
+  split2(-e.rho_o, e.NR2);
+  split2(k / (1.0 - k), e.KK2);
+  split2(e.rho_o / (e.rho_o + e.rho_i), e.T12);
+  split2(e.rho_i / (e.rho_o + e.rho_i), e.T22);
 }
 
 cudaError_t launch_log_weights(const float* w, int n, double* lnw, float* l2w, float* l2lo, int* flags,

@@ -112,8 +112,9 @@ constexpr double kLn2d = 0.69314718055994530942;
 constexpr float kLn2Hi = (float)kLn2d;
 constexpr float kLn2Lo = (float)(kLn2d - (double)(float)kLn2d);
 
-// 2^y for a float pair y with y.hi <= 64; returns 0 below 2^-126.
-__device__ __forceinline__ ff exp2(ff y) {
+// 2^y for a float pair y with y.hi <= 64; returns 0 below 2^-126.  T: the
+// table (the global one, or a copy in shared memory).
+__device__ __forceinline__ ff exp2(ff y, const Exp2Table& T = kExp2Tab) {
   if (!(y.hi > -126.f)) return ff{0.f, 0.f};
   const float n = rintf(y.hi);
   const float d = y.hi - n;               // exact, |d| <= 1/2
@@ -128,22 +129,32 @@ __device__ __forceinline__ ff exp2(ff y) {
   ff E = fast_two_sum(1.f, ph);
   E = fast_two_sum(E.hi, E.lo + q);
   const int j = (int)jf + 32;
-  const ff T{kExp2Tab.hi[j], kExp2Tab.lo[j]};
-  ff v = mul(T, E);
+  ff v = mul(ff{T.hi[j], T.lo[j]}, E);
   const float sc = pow2f((int)n);  // n in [-126, 64]
   v.hi *= sc;
   v.lo *= sc;
   return v;
 }
 
-// Natural log of a positive float pair, returned in FP64: y0 = log2(hi) from
-// the hardware approximation, then one Newton correction ln(1 + r) ~ r with
-// r = a 2^-y0 - 1 evaluated on pairs (|r| ~ 1e-7, so r^2/2 is below 1e-14).
-__device__ __forceinline__ double log(ff a) {
+constexpr ff kLn2ff{kLn2Hi, kLn2Lo};
+
+// Natural log of a positive float pair: y0 = log2(hi) from the hardware
+// approximation, then one Newton correction ln(1 + r) ~ r with r = a 2^-y0 - 1
+// evaluated on pairs (|r| ~ 1e-7, so r^2/2 is below 1e-14).
+__device__ __forceinline__ ff log_ff(ff a, const Exp2Table& T = kExp2Tab) {
   const float y0 = __log2f(a.hi);
-  const ff e = exp2(ff{-y0, 0.f});
+  const ff e = exp2(ff{-y0, 0.f}, T);
   const ff r = add(mul(a, e), -1.f);
-  return (double)y0 * kLn2d + to_double(r);
+  return add(mul(kLn2ff, y0), r);
+}
+
+// The same, returned in FP64.
+__device__ __forceinline__ double log(ff a) { return to_double(log_ff(a)); }
+
+// An integer as an exact float pair (|k| < 2^31).
+__device__ __forceinline__ ff from_int(int k) {
+  const float hi = (float)k;
+  return ff{hi, (float)(k - (int)hi)};
 }
 
 }  // namespace ffl

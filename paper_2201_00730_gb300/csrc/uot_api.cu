@@ -188,6 +188,7 @@ struct Ctx {
 // speeds up cover more than about 1.5e9 cost entries in total.
 bool worth_ordering(const uot_problem& p, double sweeps) {
   if (!tiled_path(p) || p.ordering == 2) return false;
+  if (p.ordering == 0 && small_path(p)) return false;  // the resident cluster solver needs no ordering
   return p.ordering == 1 || p.ordering == 3 || (double)p.n * (double)p.m * sweeps > 1.5e9;
 }
 
@@ -399,7 +400,25 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   const int mode = ti ? EPI_TI : EPI_PLAIN;
   int t = 0, status = 0;
   float r = NAN;
-  for (;;) {
+  if (p.ordering == 0 && small_path(p)) {
+    // the whole loop in one launch of one thread-block cluster (small problems are latency bound)
+    EpiParams eg{};
+    eg.mode = mode; eg.nq = p.m; eg.moments = 0; eg.s = c.s;
+    eg.eps = p.eps; eg.rho_o = p.rho2; eg.rho_i = p.rho1; eg.out_is_f = 0; eg.lnw_o = c.ln_b;
+    eg.l2w_o = c.l2_b; eg.l2lo_o = c.lo_b;
+    eg.resid_hist = opt->residual_history; eg.state = c.state; eg.blk = c.blk; eg.lse_policy = 1;
+    EpiParams ef = eg;
+    ef.nq = p.n; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
+    ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = fst; ef.resid_hist = nullptr;
+    ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
+    UOT_CUDA(launch_small_solve(c.px, c.py, c.l2_a, c.l2_b, p.n, p.m, p.dim, ti ? 1 : 0, opt->max_iter,
+                                opt->check_every, opt->tol, c.s, fst, gbuf[0], gbuf[1], eg, ef, c.st));
+    int iters = 0;
+    UOT_CUDA(cudaMemcpyAsync(&iters, &c.state->iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    v = read_flags(c, &status, &r);
+    if (v != UOT_OK) return v;
+    t = iters;
+  } else for (;;) {
     // g half-step of iteration t+1: column sweep over x with fb_t = f_hat + cf
     const int so = (t + 1) & 1, si = t & 1;
     int splits = 0;

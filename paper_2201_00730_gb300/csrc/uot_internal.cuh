@@ -14,14 +14,18 @@ constexpr double kLn2 = 0.69314718055994530942;   // ln(2)
 constexpr float kZeroW = -1.0e30f;
 constexpr float kInitMax = -2.0e30f;
 
-// Scalars of one half-step of the iteration, FP64 (Prop. 2 / App. B quantities).
+// Scalars of one half-step of the iteration, FP64 (Prop. 2 / App. B quantities),
+// with float-pair copies (hi, lo) that the half-step epilogues read and write:
+// FP64 arithmetic is slow on this GPU and sits on every launch's critical path.
 struct Slot {
   double A;    // Smin_a^rho1(fb) of the current fb
   double B;    // Smin_b^rho2(gb) of the current gb
   double cf;   // fb = f_hat + cf (the stored f vector is f_hat)
   double cg;   // gb = g_hat + cg
   double lam;  // lambda*(fb, gb) = tau1 B - tau2 A
-  double pad[3];
+  double pad;
+  float Af[2], Bf[2], cff[2], cgf[2], lamf[2];  // float pairs of A, B, cf, cg, lam
+  float padf[2];
 };
 
 // Device-resident iteration state, at the start of the workspace.
@@ -37,8 +41,19 @@ struct DevState {
   int lse_ready[2];      // the side's buffer holds the previous launch's row values
   int lse_ok[2];         // the next launch of the side takes them as exponent reference
   unsigned int lse_miss; // rows recomputed because the reference was too far off
-  int pad1;
+  int iters;             // iterations done by the resident small-problem solver
 };
+
+// Resident solver for small point problems (dim <= 3, p = 2, N M <= 2^20, both
+// clouds in one SM's shared memory): the plain / TI loop of the solver in one
+// launch of a thread-block cluster, eg and ef the g- and f-half-step templates
+// (per-iteration fields are set on the device); writes the iteration count to
+// state->iters.
+bool small_path(const uot_problem& p);
+struct EpiParams;
+cudaError_t launch_small_solve(const float* x, const float* y, const float* l2a, const float* l2b, int n, int m,
+                               int dim, int ti, int max_iter, int check_every, double tol, double s, float* fst,
+                               float* gb0, float* gb1, const EpiParams& eg, const EpiParams& ef, cudaStream_t st);
 
 // Largest change of a row's log-sum-exp (log2 units) between two launches of a
 // side after which the next launch uses the stored values as reference, and
@@ -187,16 +202,28 @@ struct EpiParams {
   const float* part;
   double* blk;
   unsigned int* rb_counter;  // per-row-block arrival counters (fused sweeps), zero between launches
-  const double* key_shift;   // nullable: constant added to the key potential that the sweep left out
-  double fin_kk, fin_tau1, fin_tau2;  // TI translation k/(1-k) and the lambda* weights (host-computed)
+  // nullable: the key side's pending shift in slot_in (cf for a g half-step, cg
+  // for an f half-step), which the sweep left out and the epilogue applies
+  const double* key_shift;
+  // host-computed float pairs (hi, lo), see epi_finish_params
+  float U2[2];    // 1/s = eps ln 2
+  float CS2[2];   // rho_o/(rho_o+eps)
+  float CX2[2];   // eps/(eps+rho_o) rho_o/(rho_o+rho_i)
+  float CR2[2];   // eps/(eps+rho_o) rho_i/(rho_o+rho_i)
+  float RL2[2];   // log2(e)/rho_o
+  float NR2[2];   // -rho_o
+  float KK2[2];   // TI translation k/(1-k), k = CR
+  float T12[2];   // lambda* weights tau1 = rho_o/(rho_o+rho_i), tau2 = rho_i/(rho_o+rho_i)
+  float T22[2];
+  int ff_only;    // 1: the finalisation writes only the float pairs of the slot (resident solver)
   float* lse_buf;       // nullable: per-row log-sum-exp kept between launches of this side (tiled sweeps)
   int lse_policy;       // 0: reference after a small change, 2: whenever one is stored
   const float* l2w_o;   // TI: log2 weights of the output side as float pairs (hi, lo)
   const float* l2lo_o;
   int allow_tc;         // host hint: lse_buf holds this side's previous row values (tensor-core sweep allowed)
 };
-// Fills the constants of an EpiParams that depend only on eps and the rhos
-// (call after setting eps, rho_o, rho_i).
+// Fills the constants of an EpiParams that depend only on s, eps and the rhos
+// (call after setting s, eps, rho_o, rho_i).
 void epi_finish_params(EpiParams& e);
 cudaError_t launch_combine(const EpiParams& e, cudaStream_t st);
 

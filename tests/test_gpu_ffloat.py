@@ -3,7 +3,8 @@
 The half-step epilogues compute the mass terms of the TI update through a
 table-driven exp2 on float pairs; its relative error must stay far below the
 1e-9 the translation of Prop. 2 needs.  Products and sums of pairs must agree
-with FP64 to ~2^-44.
+with FP64 to ~2^-44, and the pair log that finalises the mass sums with
+FP64's to within exp2's relative error (its Newton step evaluates 2^-y0 with it).
 """
 import os
 import shutil
@@ -28,3 +29,4 @@ def test_ffloat_accuracy(tmp_path):
     assert vals["exp2"] < 1e-11, vals
     assert vals["mul"] < 2.0 ** -43, vals
     assert vals["add"] < 2.0 ** -43, vals
+    assert vals["log"] < 1e-11, vals

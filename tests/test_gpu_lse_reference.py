@@ -95,3 +95,25 @@ def test_policies_converge_to_the_same_fixed_point(U, ordering):
     for p in ("auto", "eager"):
         assert (out[p].f - out["off"].f).abs().max().item() < 1e-4 * pr.eps + 2e-5
         assert (out[p].g - out["off"].g).abs().max().item() < 1e-4 * pr.eps + 2e-5
+
+
+def test_resident_solver_reference_misses(U):
+    """The resident cluster solver (auto ordering, N M <= 2^20) takes each row's
+    previous log-sum-exp as a fixed reference; with the strong damping and the
+    spiked warm start above the references miss, the rows are redone exactly
+    (counted in lse_misses) and the iterates still match the oracle."""
+    pr = W.random_problem(900, 1100, 2, seed=8, eps=1e-2, rho1=1e-2, rho2=1e-2, mass_a=1.0, mass_b=1.7)
+    spec = spec_of(U, pr, 0)
+    C = O.cost_matrix(pr.x, pr.y)
+    f0 = np.zeros(900, dtype=np.float32)
+    f0[0] = 5.0
+    for method in ("plain", "ti"):
+        r = U.solve(spec, method, max_iter=6, f0=torch.from_numpy(f0).cuda())
+        if method == "ti":
+            ref = O.ti_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 6, fb0=f0)
+        else:
+            ref = O.sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 6, f0=f0)
+        assert_pot_close(r.f, ref.f, pr.eps, f"{method} f")
+        assert_pot_close(r.g, ref.g, pr.eps, f"{method} g")
+        if method == "plain":
+            assert r.lse_misses > 0

@@ -38,7 +38,8 @@ def spec_of(U, p, dense=False, ordering=0):
 
 # the points cost with dim <= 3 and p = 2 has three kernels: Morton-ordered tiles on CUDA cores (1),
 # the same with the solver's half-steps on the tensor cores (3), and direct (2)
-ORDERINGS = pytest.mark.parametrize("ordering", [1, 3, 2], ids=["tiled", "tiled_tc", "direct"])
+# ordering 0 on problems with N M <= 2^18 in dim <= 3 runs the resident one-CTA solver
+ORDERINGS = pytest.mark.parametrize("ordering", [1, 3, 2, 0], ids=["tiled", "tiled_tc", "direct", "auto"])
 
 
 def pot_tol(eps, ref):
@@ -146,16 +147,41 @@ def test_config1_1000_iterations_match_golden(U, method, ordering):
 
 
 @pytest.mark.parametrize("method", ["plain", "ti"])
-@pytest.mark.parametrize("kind", ["tiled", "tiled_tc", "direct", "dense"])
+@pytest.mark.parametrize("kind", ["tiled", "tiled_tc", "direct", "dense", "small"])
 def test_iterates_match_oracle_ragged(U, method, kind):
     """N != M, rho1 != rho2, unequal masses, zero weights: iterate-by-iterate parity."""
-    pr = W.random_problem(611, 437, 2, seed=21, eps=0.05, rho1=0.3, rho2=2.0, mass_a=1.3, mass_b=0.6,
+    n, m = (311, 237) if kind == "small" else (611, 437)  # "small": the resident one-CTA solver
+    pr = W.random_problem(n, m, 2, seed=21, eps=0.05, rho1=0.3, rho2=2.0, mass_a=1.3, mass_b=0.6,
                           zero_frac=0.1)
     dense = kind == "dense"
-    spec = spec_of(U, pr, dense=dense, ordering={"tiled": 1, "tiled_tc": 3, "direct": 2, "dense": 0}[kind])
+    spec = spec_of(U, pr, dense=dense,
+                   ordering={"tiled": 1, "tiled_tc": 3, "direct": 2, "dense": 0, "small": 0}[kind])
     C = O._t(W.dense_cost_f32(pr.x, pr.y)) if dense else O.cost_matrix(pr.x, pr.y)
     for T in (1, 7, 60):
         r = U.solve(spec, method, max_iter=T)
+        ref = (O.ti_sinkhorn if method == "ti" else O.sinkhorn)(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
+        assert_pot_close(r.f, ref.f, pr.eps, f"f after {T}")
+        assert_pot_close(r.g, ref.g, pr.eps, f"g after {T}")
+        res_ref = O.fixed_point_residual(C, pr.a, pr.b, ref.f, ref.g, pr.eps, pr.rho1, pr.rho2).item()
+        assert abs(r.residual - res_ref) <= 1e-4 * pr.eps + 1e-3 * res_ref
+        if method == "ti":
+            assert abs(r.lam - ref.lam) < 1e-4 * pr.eps
+
+
+@pytest.mark.parametrize("method", ["plain", "ti"])
+@pytest.mark.parametrize("n,m,d", [(1, 1, 1), (3, 2, 2), (17, 64, 3), (255, 33, 1), (1000, 262, 3),
+                                   (1024, 1024, 2), (4096, 256, 1), (64, 4096, 3), (4096, 5, 2)])
+def test_resident_cluster_solver_sizes(U, method, n, m, d):
+    """The resident cluster solver (auto ordering, N M <= 2^20): odd counts (pair padding),
+    one to sixteen CTAs (some without rows of the short side), groups of 1 to 32 lanes per row,
+    vs the oracle iterate by iterate."""
+    pr = W.random_problem(n, m, d, seed=n + 7 * m, eps=0.03, rho1=0.5, rho2=1.7, mass_a=1.2, mass_b=0.7,
+                          zero_frac=0.05 if n > 4 else 0.0)
+    spec = spec_of(U, pr, ordering=0)
+    C = O.cost_matrix(pr.x, pr.y)
+    for T in (1, 6):
+        r = U.solve(spec, method, max_iter=T)
+        assert r.iters == T
         ref = (O.ti_sinkhorn if method == "ti" else O.sinkhorn)(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
         assert_pot_close(r.f, ref.f, pr.eps, f"f after {T}")
         assert_pot_close(r.g, ref.g, pr.eps, f"g after {T}")
