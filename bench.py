@@ -398,10 +398,23 @@ def batched_leg(U, W):
             "note": "wall time of the whole call (host set-up, graph capture and replays included)"}
 
 
+def _rate(hist):
+    """Linear contraction rate of a residual history: exp of the least-squares
+    slope of log r_t over the iterations with 1e-7 <= r_t <= 1e-3 (None when
+    fewer than 10 such iterations)."""
+    import numpy as np
+    h = hist.double().cpu().numpy()
+    t = np.nonzero(np.isfinite(h) & (h >= 1e-7) & (h <= 1e-3))[0]
+    if len(t) < 10:
+        return None
+    slope = np.polyfit(t.astype(np.float64), np.log(h[t]), 1)[0]
+    return round(float(np.exp(slope)), 6)
+
+
 def workload_legs(U, W, dev):
     """The other workloads of the method, one timed run each (CUDA events):
     1-D N = M = 256 (latency-bound: microseconds per iteration, residual recorded
-    every iteration), D = 64 Gaussians N = M = 8192 (tensor-core sweep; TI to
+    every iteration, contraction rates of plain, H- and G-Sinkhorn), D = 64 Gaussians N = M = 8192 (tensor-core sweep; TI to
     1e-6, envelope and unrolled T = 200 gradients), 3-D uniform N = M = 262144
     (TI to 1e-6 capped at 600 iterations, envelope gradient), and the row / column
     softmin entry point on the 20000-point clouds."""
@@ -424,10 +437,11 @@ def workload_legs(U, W, dev):
     s1 = U.Spec(t(p1.a), t(p1.b), p1.eps, p1.rho1, p1.rho2, x=t(p1.x), y=t(p1.y))
     w1 = s1.workspace()
     leg = {}
-    for method in ("ti", "plain"):
+    for method in ("ti", "g", "plain"):
         U.solve(s1, method, max_iter=50, ws=w1, history=True)
         r, dt = timed(lambda: U.solve(s1, method, max_iter=1000, ws=w1, history=True))
-        leg[method] = {"us_per_iteration": round(dt / 1000 * 1e6, 2), "residual_at_1000": float(r.residual)}
+        leg[method] = {"us_per_iteration": round(dt / 1000 * 1e6, 2), "residual_at_1000": float(r.residual),
+                       "contraction_rate": _rate(r.history)}
         r2, dt2 = timed(lambda: U.solve(s1, method, max_iter=20000, tol=TOL, check_every=10, ws=w1))
         leg[method].update({"iters_to_1e-6": r2.iters, "seconds_to_1e-6": round(dt2, 4)})
     out["config1_1d_256"] = leg

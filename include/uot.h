@@ -179,6 +179,20 @@ UOT_API uot_status uot_sinkhorn(const uot_problem* prob, const uot_options* opt,
 UOT_API uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
                            uot_result* result, void* ws, size_t ws_bytes, void* stream);
 
+/* G-Sinkhorn (Sec. 3): alternate maximisation of G(fb, gb, lambda), with the
+ * translation lambda* of Prop. 2 refreshed after every full iteration:
+ *   gb_{t+1} = rho2/(rho2+eps) Smin_a^eps(C - fb_t - lambda_t) + lambda_t
+ *   fb_{t+1} = rho1/(rho1+eps) Smin_b^eps(C - gb_{t+1} + lambda_t) - lambda_t
+ *   lambda_{t+1} = lambda*(fb_{t+1}, gb_{t+1})
+ * from fb_0 = 0 (or f on entry), lambda_0 = 0.  The mass reductions behind
+ * lambda* are float-pair sums (~1e-11 relative).  On return f, g hold
+ * (fb_T + lambda_T, gb_T - lambda_T) and result->lambda = lambda_T.  The
+ * residual is that of uot_sinkhorn on the returned pair, which equals
+ * |gb_{T+1} - gb_T|_inf.  Arguments, results and errors as for
+ * uot_ti_sinkhorn. */
+UOT_API uot_status uot_g_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                          uot_result* result, void* ws, size_t ws_bytes, void* stream);
+
 /* Dual objective F_eps(f, g) (Sec. 1, Eq. eq-dual-uot-kl), FP64, written to
  * out[0] (device).  If out has room for 3 doubles (want_primal != 0) it also
  * writes out[1] = primal objective (Eq. eq-primal-uot-kl) of the plan

@@ -103,9 +103,11 @@ __device__ inline Consts make_consts(const EpiParams& e) {
   const ff own = pair(e.out_is_f ? si.Af : si.Bf);
   Consts c;
   c.U = pair(e.U2);
-  c.KS = e.key_shift ? pair(e.out_is_f ? si.cgf : si.cff) : ff{0.f, 0.f};
+  const ff shift = pair(e.out_is_f ? si.cgf : si.cff);  // the key side's pending shift
+  c.KS = e.key_shift ? shift : ff{0.f, 0.f};            // null: the sweep applied it
   c.CS = pair(e.CS2);
-  c.CXX = mul(pair(e.CX2), Xin);
+  // G-Sinkhorn: the output moves with the key shift (v = aprox(S) + shift)
+  c.CXX = e.mode == EPI_G ? neg(shift) : mul(pair(e.CX2), Xin);
   c.K1 = add(base_old, neg(mul(pair(e.CR2), own)));
   c.RL = pair(e.RL2);
   c.lse_ready = e.lse_buf ? e.state->lse_ready[e.out_is_f] : 0;
@@ -145,7 +147,7 @@ struct Pre {
 
 __device__ __forceinline__ Pre prefetch(const EpiParams& e, int i) {
   Pre p;
-  const bool ti = e.mode == EPI_TI && i >= 0;
+  const bool ti = (e.mode == EPI_TI || e.mode == EPI_G) && i >= 0;
   p.lwh = ti ? e.l2w_o[i] : 0.f;
   p.lwl = ti ? e.l2lo_o[i] : 0.f;
   p.old = (e.old_out && i >= 0) ? e.old_out[i] : 0.f;
@@ -189,7 +191,7 @@ __device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int 
   const ff S = neg(add(mul(lse, c.U), c.KS));
   ff v = S;
   if (e.mode != EPI_SOFTMIN) v = mul(S, c.CS);
-  if (e.mode == EPI_TI) v = add(v, neg(c.CXX));
+  if (e.mode == EPI_TI || e.mode == EPI_G) v = add(v, neg(c.CXX));
   const float vo = v.hi + v.lo;
   if (!isfinite(vo)) a.bad = 1;
   e.out[e.perm_out ? e.perm_out[i] : i] = vo;
@@ -197,7 +199,7 @@ __device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int 
     const ff d = (e.mode == EPI_TI) ? add(add(c.K1, p.old), neg(v)) : add(neg(v), p.old);
     a.r = fmaxf(a.r, fabsf(d.hi + d.lo));
   }
-  if (e.mode == EPI_TI && p.lwh > 0.5f * kZeroW) {
+  if ((e.mode == EPI_TI || e.mode == EPI_G) && p.lwh > 0.5f * kZeroW) {
     // mass term w_i e^{-v/rho_o} = 2^y, y = log2 w_i - v log2(e)/rho_o
     const ff y = add(ff{p.lwh, p.lwl}, neg(mul(v, c.RL)));
     if (!(fabsf(y.hi) < 1e9f)) {
@@ -326,6 +328,36 @@ __device__ inline void finalize(const EpiParams& e, const Part& t, const ffl::Ex
     if (!e.ff_only) {
       if (e.out_is_f) { so.A = to_double(X); so.cf = to_double(c); so.lam = to_double(lam); }
       else { so.B = to_double(X); so.cg = to_double(c); }
+    }
+  } else if (e.mode == EPI_G) {
+    // Smin_w^rho_o of the new iterate; after the f half-step lambda_{t+1} =
+    // tau1 Smin_b(gb_{t+1}) - tau2 Smin_a(fb_{t+1}) (Prop. 2), which the next
+    // g half-step adds to its keys (cf) and the f half-step after it
+    // subtracts (cg, set by the g half-step from the slot it read)
+    const bool empty = t.ref == INT_MIN || !(t.hi > 0.f);
+    const ff lse = empty ? ff{-INFINITY, 0.f} : add(mul(kLn2ff, from_int(t.ref)), log_ff(ff{t.hi, t.lo}, tab));
+    const ff X = mul(lse, pair(e.NR2));
+    if (!isfinite(X.hi) || !isfinite(X.lo)) status |= kStatusNonfinite;
+    Slot& so = st->slot[e.slot_out];
+    ff lam{0.f, 0.f}, cg{0.f, 0.f};
+    if (e.out_is_f) {
+      so.Af[0] = X.hi; so.Af[1] = X.lo;
+      lam = add(mul(pair(e.T12), pair(so.Bf)), neg(mul(pair(e.T22), X)));
+      so.lamf[0] = lam.hi; so.lamf[1] = lam.lo;
+      so.cff[0] = lam.hi; so.cff[1] = lam.lo;
+    } else {
+      cg = neg(pair(st->slot[e.slot_in].cff));
+      so.Bf[0] = X.hi; so.Bf[1] = X.lo;
+      so.cgf[0] = cg.hi; so.cgf[1] = cg.lo;
+    }
+    if (e.old_out) {
+      st->resid = t.r;
+      if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+    }
+    st->status = status;
+    if (!e.ff_only) {
+      if (e.out_is_f) { so.A = to_double(X); so.cf = to_double(lam); so.lam = so.cf; }
+      else { so.B = to_double(X); so.cg = to_double(cg); }
     }
   } else {
     if (e.old_out) {

@@ -125,9 +125,10 @@ __global__ void __launch_bounds__(kBlk) k_ti_init(const float* f0, const double*
 
 __global__ void k_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
                            int m, const DevState* st, int slot, const int* pf, const int* pg) {
+  // ti = 1: Phi(fb, gb) with fb = f_hat + cf; ti = 2 (G-Sinkhorn): (fb + lambda, gb - lambda)
   const Slot& s = st->slot[slot];
-  const double sf = ti ? s.cf + s.lam : 0.0;
-  const double sg = ti ? s.cg - s.lam : 0.0;
+  const double sf = ti == 1 ? s.cf + s.lam : ti == 2 ? s.lam : 0.0;
+  const double sg = ti == 1 ? s.cg - s.lam : ti == 2 ? -s.lam : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
     if (i < n) {
       if (ti) f[pf ? pf[i] : i] = (float)((double)f_hat[i] + sf);

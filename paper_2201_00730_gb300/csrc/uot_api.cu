@@ -368,8 +368,10 @@ uot_status read_flags(Ctx& c, int* status, float* resid) {
   return UOT_OK;
 }
 
-uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float* f, float* g,
+// variant: 0 plain (F-)Sinkhorn, 1 H-Sinkhorn (TI), 2 G-Sinkhorn.
+uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, float* f, float* g,
                  uot_result* res, void* ws, size_t ws_bytes, void* stream) {
+  const bool ti = variant != 0;  // slots, key shifts and lambda in use
   uot_status v0 = validate(prob);
   if (v0 != UOT_OK) return v0;
   if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");
@@ -397,7 +399,7 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
   else if (c.tiled) UOT_CUDA(launch_gather_vec(f, c.perm_x, p.n, fst, c.st));
   UOT_CUDA(cudaMemsetAsync(gbuf[0], 0, sizeof(float) * p.m, c.st));
   if (ti) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
-  const int mode = ti ? EPI_TI : EPI_PLAIN;
+  const int mode = variant == 1 ? EPI_TI : variant == 2 ? EPI_G : EPI_PLAIN;
   int t = 0, status = 0;
   float r = NAN;
   if (p.ordering == 0 && small_path(p)) {
@@ -454,7 +456,7 @@ uot_status solve(bool ti, const uot_problem* prob, const uot_options* opt, float
     if (!fused) UOT_CUDA(launch_combine(ef, c.st));
     ++t;
   }
-  UOT_CUDA(launch_finalize(ti ? 1 : 0, fst, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y, c.st));
+  UOT_CUDA(launch_finalize(variant, fst, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y, c.st));
   Slot slot{};
   unsigned int misses = 0;
   UOT_CUDA(cudaMemcpyAsync(&slot, &c.state->slot[t & 1], sizeof(Slot), cudaMemcpyDeviceToHost, c.st));
@@ -797,12 +799,17 @@ uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, 
 
 uot_status uot_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
                         uot_result* result, void* ws, size_t ws_bytes, void* stream) {
-  return solve(false, prob, opt, f, g, result, ws, ws_bytes, stream);
+  return solve(0, prob, opt, f, g, result, ws, ws_bytes, stream);
 }
 
 uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
                            uot_result* result, void* ws, size_t ws_bytes, void* stream) {
-  return solve(true, prob, opt, f, g, result, ws, ws_bytes, stream);
+  return solve(1, prob, opt, f, g, result, ws, ws_bytes, stream);
+}
+
+uot_status uot_g_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                          uot_result* result, void* ws, size_t ws_bytes, void* stream) {
+  return solve(2, prob, opt, f, g, result, ws, ws_bytes, stream);
 }
 
 uot_status uot_dual_value(const uot_problem* prob, const float* f, const float* g, double* out,

@@ -180,6 +180,7 @@ enum EpiMode {
   EPI_SOFTMIN = 0,   // out = S (cost units)
   EPI_PLAIN = 1,     // out = rho_o/(rho_o+eps) S; residual vs old (if given)
   EPI_TI = 2,        // out = g_hat / f_hat; FP64 mass reduction; finalize scalars
+  EPI_G = 3,         // G-Sinkhorn: out = aprox(S) +- lambda_t; mass reduction; lambda_{t+1} after the f half-step
 };
 
 struct EpiParams {

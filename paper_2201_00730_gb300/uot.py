@@ -75,7 +75,7 @@ def lib() -> C.CDLL:
         L.uot_softmin.restype = C.c_int
         L.uot_softmin_noalloc.argtypes = [P, C.c_int32, V, V, V]
         L.uot_softmin_noalloc.restype = C.c_int
-        for fn in (L.uot_sinkhorn, L.uot_ti_sinkhorn):
+        for fn in (L.uot_sinkhorn, L.uot_ti_sinkhorn, L.uot_g_sinkhorn):
             fn.argtypes = [P, C.POINTER(Options), V, V, C.POINTER(Result), V, S, V]
             fn.restype = C.c_int
         L.uot_dual_value.argtypes = [P, V, V, V, C.c_int32, V, S, V]
@@ -232,7 +232,7 @@ LSE_REFERENCE = {"auto": 0, "off": 1, "eager": 2}
 def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0, check_every: int = 10,
           f0: torch.Tensor | None = None, history: bool = False, ws: torch.Tensor | None = None,
           f: torch.Tensor | None = None, g: torch.Tensor | None = None, lse_reference: str = "auto") -> SolveOut:
-    """Plain ('plain') or translation-invariant ('ti') Sinkhorn on the device.
+    """Plain ('plain'), translation-invariant ('ti', H-Sinkhorn) or G-Sinkhorn ('g') on the device.
 
     Returns the translated potentials (f, g), the iteration count and the
     fixed-point residual of the returned pair.  `lse_reference` ('auto', 'off',
@@ -252,9 +252,9 @@ def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0
                   LSE_REFERENCE[lse_reference], None if hist is None else hist.data_ptr())
     res = Result()
     ws = spec.workspace() if ws is None else ws
-    fn = lib().uot_ti_sinkhorn if method == "ti" else lib().uot_sinkhorn
-    if method not in ("ti", "plain"):
-        raise ValueError("method must be 'ti' or 'plain'")
+    if method not in ("ti", "plain", "g"):
+        raise ValueError("method must be 'ti', 'plain' or 'g'")
+    fn = {"ti": lib().uot_ti_sinkhorn, "plain": lib().uot_sinkhorn, "g": lib().uot_g_sinkhorn}[method]
     st = fn(C.byref(pr), C.byref(opt), _ptr(f), _ptr(g), C.byref(res), _ptr(ws), ws.numel(), _stream())
     _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
     return SolveOut(f, g, res.iters, bool(res.converged), st, res.residual, res.lambda_, hist, res.lse_misses)

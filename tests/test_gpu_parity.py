@@ -146,7 +146,30 @@ def test_config1_1000_iterations_match_golden(U, method, ordering):
     assert abs(val - d[key]["value"]) < 1e-6 * abs(d[key]["value"])
 
 
-@pytest.mark.parametrize("method", ["plain", "ti"])
+@ORDERINGS
+def test_config1_g_sinkhorn_1000_iterations(U, ordering):
+    """G-Sinkhorn (Sec. 3) on the 1-D N = M = 256 problem, 1000 iterations, against the
+    FP64 oracle run here; lambda_t drifts with rounding like H-Sinkhorn's (see the
+    golden test above), and the returned pair must satisfy the mass equality of Prop. 1."""
+    pr = W.config1()
+    spec = spec_of(U, pr, ordering=ordering)
+    C = O.cost_matrix(pr.x, pr.y)
+    r = U.solve(spec, "g", max_iter=1000, tol=0.0)
+    ref = O.g_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 1000)
+    assert r.iters == 1000
+    assert_pot_close(r.f, ref.f, pr.eps, "g-sinkhorn f")
+    assert_pot_close(r.g, ref.g, pr.eps, "g-sinkhorn g")
+    assert abs(r.lam - ref.lam) < 1e-4 * pr.eps * (1000 / 60)
+    f, g = r.f.double().cpu(), r.g.double().cpu()
+    A = (O._t(pr.a) * torch.exp(-f / pr.rho1)).sum().item()
+    B = (O._t(pr.b) * torch.exp(-g / pr.rho2)).sum().item()
+    assert abs(A - B) < 1e-6 * A
+
+
+ORACLE_SOLVER = {"plain": O.sinkhorn, "ti": O.ti_sinkhorn, "g": O.g_sinkhorn}
+
+
+@pytest.mark.parametrize("method", ["plain", "ti", "g"])
 @pytest.mark.parametrize("kind", ["tiled", "tiled_tc", "direct", "dense", "small"])
 def test_iterates_match_oracle_ragged(U, method, kind):
     """N != M, rho1 != rho2, unequal masses, zero weights: iterate-by-iterate parity."""
@@ -159,16 +182,16 @@ def test_iterates_match_oracle_ragged(U, method, kind):
     C = O._t(W.dense_cost_f32(pr.x, pr.y)) if dense else O.cost_matrix(pr.x, pr.y)
     for T in (1, 7, 60):
         r = U.solve(spec, method, max_iter=T)
-        ref = (O.ti_sinkhorn if method == "ti" else O.sinkhorn)(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
+        ref = ORACLE_SOLVER[method](C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
         assert_pot_close(r.f, ref.f, pr.eps, f"f after {T}")
         assert_pot_close(r.g, ref.g, pr.eps, f"g after {T}")
         res_ref = O.fixed_point_residual(C, pr.a, pr.b, ref.f, ref.g, pr.eps, pr.rho1, pr.rho2).item()
         assert abs(r.residual - res_ref) <= 1e-4 * pr.eps + 1e-3 * res_ref
-        if method == "ti":
+        if method != "plain":
             assert abs(r.lam - ref.lam) < 1e-4 * pr.eps
 
 
-@pytest.mark.parametrize("method", ["plain", "ti"])
+@pytest.mark.parametrize("method", ["plain", "ti", "g"])
 @pytest.mark.parametrize("n,m,d", [(1, 1, 1), (3, 2, 2), (17, 64, 3), (255, 33, 1), (1000, 262, 3),
                                    (1024, 1024, 2), (4096, 256, 1), (64, 4096, 3), (4096, 5, 2)])
 def test_resident_cluster_solver_sizes(U, method, n, m, d):
@@ -182,12 +205,12 @@ def test_resident_cluster_solver_sizes(U, method, n, m, d):
     for T in (1, 6):
         r = U.solve(spec, method, max_iter=T)
         assert r.iters == T
-        ref = (O.ti_sinkhorn if method == "ti" else O.sinkhorn)(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
+        ref = ORACLE_SOLVER[method](C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, T)
         assert_pot_close(r.f, ref.f, pr.eps, f"f after {T}")
         assert_pot_close(r.g, ref.g, pr.eps, f"g after {T}")
         res_ref = O.fixed_point_residual(C, pr.a, pr.b, ref.f, ref.g, pr.eps, pr.rho1, pr.rho2).item()
         assert abs(r.residual - res_ref) <= 1e-4 * pr.eps + 1e-3 * res_ref
-        if method == "ti":
+        if method != "plain":
             assert abs(r.lam - ref.lam) < 1e-4 * pr.eps
 
 
@@ -214,11 +237,14 @@ def test_ti_faster_than_plain_same_fixed_point(U):
     pr = W.random_problem(1500, 1200, 2, seed=9, eps=0.01, rho1=1.0, rho2=1.0, mass_a=1.0, mass_b=1.5)
     spec = spec_of(U, pr)
     ti = U.solve(spec, "ti", max_iter=20000, tol=1e-6, check_every=10)
+    gs = U.solve(spec, "g", max_iter=20000, tol=1e-6, check_every=10)
     pl = U.solve(spec, "plain", max_iter=20000, tol=1e-6, check_every=10)
-    assert ti.converged and pl.converged
-    assert ti.iters < pl.iters
+    assert ti.converged and gs.converged and pl.converged
+    # Sec. 3 / Fig. 1: both translation-invariant schemes beat plain Sinkhorn when eps << rho
+    assert ti.iters < pl.iters and gs.iters < pl.iters
     # same fixed point (T3) to within the residual-implied error
     assert (ti.f - pl.f).abs().max().item() < 2e-4
+    assert (gs.f - pl.f).abs().max().item() < 2e-4
 
 
 @ORDERINGS
