@@ -77,7 +77,10 @@ typedef struct {
                        /* on the tensor-core sweep (tcgen05; correct, currently slower than 1).     */
                        /* Results agree within rounding; ordering costs a few hundred us per call   */
                        /* and pays off from about 1.5e9 cost entries per call, the automatic        */
-                       /* threshold.                                                                */
+                       /* threshold.  With 0, a solve of a problem with N M <= 2^20 whose clouds    */
+                       /* fit one SM's shared memory (16 N + 20 M + 12 max(N, M) bytes plus 8 (1-D) */
+                       /* or 16 bytes per point, <= 200 KB) runs the whole loop in one launch of a  */
+                       /* thread-block cluster instead (no ordering).                               */
   double eps, rho1, rho2;
   const float* x;      /* device, N x dim (points)        */
   const float* y;      /* device, M x dim (points)        */
@@ -86,7 +89,7 @@ typedef struct {
   const float* b;      /* device, M weights, b_j >= 0      */
 } uot_problem;
 
-/* Iteration control for uot_sinkhorn / uot_ti_sinkhorn. */
+/* Iteration control for uot_sinkhorn / uot_ti_sinkhorn / uot_g_sinkhorn. */
 typedef struct {
   int32_t max_iter;          /* >= 1 full iterations (g half-step, then f half-step)          */
   int32_t check_every;       /* >= 1: residual tested against tol every check_every iterations */

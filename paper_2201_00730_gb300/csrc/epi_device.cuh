@@ -222,13 +222,20 @@ __device__ __forceinline__ void row(const EpiParams& e, const Consts& c, int i, 
   row_ff(e, c, i, M[0], L[0], p, a);
 }
 
+// Last-arriver test of a group of blocks.  The group's barrier orders every
+// thread's earlier writes before thread 0's fence (fences are cumulative), so
+// one fence before the increment publishes the whole block's writes, and one
+// after it (last arriver only) orders the other blocks' writes before what
+// the group reads next.
 __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total, const Grp& g) {
   __shared__ bool last;
-  __threadfence();
   g.sync();
-  if (g.tid == 0) last = (atomicAdd(counter, 1u) == total - 1);
+  if (g.tid == 0) {
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == total - 1);
+    if (last) __threadfence();
+  }
   g.sync();
-  if (last) __threadfence();
   return last;
 }
 __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
