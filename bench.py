@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--rho", type=float, default=1.0)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-tol, dense and CPU legs")
     ap.add_argument("--plain-cap", type=int, default=30000, help="iteration cap of plain Sinkhorn in time-to-tol")
-    ap.add_argument("--kernel-case", choices=["points", "dense", "d64"], default=None,
+    ap.add_argument("--kernel-case", choices=["points", "dense", "d64", "small"], default=None,
                     help="only launch a few sweeps of the workload (for Nsight Compute captures) and exit")
     return ap.parse_args()
 
@@ -283,7 +283,8 @@ def run_gpu(args):
     achieved = NM / (sweep_us * 1e-6) / 1e9
     src_hash = kernel_source_hash("paper_2201_00730_gb300/csrc/sweep_tiles.cu",
                                   "paper_2201_00730_gb300/csrc/epi_device.cuh",
-                                  "paper_2201_00730_gb300/csrc/ffloat.cuh")
+                                  "paper_2201_00730_gb300/csrc/ffloat.cuh",
+                                  "paper_2201_00730_gb300/csrc/sweep_common.cuh")
     roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak_ex2, 2),
                 "unit": "G ex2/s (MUFU exp pipe)", "frac": round(achieved / peak_ex2, 4),
                 "traffic": profiled_traffic("sweep_tiles_d3", src_hash),
@@ -518,7 +519,14 @@ def run_kernel_case(args):
     dev = torch.device("cuda", 0)
     p = W.config2(args.rho)
     t = lambda v: torch.from_numpy(v).to(dev)
-    if args.kernel_case == "d64":
+    if args.kernel_case == "small":
+        # 1-D N = M = 256: the resident cluster solver, one launch per solve
+        q = W.config1()
+        spec = U.Spec(t(q.a), t(q.b), q.eps, q.rho1, q.rho2, x=t(q.x), y=t(q.y))
+        ws = spec.workspace()
+        for _ in range(2):
+            U.solve(spec, "ti", max_iter=200, ws=ws)
+    elif args.kernel_case == "d64":
         # D = 64 Gaussian clouds, N = M = 8192: the tensor-core sweep
         q = W.config3()
         spec = U.Spec(t(q.a), t(q.b), q.eps, q.rho1, q.rho2, x=t(q.x), y=t(q.y))
