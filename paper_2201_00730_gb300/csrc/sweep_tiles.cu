@@ -53,6 +53,12 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
               const float4* __restrict__ centers, const float* __restrict__ l2w, const float* __restrict__ pot,
               const double* __restrict__ shift, double s, int kps, float* __restrict__ part, EpiParams e) {
   static_assert(D >= 1 && D <= 3, "tiled sweep covers dim 1..3");
+  // Programmatic dependent launch: this grid may be scheduled while the
+  // previous kernel of the stream finishes; it waits here for that kernel's
+  // completion (and memory) before reading anything, and lets the next grid
+  // be scheduled as soon as all of its own CTAs have started.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ ulonglong2 sA[kPairsPerStage];  // {Y0 pair, Y1 pair}
   __shared__ ulonglong2 sB[kPairsPerStage];  // {Y2 pair, H pair}
   __shared__ float4 sC[kTilesPerStage];
@@ -333,8 +339,21 @@ cudaError_t run(const SideDesc& q, const SideDesc& k, const float4* centers, con
   if (epi) {
     EpiParams e = *epi;
     epi_finish_params(e);
-    k_sweep_tiles<D, R, true><<<grid, kThreads, 0, st>>>(q.pts, q.n, k.pts, k.n, centers, k.l2w, pot, shift, s,
-                                                         g.keys_per_split, part, e);
+    // launched with programmatic stream serialisation: the launch latency of
+    // one half-step hides behind the previous half-step's epilogue tail
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t err = cudaLaunchKernelEx(&cfg, k_sweep_tiles<D, R, true>, q.pts, q.n, k.pts, k.n, centers, k.l2w,
+                                         pot, shift, s, g.keys_per_split, part, e);
+    if (err != cudaSuccess) return err;
   } else {
     EpiParams none{};
     k_sweep_tiles<D, R, false><<<grid, kThreads, 0, st>>>(q.pts, q.n, k.pts, k.n, centers, k.l2w, pot, shift, s,
