@@ -79,6 +79,39 @@ __device__ __forceinline__ void merge_rows(const float* part, int CH, int nq, in
   for (int r = 0; r < R; ++r) { Mo[r] = M[r]; Lo[r] = log2f(S[r]); }
 }
 
+// The same when every chunk's partial was taken against the same reference
+// ref[r] (fixed-reference sweeps): the maxima are ref and the merge is a plain
+// sum of the chunks' sums, in the same order and with the same result as
+// merge_rows, without the maxima's loads and the rescaling exponentials.
+template <int R>
+__device__ __forceinline__ void merge_rows_ref(const float* part, int CH, int nq, int splits, const int (&idx)[R],
+                                               const float (&ref)[R], float (&Mo)[R], float (&Lo)[R]) {
+  const size_t stride = (size_t)CH * nq;
+  float S[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) S[r] = 0.f;
+  for (int k0 = 0; k0 < splits; k0 += 8) {
+    float sv[R][8];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
+        sv[r][u] = (k < splits && idx[r] >= 0) ? __ldcg(part + (size_t)k * stride + (size_t)nq + idx[r]) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float a = S[r];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a += sv[r][u];
+      S[r] = a;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) { Mo[r] = ref[r]; Lo[r] = log2f(S[r]); }
+}
+
 // Per-launch constants of the half-step as float pairs, made once per block
 // (thread 0, FP32 only: the FP64 parts come precomputed from the host and the
 // state's float-pair copies) and read from shared memory by the rows.
