@@ -21,6 +21,8 @@ Frank-Wolfe", AISTATS 2022):
   * H-Sinkhorn (TI-Sinkhorn) -- Sec. 3, Prop. 4 and its proof in App. B,
                                 general rho1 != rho2 (Eq. eq-general-iter-h-sink)
   * G-Sinkhorn               -- Sec. 3, with the +-lambda_t terms made explicit
+  * Anderson extrapolation   -- appendix "Combining Sinkhorn with Anderson
+                                acceleration" (restarted blocks of K iterations)
 
 Conventions fixed where the paper is ambiguous (each is also listed in the
 design notes):
@@ -363,6 +365,68 @@ def g_sinkhorn(C, a, b, eps, rho1, rho2, n_iter, tol=0.0, check_every=1) -> Solv
             if res <= tol:
                 break
     return SolveResult(fb + lam, gb - lam, t, res, float(lam), fb, gb, hist)
+
+
+def anderson_weights(U, r: float) -> torch.Tensor:
+    """Anderson extrapolation weights (appendix, "Combining Sinkhorn with Anderson
+    acceleration"): c = (G + r I)^{-1} 1 / 1^T (G + r I)^{-1} 1 with G = U^T U, the
+    minimiser of c^T (G + r I) c under 1^T c = 1, for the K residuals as the columns
+    of U.  The regularisation is relative: G is divided by its trace first (the
+    paper's r = 1e-7 is scale-free only in that reading)."""
+    U = _t(U)
+    G = U.T @ U
+    tr = torch.trace(G)
+    if tr > 0:
+        G = G / tr
+    z = torch.linalg.solve(G + r * torch.eye(G.shape[0], dtype=F64), torch.ones(G.shape[0], dtype=F64))
+    return z / z.sum()
+
+
+def anderson_sinkhorn(C, a, b, eps, rho1, rho2, n_iter, method="ti", K=4, r=1e-7, tol=0.0,
+                      check_every=1) -> SolveResult:
+    """F- ('plain'), H- ('ti') or G-Sinkhorn ('g') with Anderson extrapolation (appendix).
+
+    The iterate x is f (F), fb (H) or fb with lambda carried alongside (G).  From a
+    block start x_0, base iterations x_{k+1} = T(x_k) give residuals u_k = x_{k+1} - x_k;
+    after every K-th iteration t (t % K == 0), unless t is the last one or a residual
+    check, the last K + 1 iterates x_{t-K}, ..., x_t are replaced by the extrapolation
+    sum_{k<K} c_k x_{t-K+k}, c = anderson_weights([u_0 ... u_{K-1}], r), which starts the
+    next block (lambda of G takes the same combination).  The returned pair is always
+    the last base iterate's, as for the plain solvers.
+    """
+    C = _t(C)
+    x = torch.zeros(C.shape[0], dtype=F64)
+    lam = torch.tensor(0.0, dtype=F64)
+    hist, lams = [x.clone()], [lam.clone()]
+    res, t = math.nan, 0
+    out = None
+    for t in range(1, n_iter + 1):
+        if method == "plain":
+            x, g = f_sinkhorn_iteration(C, a, b, x, eps, rho1, rho2)
+            out = (x, g, 0.0)
+        elif method == "ti":
+            x, gb = h_sinkhorn_iteration(C, a, b, x, eps, rho1, rho2)
+            f, g, lo = phi_map(a, b, x, gb, rho1, rho2)
+            out = (f, g, float(lo))
+        else:
+            x, gb, lam = g_sinkhorn_iteration(C, a, b, x, lam, eps, rho1, rho2)
+            out = (x + lam, gb - lam, float(lam))
+        check = tol > 0 and t % check_every == 0
+        if check:
+            res = float(fixed_point_residual(C, a, b, out[0], out[1], eps, rho1, rho2))
+            if res <= tol:
+                break
+        hist.append(x.clone())
+        lams.append(lam.clone())
+        if t % K == 0 and t < n_iter and not check:
+            xs, ls = hist[-(K + 1):], lams[-(K + 1):]
+            U = torch.stack([xs[k + 1] - xs[k] for k in range(K)], dim=1)
+            c = anderson_weights(U, r)
+            x = sum(c[k] * xs[k] for k in range(K))
+            lam = sum(c[k] * ls[k] for k in range(K))
+            hist, lams = [x.clone()], [lam.clone()]
+    f, g, lo = out
+    return SolveResult(f, g, t, res, lo, None, None, [])
 
 
 def contraction_rate(errors) -> float:

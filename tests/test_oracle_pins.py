@@ -420,3 +420,67 @@ def test_unrolled_grads_with_zero_weights_vs_one_sided_differences():
             args = {"a": a, "b": b, name: w2}
             fd = (O.truncated_ti_value(x, y, args["a"], args["b"], p.eps, p.rho1, p.rho2, T).item() - val.item()) / h
             assert abs(fd - g[k].item()) < 1e-5 * max(1.0, abs(fd)), (name, k, fd, g[k].item())
+
+
+# ---- Anderson extrapolation (appendix, "Combining Sinkhorn with Anderson acceleration")
+
+def test_anderson_weights_exact_on_a_linear_contraction():
+    """For x_{k+1} = A x_k + b in R^3 and K = 4 residuals, the constrained minimiser has
+    U c = 0, so sum_k c_k x_k is the fixed point (I - A)^{-1} b up to the regularisation."""
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        d = 3
+        A = rng.standard_normal((d, d))
+        A = 0.7 * A / np.linalg.norm(A, 2)
+        b = rng.standard_normal(d)
+        xs = [rng.standard_normal(d)]
+        for _k in range(4):
+            xs.append(A @ xs[-1] + b)
+        U = np.stack([xs[k + 1] - xs[k] for k in range(4)], axis=1)
+        c = O.anderson_weights(torch.tensor(U), 1e-14).numpy()
+        assert abs(c.sum() - 1.0) < 1e-12
+        xe = sum(c[k] * xs[k] for k in range(4))
+        assert np.abs(xe - np.linalg.solve(np.eye(d) - A, b)).max() < 1e-8
+
+
+def test_anderson_weights_symmetric_and_regularised_limits():
+    """Orthogonal residuals of equal norm: every weight is 1/K (symmetry).  A huge r makes
+    G + r I ~ r I, so the weights tend to 1/K whatever U is; two identical
+    residual directions of different lengths (a rank-deficient G) and a tiny r puts the
+    weight on a combination with U c ~ 0."""
+    U = np.eye(4) * 3.0
+    assert np.allclose(O.anderson_weights(torch.tensor(U), 1e-7).numpy(), 0.25, atol=1e-12)
+    rng = np.random.default_rng(1)
+    U = rng.standard_normal((10, 4))
+    assert np.allclose(O.anderson_weights(torch.tensor(U), 1e9).numpy(), 0.25, atol=1e-8)
+    v = rng.standard_normal(6)
+    U = np.stack([v, 2 * v, rng.standard_normal(6), rng.standard_normal(6)], axis=1)
+    c = O.anderson_weights(torch.tensor(U), 1e-14).numpy()
+    assert np.abs(U @ c).max() < 1e-5 * np.abs(U).max() and abs(c.sum() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("method", ["plain", "ti", "g"])
+def test_anderson_without_extrapolation_is_the_base_solver(method):
+    """K > n_iter: no block ever completes, and the iterates are those of the base solver."""
+    pr = W.random_problem(40, 30, 1, seed=3, eps=0.05, rho1=0.7, rho2=1.3)
+    C = O.cost_matrix(pr.x, pr.y)
+    base = {"plain": O.sinkhorn, "ti": O.ti_sinkhorn, "g": O.g_sinkhorn}[method](
+        C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 12)
+    acc = O.anderson_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 12, method=method, K=50)
+    assert torch.equal(acc.f, base.f) and torch.equal(acc.g, base.g)
+
+
+@pytest.mark.parametrize("method", ["plain", "ti", "g"])
+def test_anderson_same_fixed_point_in_fewer_iterations(method):
+    """The appendix's claim on the 1-D problem (eps = 1e-2 << rho = 1): with K = 4,
+    r = 1e-7 every variant reaches the same fixed point, to residual 1e-9, in fewer
+    iterations than without extrapolation."""
+    pr = W.config1()
+    C = O.cost_matrix(pr.x, pr.y)
+    base = {"plain": O.sinkhorn, "ti": O.ti_sinkhorn, "g": O.g_sinkhorn}[method](
+        C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 5000, tol=1e-9, check_every=10)
+    acc = O.anderson_sinkhorn(C, pr.a, pr.b, pr.eps, pr.rho1, pr.rho2, 5000, method=method, K=4, r=1e-7,
+                              tol=1e-9, check_every=10)
+    assert acc.residual <= 1e-9 and base.residual <= 1e-9
+    assert acc.iters < base.iters
+    assert (acc.f - base.f).abs().max().item() < 1e-6 and (acc.g - base.g).abs().max().item() < 1e-6
