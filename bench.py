@@ -359,11 +359,13 @@ def time_to_tol(U, W, dev, args):
         spec = U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y))
         ws = spec.workspace()
         row = {}
-        for meth, cap in (("ti", MAX_ITER), ("plain", args.plain_cap)):
+        for meth, cap, ak in (("ti", MAX_ITER, 0), ("plain", args.plain_cap, 0), ("ti", MAX_ITER, 4)):
             U.solve(spec, meth, max_iter=3, ws=ws)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = U.solve(spec, meth, max_iter=cap, tol=TOL, check_every=10, ws=ws)
+            r = U.solve(spec, meth, max_iter=cap, tol=TOL, check_every=10, ws=ws, anderson_k=ak)
+            if ak:
+                meth = "ti_anderson_k4"
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             row[meth] = {"seconds": round(dt, 4), "iters": r.iters, "converged": r.converged,
@@ -445,6 +447,12 @@ def workload_legs(U, W, dev):
                        "contraction_rate": _rate(r.history)}
         r2, dt2 = timed(lambda: U.solve(s1, method, max_iter=20000, tol=TOL, check_every=10, ws=w1))
         leg[method].update({"iters_to_1e-6": r2.iters, "seconds_to_1e-6": round(dt2, 4)})
+        # Anderson extrapolation (appendix: K = 4, r = 1e-7) on the multi-launch loop
+        r3, dt3 = timed(lambda: U.solve(s1, method, max_iter=20000, tol=TOL, check_every=10, ws=w1,
+                                        anderson_k=4, anderson_reg=1e-7))
+        r4 = U.solve(s1, method, max_iter=300, ws=w1, history=True, anderson_k=4, anderson_reg=1e-7)
+        leg[method].update({"anderson_k4_iters_to_1e-6": r3.iters, "anderson_k4_seconds_to_1e-6": round(dt3, 4),
+                            "anderson_k4_contraction_rate": _rate(r4.history)})
     out["config1_1d_256"] = leg
 
     # D = 64 Gaussians

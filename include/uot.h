@@ -107,7 +107,21 @@ typedef struct {
                              /* within rounding; only the time differs.  Other paths ignore it. */
   float* residual_history;   /* device, nullable, >= max_iter+1 floats: entry t is the residual */
                              /* of iterate t (t = 1..iters); entry 0 is unused                   */
+  /* Anderson extrapolation (appendix, "Combining Sinkhorn with Anderson acceleration"),     */
+  /* uot_sinkhorn / uot_ti_sinkhorn / uot_g_sinkhorn.  The iterate x is f, fb or fb (with      */
+  /* lambda carried alongside) respectively; after every anderson_k-th iteration t, unless t   */
+  /* is the last one or a residual check, the last anderson_k + 1 iterates x_{t-K}..x_t are     */
+  /* replaced by sum_{k<K} c_k x_{t-K+k}, c = (G + r I)^{-1} 1 / 1^T (G + r I)^{-1} 1, with      */
+  /* G = U^T U / trace(U^T U) for the residuals u_k = x_{t-K+k+1} - x_{t-K+k} (FP64, on the    */
+  /* device), which starts the next block.  The returned pair is always a plain iterate's.   */
+  int32_t anderson_k;        /* 0 = off, else K in 2..6                                        */
+  double anderson_reg;       /* r >= 0 (the paper's experiment: 1e-7)                          */
+  void* anderson_buf;        /* device, >= uot_anderson_workspace(n, anderson_k) bytes, 16-byte */
+                             /* aligned, when anderson_k > 0; caller-owned scratch              */
 } uot_options;
+
+/* Bytes of the scratch uot_options.anderson_buf needs for N = n and K = k. */
+UOT_API size_t uot_anderson_workspace(int32_t n, int32_t k);
 
 /* Outcome of a solve, written to host memory before the call returns. */
 typedef struct {

@@ -103,8 +103,8 @@ uot_status uot_sinkhorn_batched(const uot_batch* b, const uot_options* opt, int3
   if (!opt) return bfail(UOT_ERR_INVALID_ARG, "options is NULL");
   if (opt->max_iter < 1 || opt->check_every < 1 || !(opt->tol >= 0.0))
     return bfail(UOT_ERR_INVALID_ARG, "need max_iter >= 1, check_every >= 1, tol >= 0");
-  if (opt->warm_start || opt->residual_history)
-    return bfail(UOT_ERR_UNSUPPORTED, "batched solves take no warm start and no residual history");
+  if (opt->warm_start || opt->residual_history || opt->anderson_k)
+    return bfail(UOT_ERR_UNSUPPORTED, "batched solves take no warm start, residual history or Anderson extrapolation");
   if (!f || !g || !results) return bfail(UOT_ERR_INVALID_ARG, "f, g and results must not be NULL");
   if (!ws) return bfail(UOT_ERR_WORKSPACE, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(ws) & 255) return bfail(UOT_ERR_WORKSPACE, "workspace must be 256-byte aligned");

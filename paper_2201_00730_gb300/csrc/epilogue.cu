@@ -86,9 +86,11 @@ __global__ void __launch_bounds__(kBlk) k_combine(EpiParams e) {
   epi::block_finish(e, acc, blockIdx.x, gridDim.x);
 }
 
-// slot 0 <- {A = Smin_a^rho1(f0) = -rho1 log sum_i a_i e^{-f0_i/rho1}, B = cf = cg = lam = 0}
+// only < 0: both slots <- {A = Smin_a^rho1(f0) = -rho1 log sum_i a_i e^{-f0_i/rho1}, B = cf = cg = lam = 0};
+// only = q >= 0: slot q's A <- Smin_a^rho1(f0) and cf <- 0, the rest of the state kept (a new fb
+// stored in full, e.g. after an Anderson extrapolation)
 __global__ void __launch_bounds__(kBlk) k_ti_init(const float* f0, const double* ln_a, int n, double rho1,
-                                                  DevState* st, double* blk) {
+                                                  DevState* st, double* blk, int only) {
   Red4 acc{-INFINITY, 0.0, 0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double lw = ln_a[i];
@@ -112,11 +114,18 @@ __global__ void __launch_bounds__(kBlk) k_ti_init(const float* f0, const double*
   if (threadIdx.x == 0) {
     const double A = -rho1 * (t.m + log(t.s));
     const float Ah = (float)A, Al = (float)(A - (double)Ah);
-    for (int q = 0; q < 2; ++q) {
-      Slot& o = st->slot[q];
-      o.A = A; o.B = 0.0; o.cf = 0.0; o.cg = 0.0; o.lam = 0.0;
+    if (only >= 0) {
+      Slot& o = st->slot[only];
+      o.A = A; o.cf = 0.0;
       o.Af[0] = Ah; o.Af[1] = Al;
-      o.Bf[0] = o.Bf[1] = o.cff[0] = o.cff[1] = o.cgf[0] = o.cgf[1] = o.lamf[0] = o.lamf[1] = 0.f;
+      o.cff[0] = o.cff[1] = 0.f;
+    } else {
+      for (int q = 0; q < 2; ++q) {
+        Slot& o = st->slot[q];
+        o.A = A; o.B = 0.0; o.cf = 0.0; o.cg = 0.0; o.lam = 0.0;
+        o.Af[0] = Ah; o.Af[1] = Al;
+        o.Bf[0] = o.Bf[1] = o.cff[0] = o.cff[1] = o.cgf[0] = o.cgf[1] = o.lamf[0] = o.lamf[1] = 0.f;
+      }
     }
     if (!isfinite(A) || t.bad != 0.0) st->status |= kStatusNonfinite;
     st->counter = 0;
@@ -310,8 +319,8 @@ cudaError_t launch_combine(const EpiParams& e0, cudaStream_t st) {
 }
 
 cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rho1, DevState* s,
-                           double* blk, cudaStream_t st) {
-  k_ti_init<<<grid_for(n), kBlk, 0, st>>>(f0, ln_a, n, rho1, s, blk);
+                           double* blk, cudaStream_t st, int only) {
+  k_ti_init<<<grid_for(n), kBlk, 0, st>>>(f0, ln_a, n, rho1, s, blk, only);
   note_launch();
   return cudaGetLastError();
 }

@@ -384,6 +384,14 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
   if (!(opt->tol >= 0.0) || !isfinite(opt->tol)) return fail(UOT_ERR_INVALID_ARG, "tol must be finite and >= 0");
   if (opt->lse_reference < 0 || opt->lse_reference > 2)
     return fail(UOT_ERR_INVALID_ARG, "lse_reference must be 0, 1 or 2");
+  const int AK = opt->anderson_k;
+  if (AK != 0) {
+    if (AK < 2 || AK > 6) return fail(UOT_ERR_INVALID_ARG, "anderson_k must be 0 or 2..6");
+    if (!(opt->anderson_reg >= 0.0) || !isfinite(opt->anderson_reg))
+      return fail(UOT_ERR_INVALID_ARG, "anderson_reg must be finite and >= 0");
+    if (!opt->anderson_buf || (reinterpret_cast<uintptr_t>(opt->anderson_buf) & 15))
+      return fail(UOT_ERR_INVALID_ARG, "anderson_buf must be a 16-byte aligned device pointer");
+  }
   const uot_problem& p = c.p;
   // tiled path: every row's log-sum-exp is kept between the sweeps of a side
   // (the temporaries, which a solve does not otherwise use), for the fixed
@@ -402,7 +410,7 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
   const int mode = variant == 1 ? EPI_TI : variant == 2 ? EPI_G : EPI_PLAIN;
   int t = 0, status = 0;
   float r = NAN;
-  if (p.ordering == 0 && small_path(p)) {
+  if (p.ordering == 0 && small_path(p) && AK == 0) {
     // the whole loop in one launch of one thread-block cluster (small problems are latency bound)
     EpiParams eg{};
     eg.mode = mode; eg.nq = p.m; eg.moments = 0; eg.s = c.s;
@@ -421,6 +429,10 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
     if (v != UOT_OK) return v;
     t = iters;
   } else for (;;) {
+    if (AK && t == 0) {
+      UOT_CUDA(anderson_reset(opt->anderson_buf, p.n, AK, c.st));
+      UOT_CUDA(launch_anderson_store(fst, p.n, AK, 0, variant, &c.state->slot[0], opt->anderson_buf, c.st));
+    }
     // g half-step of iteration t+1: column sweep over x with fb_t = f_hat + cf
     const int so = (t + 1) & 1, si = t & 1;
     int splits = 0;
@@ -455,6 +467,19 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
     ef.splits = splits;
     if (!fused) UOT_CUDA(launch_combine(ef, c.st));
     ++t;
+    if (AK) {
+      // Anderson: keep x_t; after every AK-th iteration that is neither the last nor a
+      // residual check, the last AK + 1 iterates give the next one
+      Slot* sl = &c.state->slot[t & 1];
+      UOT_CUDA(launch_anderson_store(fst, p.n, AK, t % (AK + 1), variant, sl, opt->anderson_buf, c.st));
+      if (t % AK == 0 && t < opt->max_iter && !(opt->tol > 0.0 && t % opt->check_every == 0)) {
+        const int p0 = (t - AK) % (AK + 1);
+        UOT_CUDA(launch_anderson_extrapolate(fst, p.n, AK, p0, opt->anderson_reg, opt->anderson_buf,
+                                             variant == 2 ? sl : nullptr, &c.state->status, c.st));
+        // H: the new fb is held in full (cf = 0); its Smin_a^rho1 for the next g half-step
+        if (variant == 1) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st, t & 1));
+      }
+    }
   }
   UOT_CUDA(launch_finalize(variant, fst, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y, c.st));
   Slot slot{};

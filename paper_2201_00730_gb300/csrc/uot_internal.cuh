@@ -229,8 +229,23 @@ void epi_finish_params(EpiParams& e);
 cudaError_t launch_combine(const EpiParams& e, cudaStream_t st);
 
 // Initial TI scalars: slot 0 = {A = Smin_a^rho1(f0), B = 0, cf = cg = 0}.
+// only >= 0: refresh slot `only`'s A for a new fb held in full (cf <- 0), keep the rest.
 cudaError_t launch_ti_init(const float* f0, const double* ln_a, int n, double rho1, DevState* st_dev,
-                           double* blk, cudaStream_t st);
+                           double* blk, cudaStream_t st, int only = -1);
+
+// ---- Anderson extrapolation (uot_options.anderson_*) ----------------------
+// Scratch: a ring of K + 1 iterates (n floats each), their lambdas, the weights.
+size_t anderson_bytes(int n, int K);
+// Zeroes the scratch's block counter (before the first extrapolation of a solve).
+cudaError_t anderson_reset(void* buf, int n, int K, cudaStream_t st);
+// Stores iterate x into ring position pos: x = f (mode 0), f + slot->cf (mode 1,
+// the TI fb = f_hat + cf), or f with slot->lam kept alongside (mode 2, G).
+cudaError_t launch_anderson_store(const float* f, int n, int K, int pos, int mode, const Slot* slot, void* buf,
+                                  cudaStream_t st);
+// Replaces f by sum_{k<K} c_k x_{p0+k} (ring positions mod K + 1) and writes it to
+// ring position (p0 + K) mod (K + 1); with slot_g (G) also lambda (slot cf and lam).
+cudaError_t launch_anderson_extrapolate(float* f, int n, int K, int p0, double r, void* buf, Slot* slot_g,
+                                        int* status, cudaStream_t st);
 // Output map Phi (TI) or copy (plain) of iterate in slot `slot`; perm_f / perm_g
 // (nullable) scatter sorted rows back to the caller's order.
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,

@@ -41,7 +41,8 @@ class Problem(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double),
-                ("warm_start", C.c_int32), ("lse_reference", C.c_int32), ("residual_history", C.c_void_p)]
+                ("warm_start", C.c_int32), ("lse_reference", C.c_int32), ("residual_history", C.c_void_p),
+                ("anderson_k", C.c_int32), ("anderson_reg", C.c_double), ("anderson_buf", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -82,6 +83,8 @@ def lib() -> C.CDLL:
         L.uot_dual_value.restype = C.c_int
         L.uot_grad.argtypes = [P, V, V, V, V, V, V, V, S, V]
         L.uot_grad.restype = C.c_int
+        L.uot_anderson_workspace.argtypes = [C.c_int32, C.c_int32]
+        L.uot_anderson_workspace.restype = S
         L.uot_unrolled_workspace_size.argtypes = [P, C.c_int32, C.c_int32]
         L.uot_unrolled_workspace_size.restype = S
         L.uot_grad_unrolled.argtypes = [P, C.c_int32, C.c_int32, V, V, V, V, V, V, S, V]
@@ -231,13 +234,16 @@ LSE_REFERENCE = {"auto": 0, "off": 1, "eager": 2}
 
 def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0, check_every: int = 10,
           f0: torch.Tensor | None = None, history: bool = False, ws: torch.Tensor | None = None,
-          f: torch.Tensor | None = None, g: torch.Tensor | None = None, lse_reference: str = "auto") -> SolveOut:
+          f: torch.Tensor | None = None, g: torch.Tensor | None = None, lse_reference: str = "auto",
+          anderson_k: int = 0, anderson_reg: float = 1e-7) -> SolveOut:
     """Plain ('plain'), translation-invariant ('ti', H-Sinkhorn) or G-Sinkhorn ('g') on the device.
 
     Returns the translated potentials (f, g), the iteration count and the
     fixed-point residual of the returned pair.  `lse_reference` ('auto', 'off',
     'eager') controls the fixed-reference sweeps of the tiled path (same result
-    within rounding, different speed).
+    within rounding, different speed).  anderson_k in 2..6 turns on Anderson
+    extrapolation every anderson_k iterations (regularisation anderson_reg,
+    relative to the trace of the residuals' Gram matrix).
     """
     pr = spec.struct()
     dev = spec.a.device
@@ -248,8 +254,15 @@ def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0
     hist = torch.full((max_iter + 1,), float("nan"), dtype=torch.float32, device=dev) if history else None
     if lse_reference not in LSE_REFERENCE:
         raise ValueError("lse_reference must be 'auto', 'off' or 'eager'")
+    abuf = None
+    if anderson_k:
+        nbytes = int(lib().uot_anderson_workspace(spec.n, int(anderson_k)))
+        if nbytes == 0:
+            raise ValueError("anderson_k must be 0 or 2..6")
+        abuf = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     opt = Options(int(max_iter), int(check_every), float(tol), 1 if f0 is not None else 0,
-                  LSE_REFERENCE[lse_reference], None if hist is None else hist.data_ptr())
+                  LSE_REFERENCE[lse_reference], None if hist is None else hist.data_ptr(),
+                  int(anderson_k), float(anderson_reg), None if abuf is None else abuf.data_ptr())
     res = Result()
     ws = spec.workspace() if ws is None else ws
     if method not in ("ti", "plain", "g"):

@@ -78,6 +78,17 @@ def test_argument_errors_without_device_work(L):
     bad_ref = uot.Options(10, 1, 0.0, 0, 3, None)
     st = L.uot_ti_sinkhorn(C.byref(ok), C.byref(bad_ref), 256, 256, None, 1 << 30, 1 << 40, None)
     assert st == 1 and b"lse_reference" in L.uot_last_error()
+    bad_k = uot.Options(10, 1, 0.0, 0, 0, None, 7, 1e-7, None)
+    st = L.uot_ti_sinkhorn(C.byref(ok), C.byref(bad_k), 256, 256, None, 1 << 30, 1 << 40, None)
+    assert st == 1 and b"anderson_k" in L.uot_last_error()
+    bad_reg = uot.Options(10, 1, 0.0, 0, 0, None, 4, -1.0, 1 << 30)
+    st = L.uot_g_sinkhorn(C.byref(ok), C.byref(bad_reg), 256, 256, None, 1 << 30, 1 << 40, None)
+    assert st == 1 and b"anderson_reg" in L.uot_last_error()
+    no_buf = uot.Options(10, 1, 0.0, 0, 0, None, 4, 1e-7, None)
+    st = L.uot_sinkhorn(C.byref(ok), C.byref(no_buf), 256, 256, None, 1 << 30, 1 << 40, None)
+    assert st == 1 and b"anderson_buf" in L.uot_last_error()
+    assert L.uot_anderson_workspace(100, 4) >= 5 * 100 * 4 and L.uot_anderson_workspace(100, 7) == 0
+    assert L.uot_anderson_workspace(0, 4) == 0
     bad_order = uot.Problem(4, 5, 1, 0, 2.0, 4, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
     assert L.uot_workspace_size(C.byref(bad_order)) == 0 and b"ordering" in L.uot_last_error()
     st = L.uot_softmin(C.byref(ok), 3, 256, 256, 256, 1 << 30, None)
