@@ -1,0 +1,372 @@
+// Softmin sweep for high-dimensional point clouds (dim >= 32, p = 2) on the
+// fifth-generation tensor cores (tcgen05, accumulators in TMEM):
+//
+//   t_ij = h_j - s |x_i - y_j|^2 = H_j + R_i + 2 s x'_i . y'_j,
+//   x' = x - c, y' = y - c (c the clouds' common centre),
+//   H_j = h_j - s |y'_j|^2,  R_i = -s |x'_i|^2,
+//
+// with the dot products x'.y' a dense (rows x dim) x (dim x keys)
+// contraction.  Each coordinate is split into TF32 parts hi + lo and the
+// product is hi.hi + lo.hi + hi.lo (three kind::tf32 MMA passes, about FP32
+// accuracy).  The split operands of both clouds are built once per call in
+// the canonical K-major layout (8-row x 16-byte core matrices, no swizzle),
+// so that a tile of 8k rows is one contiguous block: a CTA copies its 128
+// query rows and each 128-key tile into shared memory with bulk asynchronous
+// copies completing on mbarriers (two key stages); one lane issues
+// the MMAs of a tile into a ring of four TMEM accumulators while eight consumer
+// warps read the earlier ones (two threads per row, one per column half; tcgen05.ld),
+// add H_j and keep a running (max, sum of 2^(t - max)) per row.  Output: the
+// (max + R_i, sum) partials per (row, key chunk) of the other sweeps.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "sweep_common.cuh"
+#include "tc_ptx.cuh"
+#include "uot_internal.cuh"
+
+namespace uot {
+namespace {
+
+using namespace simd;
+
+constexpr int kRows = 128;                    // MMA M
+constexpr int kKeys = 128;                    // MMA N (keys per tile)
+constexpr int kStages = 2;                    // key-tile buffers
+constexpr int kAccCols = kKeys;               // TMEM columns per accumulator (N fp32)
+constexpr int kAcc = 4;                       // accumulators in TMEM (a ring)
+constexpr int kTmemCols = kAcc * kAccCols;
+constexpr int kMaxChunk = 4096;               // keys per CTA (H_j kept in shared memory)
+constexpr long long kSpin = 1LL << 24;        // mbarrier polls before giving up
+constexpr uint32_t kIdesc = tc::idesc_tf32(kRows, kKeys);
+constexpr uint32_t kPiece = 16384;            // bytes per bulk copy
+
+__device__ __forceinline__ float tf32r(float x) { return tc::to_tf32(x); }
+
+// Operand matrix of one cloud: row r, split coordinates of r - c as
+// [hi (dim8) | lo (dim8)] in the canonical K-major layout, KA = 2 dim8 values a
+// row, rows padded with zeros to a multiple of 128; norm2[r] = |x'_r|^2.
+__global__ void k_umma_operand(const float* __restrict__ pts, int n, int npad, int dim, int dim8,
+                               const float* __restrict__ center, float* __restrict__ op, float* __restrict__ norm2) {
+  const int KA = 2 * dim8;
+  const int sbo = KA * 32;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < npad; r += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int d0 = 0; d0 < dim8; d0 += 4) {
+      float hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int d = d0 + e;
+        const float v = (r < n && d < dim) ? pts[(size_t)r * dim + d] - center[d] : 0.f;
+        hi[e] = tf32r(v);
+        lo[e] = tf32r(v - hi[e]);
+        const float w = hi[e] + lo[e];
+        acc = fmaf(w, w, acc);
+      }
+      char* base = reinterpret_cast<char*>(op);
+      *reinterpret_cast<float4*>(base + tc::kmajor_offset(r, d0, sbo)) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<float4*>(base + tc::kmajor_offset(r, dim8 + d0, sbo)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    if (r < n) norm2[r] = acc;
+  }
+}
+
+struct Bars {
+  uint64_t a_full;
+  uint64_t b_full[kStages];   // key stage landed (bulk copies)
+  uint64_t m_done[kAcc];      // the MMAs of an accumulator completed
+  uint64_t empty[kAcc];       // the 8 consumer warps read an accumulator
+  uint32_t tmem;
+  int err;
+  float hm[kRows];            // second column half's (max, sum) per row
+  float hs[kRows];
+};
+
+__device__ __forceinline__ void copy_pieces(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  tc::mbar_arrive_expect_tx(bar, bytes);
+  for (uint32_t o = 0; o < bytes; o += kPiece) {
+    const uint32_t len = bytes - o < kPiece ? bytes - o : kPiece;
+    tc::bulk_g2s(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o, len, bar);
+  }
+}
+
+// Roles: warps 0..7 read the accumulators (warp w: TMEM lane quarter w % 4,
+// i.e. rows 32 (w % 4) .. + 31, and column half w / 4 of every tile); lane 0
+// of warp 8 issues the copies and the MMAs.  Handoffs: b_full (copies ->
+// issuer), m_done (MMAs -> consumers and the issuer, which then reuses the key
+// stage), empty (consumers -> issuer, accumulator free again).  Every wait is
+// bounded; a wait that gives up sets err, which stops every role, and the
+// issuer then lets every copy and MMA in flight land before the CTA ends.
+constexpr int kConsWarps = 8;
+constexpr int kAllThreads = 32 * (kConsWarps + 1);
+
+// grid: (row blocks of 128, key chunks of kps keys, kps a multiple of 64 and <= kMaxChunk);
+// KS = dim8 / 8 MMA K-steps per pass
+template <int KS>
+__global__ void __launch_bounds__(kAllThreads, 1)
+k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int nq, const float* __restrict__ opk,
+             const float* __restrict__ nk2, int nk, const float* __restrict__ l2w, const float* __restrict__ pot,
+             const double* __restrict__ shift, double s, int kps, float* __restrict__ part) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  constexpr int dim8 = 8 * KS;
+  constexpr int KA = 2 * dim8;
+  const uint32_t sbo = (uint32_t)KA * 32u;
+  const uint32_t bytesA = 16u * sbo, bytesB = (uint32_t)(kKeys / 8) * sbo;
+  float* A = reinterpret_cast<float*>(smraw);
+  float* B = reinterpret_cast<float*>(smraw + bytesA);  // [kStages][kKeys x KA]
+  float* Hs = reinterpret_cast<float*>(smraw + bytesA + kStages * bytesB);
+  Bars& br = *reinterpret_cast<Bars*>(smraw + bytesA + kStages * bytesB + sizeof(float) * kMaxChunk);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rb = blockIdx.x, split = blockIdx.y;
+  const int j0 = split * kps, j1 = min(nk, j0 + kps);
+  const int T = (j1 - j0 + kKeys - 1) / kKeys;
+  const float s2 = (float)(2.0 * s);
+  const double sh = shift ? *shift : 0.0;
+  const int tile0 = j0 / kKeys;
+
+  if (warp == 0) tc::tmem_alloc(&br.tmem, kTmemCols);
+  if (tid == 32 * kConsWarps) {
+    tc::mbar_init(&br.a_full, 1);
+    for (int b = 0; b < kStages; ++b) tc::mbar_init(&br.b_full[b], 1);
+    for (int b = 0; b < kAcc; ++b) {
+      tc::mbar_init(&br.m_done[b], 1);
+      tc::mbar_init(&br.empty[b], kConsWarps);
+    }
+    tc::fence_mbar_init();
+    br.err = 0;
+    copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb * bytesA, bytesA, &br.a_full);
+    for (int t = 0; t < T && t < kStages; ++t)
+      copy_pieces(reinterpret_cast<char*>(B) + (size_t)t * bytesB,
+                  reinterpret_cast<const char*>(opk) + (size_t)(tile0 + t) * bytesB, bytesB, &br.b_full[t]);
+  }
+  // key constants H_j = h_j - s |y'_j|^2 of this chunk (zero-weight and padding keys: kZeroW)
+  for (int u = tid; u < T * kKeys; u += kAllThreads) {
+    const int j = j0 + u;
+    float H = kZeroW;
+    if (j < j1) {
+      const float lw = l2w[j];
+      if (lw > 0.5f * kZeroW) {
+        const double pj = pot ? (double)pot[j] : 0.0;
+        H = (float)((double)lw + s * (pj + sh) - s * (double)nk2[j]);
+      }
+    }
+    Hs[u] = H;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = br.tmem;
+  volatile int* err = &br.err;
+
+  if (warp == kConsWarps) {
+    // ------------------------------------------------------------------ issuer
+    if (lane == 0) {
+      int armed[kStages] = {}, used[kStages] = {};
+      for (int t = 0; t < T && t < kStages; ++t) armed[t] = 1;
+      bool a_done = false;
+      int committed = -1, reused = -1;  // tiles committed; MMAs of tiles <= reused known complete
+      // descriptors: one K-step (two 16-byte core-matrix columns, 256 bytes) adds 16 to the start field
+      const uint64_t dAh = tc::smem_desc(tc::smem_addr(A), 128, sbo);
+      const uint64_t dAl = dAh + (uint64_t)(KS * 16);
+      for (int t = 0; t < T && !*err; ++t) {
+        const int st = t % kStages, b = t % kAcc;
+        bool ok = true;
+        if (!a_done) ok = a_done = tc::mbar_wait(&br.a_full, 0, kSpin);
+        ok = ok && tc::mbar_wait(&br.b_full[st], (uint32_t)((t / kStages) & 1), kSpin);
+        if (ok) ++used[st];
+        // accumulator b was last read for tile t - kAcc
+        ok = ok && (t < kAcc || tc::mbar_wait(&br.empty[b], (uint32_t)(((t - kAcc) / kAcc) & 1), kSpin));
+        if (!ok) { *err = 1; break; }
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(b * kAccCols);
+        const uint64_t dBh = tc::smem_desc(tc::smem_addr(reinterpret_cast<char*>(B) + (size_t)st * bytesB), 128, sbo);
+        const uint64_t dBl = dBh + (uint64_t)(KS * 16);
+        // hi.hi, then lo.hi (lo parts of x), then hi.lo (lo parts of y)
+#pragma unroll
+        for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAh + 16 * k, dBh + 16 * k, kIdesc, k > 0);
+#pragma unroll
+        for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAl + 16 * k, dBh + 16 * k, kIdesc, true);
+#pragma unroll
+        for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAh + 16 * k, dBl + 16 * k, kIdesc, true);
+        tc::commit(&br.m_done[b]);
+        committed = t;
+        // key stage of tile t - 1 -> tile t - 1 + kStages, once the MMAs of tile t - 1 completed
+        if (t >= 1 && t - 1 + kStages < T) {
+          if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), kSpin)) { *err = 1; break; }
+          reused = t - 1;
+          const int rs = (t - 1) % kStages;
+          copy_pieces(reinterpret_cast<char*>(B) + (size_t)rs * bytesB,
+                      reinterpret_cast<const char*>(opk) + (size_t)(tile0 + t - 1 + kStages) * bytesB, bytesB,
+                      &br.b_full[rs]);
+          ++armed[rs];
+        }
+      }
+      if (*err) {
+        // drain: copies armed but never consumed, MMAs committed but never seen complete (bounded)
+        if (!a_done) (void)tc::mbar_wait(&br.a_full, 0, kSpin);
+        for (int st = 0; st < kStages; ++st)
+          for (; used[st] < armed[st]; ++used[st])
+            (void)tc::mbar_wait(&br.b_full[st], (uint32_t)(used[st] & 1), kSpin);
+        for (int t = reused + 1; t <= committed; ++t) {
+          // only the most recent commit of each accumulator: wait for that phase
+          if (t + kAcc <= committed) continue;
+          (void)tc::mbar_wait(&br.m_done[t % kAcc], (uint32_t)((t / kAcc) & 1), kSpin);
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // --------------------------------------------------------------- consumers
+    const int q = warp & 3, h = warp >> 2;
+    const int row = 32 * q + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((kKeys / 2) * h);
+    float M = kInitMax, S = 0.f;
+    for (int t = 0; t < T; ++t) {
+      const int b = t % kAcc;
+      bool done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), kSpin);
+      done = __all_sync(0xffffffffu, done);  // tcgen05.ld is warp-wide
+      if (!done) {
+        if (lane == 0) *err = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      float v[kKeys / 2];
+      tc::ld64(tl + (uint32_t)(b * kAccCols), v);
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&br.empty[b]);
+      const float* H = Hs + t * kKeys + (kKeys / 2) * h;
+#pragma unroll
+      for (int c0 = 0; c0 < kKeys / 2; c0 += 32) {
+        float* vv = v + c0;
+        const float* HH = H + c0;
+#pragma unroll
+        for (int e = 0; e < 32; e += 4) {
+          const float4 hv = *reinterpret_cast<const float4*>(HH + e);
+          vv[e] = fmaf(s2, vv[e], hv.x);
+          vv[e + 1] = fmaf(s2, vv[e + 1], hv.y);
+          vv[e + 2] = fmaf(s2, vv[e + 2], hv.z);
+          vv[e + 3] = fmaf(s2, vv[e + 3], hv.w);
+        }
+        float cm = vv[0];
+#pragma unroll
+        for (int e = 1; e < 31; e += 2) cm = max3f(cm, vv[e], vv[e + 1]);
+        cm = fmaxf(cm, vv[31]);
+        const float mn = fmaxf(M, cm);
+        const u64 nm = pk(-mn, -mn);
+        u64 a2[4] = {pk(0.f, 0.f), pk(0.f, 0.f), pk(0.f, 0.f), pk(0.f, 0.f)};
+#pragma unroll
+        for (int e = 0; e < 32; e += 2) {
+          float w0, w1;
+          upk(add2(pk(vv[e], vv[e + 1]), nm), w0, w1);
+          a2[(e >> 1) & 3] = add2(a2[(e >> 1) & 3], pk(ex2f(w0), ex2f(w1)));
+        }
+        float s0, s1;
+        upk(add2(add2(a2[0], a2[1]), add2(a2[2], a2[3])), s0, s1);
+        S = S * ex2f(M - mn) + (s0 + s1);
+        M = mn;
+      }
+    }
+    if (h == 1) {
+      br.hm[row] = M;
+      br.hs[row] = S;
+    }
+    // the two column halves of a row meet below
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsWarps) : "memory");
+    if (h == 0) {
+      const float M2 = br.hm[row], S2 = br.hs[row];
+      const float mn = fmaxf(M, M2);
+      const float St = S * ex2f(M - mn) + S2 * ex2f(M2 - mn);
+      const int i = rb * kRows + row;
+      if (i < nq) {
+        float* base = part + (size_t)split * 2 * nq;
+        const bool bad = *err != 0;
+        base[i] = bad ? __int_as_float(0x7fc00000) : mn - (float)s * nq2[i];
+        base[(size_t)nq + i] = bad ? __int_as_float(0x7fc00000) : St;
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+size_t umma_smem_bytes(int dim8) {
+  const size_t KA = 2 * (size_t)dim8;
+  return 16 * KA * 32 + kStages * (kKeys / 8) * KA * 32 + sizeof(float) * kMaxChunk + sizeof(Bars);
+}
+
+template <int KS>
+cudaError_t run_umma(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
+                     const float* l2w, const float* pot, const double* shift, double s, float* part,
+                     const SweepGeom& g, cudaStream_t st) {
+  const size_t smem = umma_smem_bytes(8 * KS);
+  static std::mutex mu;
+  static bool attr = false;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_sweep_umma<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+  }
+  dim3 grid(g.row_blocks, g.splits);
+  k_sweep_umma<KS><<<grid, kAllThreads, smem, st>>>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, g.keys_per_split,
+                                                    part);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int umma_dim8(int dim) { return (dim + 7) & ~7; }
+
+size_t umma_operand_floats(int n, int dim) {
+  const size_t npad = ((size_t)n + kRows - 1) / kRows * kRows;
+  return npad * 2 * (size_t)umma_dim8(dim);
+}
+
+cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, float* op, float* norm2,
+                                cudaStream_t st) {
+  const int npad = (n + kRows - 1) / kRows * kRows;
+  const int blocks = (npad + 255) / 256;
+  k_umma_operand<<<blocks, 256, 0, st>>>(pts, n, npad, dim, umma_dim8(dim), center, op, norm2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+SweepGeom umma_geom(int nq, int nk) {
+  SweepGeom g{};
+  g.threads = kAllThreads;
+  g.rows = 1;
+  g.row_blocks = (nq + kRows - 1) / kRows;
+  const int sms = device_sm_count();
+  const int tiles = (nk + kKeys - 1) / kKeys;
+  // one CTA per SM: as many key chunks as keep the row blocks x chunks within one wave,
+  // and at most kMaxChunk keys a chunk
+  int splits = sms / g.row_blocks;
+  if (splits < 1) splits = 1;
+  const int min_splits = (nk + kMaxChunk - 1) / kMaxChunk;
+  if (splits < min_splits) splits = min_splits;
+  if (splits > tiles) splits = tiles;
+  const int tiles_per = (tiles + splits - 1) / splits;
+  g.keys_per_split = tiles_per * kKeys;
+  g.splits = (nk + g.keys_per_split - 1) / g.keys_per_split;
+  return g;
+}
+
+cudaError_t launch_umma_sweep(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
+                              int dim, const float* l2w, const float* pot, const double* shift, double s, float* part,
+                              const SweepGeom& g, cudaStream_t st) {
+  const int dim8 = umma_dim8(dim);
+  switch (dim8 / 8) {
+    case 4: return run_umma<4>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
+    case 5: return run_umma<5>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
+    case 6: return run_umma<6>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
+    case 7: return run_umma<7>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
+    default: return run_umma<8>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
+  }
+}
+
+}  // namespace uot

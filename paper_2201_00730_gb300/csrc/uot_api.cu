@@ -99,8 +99,8 @@ PartSizes part_sizes(const uot_problem& p) {
       upd(ps.cols, (size_t)tc_geom(p.m, p.n, p.dim).splits * 2 * p.m);
     }
     if (mma_path(p)) {
-      upd(ps.rows, (size_t)mma_geom(p.n, p.m).splits * 2 * p.n);
-      upd(ps.cols, (size_t)mma_geom(p.m, p.n).splits * 2 * p.m);
+      upd(ps.rows, (size_t)umma_geom(p.n, p.m).splits * 2 * p.n);
+      upd(ps.cols, (size_t)umma_geom(p.m, p.n).splits * 2 * p.m);
       upd(ps.rows, (size_t)flash_geom(p.n, p.m).splits * (2 + p.dim) * p.n);
       upd(ps.cols, (size_t)flash_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
     }
@@ -115,6 +115,7 @@ PartSizes part_sizes(const uot_problem& p) {
 
 struct WsLayout {
   size_t state, ln_a, ln_b, l2_a, l2_b, lo_a, lo_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc, center;
+  size_t op_x, op_y, n2_x, n2_y;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
   size_t sort_tmp_bytes, total;
@@ -140,6 +141,12 @@ WsLayout ws_layout(const uot_problem& p) {
   L.blk = take(sizeof(double) * kMaxBlocks * 10);
   L.rbc = take(sizeof(unsigned int) * kMaxBlocks);
   L.center = take(sizeof(float) * 64);
+  if (mma_path(p)) {
+    L.op_x = take(sizeof(float) * umma_operand_floats(p.n, p.dim));
+    L.op_y = take(sizeof(float) * umma_operand_floats(p.m, p.dim));
+    L.n2_x = take(sizeof(float) * p.n);
+    L.n2_y = take(sizeof(float) * p.m);
+  }
   if (tiled_path(p)) {
     const int nmax = p.n > p.m ? p.n : p.m;
     L.perm_x = take(sizeof(int) * p.n);
@@ -171,6 +178,7 @@ struct Ctx {
   float *l2_a, *l2_b, *lo_a, *lo_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;  // lo_*: log2 w - l2_*
   unsigned int* rbc;  // per-row-block counters of the fused sweeps
   float* center;      // common centre of the clouds (tensor-core path)
+  float *op_x, *op_y, *n2_x, *n2_y;  // tcgen05 operands and squared norms (dim >= 32)
   cudaStream_t st;
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
@@ -218,6 +226,13 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->blk = reinterpret_cast<double*>(b + L.blk);
   c->rbc = reinterpret_cast<unsigned int*>(b + L.rbc);
   c->center = reinterpret_cast<float*>(b + L.center);
+  c->op_x = c->op_y = c->n2_x = c->n2_y = nullptr;
+  if (mma_path(*prob)) {
+    c->op_x = reinterpret_cast<float*>(b + L.op_x);
+    c->op_y = reinterpret_cast<float*>(b + L.op_y);
+    c->n2_x = reinterpret_cast<float*>(b + L.n2_x);
+    c->n2_y = reinterpret_cast<float*>(b + L.n2_y);
+  }
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
@@ -259,7 +274,11 @@ uot_status prepare(Ctx& c) {
     UOT_CUDA(launch_order_points(c.p.x, c.p.a, c.p.n, c.p.dim, c.osc, c.perm_x, c.xs, c.as, c.cen_x, c.st));
     UOT_CUDA(launch_order_points(c.p.y, c.p.b, c.p.m, c.p.dim, c.osc, c.perm_y, c.ys, c.bs, c.cen_y, c.st));
   }
-  if (mma_path(c.p)) UOT_CUDA(launch_center(c.p.x, c.p.n, c.p.y, c.p.m, c.p.dim, c.center, c.st));
+  if (mma_path(c.p)) {
+    UOT_CUDA(launch_center(c.p.x, c.p.n, c.p.y, c.p.m, c.p.dim, c.center, c.st));
+    UOT_CUDA(launch_umma_operand(c.p.x, c.p.n, c.p.dim, c.center, c.op_x, c.n2_x, c.st));
+    UOT_CUDA(launch_umma_operand(c.p.y, c.p.m, c.p.dim, c.center, c.op_y, c.n2_y, c.st));
+  }
   UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, c.lo_a, &c.state->status, c.st));
   UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, c.lo_b, &c.state->status, c.st));
   return UOT_OK;
@@ -336,9 +355,11 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       UOT_CUDA(launch_tile_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, shift, c.s, part, g, epi,
                                  c.st));
     } else if (mma_path(p) && !moments) {
-      SweepGeom g = mma_geom(q.n, k.n);
+      SweepGeom g = umma_geom(q.n, k.n);
       *splits = g.splits;
-      UOT_CUDA(launch_mma_sweep(q, k, p.dim, c.center, pot, shift, c.s, part, g, c.st));
+      UOT_CUDA(launch_umma_sweep(axis == 0 ? c.op_x : c.op_y, axis == 0 ? c.n2_x : c.n2_y, q.n,
+                                 axis == 0 ? c.op_y : c.op_x, axis == 0 ? c.n2_y : c.n2_x, k.n, p.dim, k.l2w, pot,
+                                 shift, c.s, part, g, c.st));
     } else if (mma_path(p)) {
       // gradient sweep with moments: dC/dx = 2 (x - y)
       SweepGeom g = flash_geom(q.n, k.n);

@@ -167,6 +167,17 @@ cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, 
                                const float* l2w, const float* pot, const double* shift, const float* zrow,
                                const float* hk, const float* mk, double s, float momscale, float* part,
                                const SweepGeom& g, cudaStream_t st);
+// tcgen05 sweep (dim >= 32, p = 2): the operand matrices of both clouds (split
+// TF32 coordinates relative to the common centre, canonical K-major layout,
+// rows padded to 128) and their squared norms, built once per call.
+int umma_dim8(int dim);
+size_t umma_operand_floats(int n, int dim);
+cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, float* op, float* norm2,
+                                cudaStream_t st);
+SweepGeom umma_geom(int nq, int nk);
+cudaError_t launch_umma_sweep(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
+                              int dim, const float* l2w, const float* pot, const double* shift, double s, float* part,
+                              const SweepGeom& g, cudaStream_t st);
 // Tensor-core sweep (dim >= 32, p = 2): centre = common centre of the clouds (dim floats).
 cudaError_t launch_mma_sweep(const SideDesc& q, const SideDesc& k, int dim, const float* center, const float* pot_k,
                              const double* shift_k, double s, float* part, const SweepGeom& g, cudaStream_t st);
