@@ -1,17 +1,15 @@
-// Softmin sweep for high-dimensional point clouds (dim >= 32, p = 2) with the
-// cross term on the tensor cores.
+// Gradient and adjoint sweeps for high-dimensional point clouds (dim >= 32,
+// p = 2) with the contractions on mma.sync tensor-core fragments (the
+// non-moment sweeps run on tcgen05, sweep_umma.cu):
 //
 //   t_ij = h_j - s |x_i - y_j|^2 = (h_j - s |y_j|^2) + (-s |x_i|^2) + 2 s x_i . y_j
 //
 // (coordinates taken relative to a common centre c, so the two squared norms
-// stay small).  The dot products x_i . y_j form a dense (rows x dim) x (dim x
-// keys) contraction evaluated with mma.sync m16n8k8 TF32 in three passes
-// (hi.hi + hi.lo + lo.hi with x = hi + lo, hi = tf32(x)), which keeps the
-// product at about FP32 accuracy (one TF32 pass would cost ~1e-3 relative).
-// The online log-sum-exp runs on the accumulator fragments in registers, as in
-// fused attention kernels: per 64-key tile a row max over the quad of threads
-// sharing a row, one ex2 per entry, and the running (max, sum) per row.
-// Output: (max, sum) partials per (row, key chunk) like the other sweeps.
+// stay small).  The dot products x_i . y_j are evaluated with mma.sync
+// m16n8k8 TF32 in three passes (hi.hi + hi.lo + lo.hi with x = hi + lo,
+// hi = tf32(x)), which keeps the product at about FP32 accuracy (one TF32
+// pass would cost ~1e-3 relative), with the online log-sum-exp on the
+// accumulator fragments in registers as in fused attention kernels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,144 +50,6 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1
       "{%0,%1,%2,%3};"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// grid: (row blocks of 128, key chunks).  dim8 = dim rounded up to a multiple of 8.
-__global__ void __launch_bounds__(kThreads)
-k_sweep_mma(const float* __restrict__ q, int nq, const float* __restrict__ kp, int nk, int dim,
-            const float* __restrict__ center, const float* __restrict__ l2w, const float* __restrict__ pot,
-            const double* __restrict__ shift, double s, int kps, float* __restrict__ part) {
-  extern __shared__ uint32_t smem[];
-  uint32_t* khi = smem;                      // [kKeys][kLd]
-  uint32_t* klo = khi + kKeys * kLd;         // [kKeys][kLd]
-  float* kH = reinterpret_cast<float*>(klo + kKeys * kLd);  // [kKeys]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tg = lane & 3;
-  const int split = blockIdx.y;
-  const int j0 = split * kps, j1 = min(nk, j0 + kps);
-  const int dim8 = (dim + 7) & ~7;
-  const double sh = shift ? *shift : 0.0;
-  const float sf = (float)s, s2 = (float)(2.0 * s);
-
-  // ---- query fragments (kept in registers): rows r0 = 128*bx + 16*warp + g and r0 + 8
-  const int rbase = blockIdx.x * kRows + warp * 16;
-  const int rA = rbase + g, rB = rbase + g + 8;
-  uint32_t ahi[kDMax / 8][4], alo[kDMax / 8][4];
-  float qn[2] = {0.f, 0.f};  // |x - c|^2 of rows rA, rB (partial over this thread's columns)
-#pragma unroll
-  for (int ks = 0; ks < kDMax / 8; ++ks) {
-    if (ks * 8 < dim8) {
-      const int c0 = ks * 8 + tg, c1 = ks * 8 + tg + 4;
-      float v[4];
-      v[0] = (rA < nq && c0 < dim) ? q[(size_t)rA * dim + c0] - center[c0] : 0.f;
-      v[1] = (rB < nq && c0 < dim) ? q[(size_t)rB * dim + c0] - center[c0] : 0.f;
-      v[2] = (rA < nq && c1 < dim) ? q[(size_t)rA * dim + c1] - center[c1] : 0.f;
-      v[3] = (rB < nq && c1 < dim) ? q[(size_t)rB * dim + c1] - center[c1] : 0.f;
-      qn[0] = fmaf(v[0], v[0], fmaf(v[2], v[2], qn[0]));
-      qn[1] = fmaf(v[1], v[1], fmaf(v[3], v[3], qn[1]));
-#pragma unroll
-      for (int e = 0; e < 4; ++e) split_tf32(v[e], ahi[ks][e], alo[ks][e]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { ahi[ks][e] = 0u; alo[ks][e] = 0u; }
-    }
-  }
-  // the quad (tg = 0..3) holds the whole row: sum its parts
-  qn[0] += __shfl_xor_sync(0xffffffffu, qn[0], 1);
-  qn[0] += __shfl_xor_sync(0xffffffffu, qn[0], 2);
-  qn[1] += __shfl_xor_sync(0xffffffffu, qn[1], 1);
-  qn[1] += __shfl_xor_sync(0xffffffffu, qn[1], 2);
-  const float Rr[2] = {-sf * qn[0], -sf * qn[1]};  // row constants, added at the merge
-  float mu[2] = {kInitMax, kInitMax}, acc[2] = {0.f, 0.f};
-
-  for (int jt = j0; jt < j1; jt += kKeys) {
-    const int cnt = min(kKeys, j1 - jt);
-    __syncthreads();
-    // stage the key tile: TF32 hi/lo coordinates relative to c, and H_j = h_j - s |y_j - c|^2
-    for (int e = threadIdx.x; e < kKeys * dim8; e += kThreads) {
-      const int u = e / dim8, d = e - u * dim8;
-      float v = 0.f;
-      if (u < cnt && d < dim) v = kp[(size_t)(jt + u) * dim + d] - center[d];
-      uint32_t hi, lo;
-      split_tf32(v, hi, lo);
-      khi[u * kLd + d] = hi;
-      klo[u * kLd + d] = lo;
-    }
-    __syncthreads();
-    if (threadIdx.x < kKeys) {
-      // H_j = h_j - s |y_j - c|^2, with |y_j - c|^2 summed from the staged hi + lo parts
-      const int u = threadIdx.x;
-      float H = kZeroW;
-      if (u < cnt) {
-        const int j = jt + u;
-        const float lw = l2w[j];
-        if (lw > 0.5f * kZeroW) {
-          float y2 = 0.f;
-#pragma unroll 8
-          for (int d = 0; d < dim8; ++d) {
-            const float v = __uint_as_float(khi[u * kLd + d]) + __uint_as_float(klo[u * kLd + d]);
-            y2 = fmaf(v, v, y2);
-          }
-          const double pj = pot ? (double)pot[j] : 0.0;
-          H = (float)((double)lw + s * (pj + sh) - s * (double)y2);
-        }
-      }
-      kH[u] = H;
-    }
-    __syncthreads();
-    // dot products: 16 rows x 64 keys per warp, 8 n-blocks of 8 keys
-    float c[kKeys / 8][4];
-#pragma unroll
-    for (int nb = 0; nb < kKeys / 8; ++nb) {
-      c[nb][0] = c[nb][1] = c[nb][2] = c[nb][3] = 0.f;
-#pragma unroll
-      for (int ks = 0; ks < kDMax / 8; ++ks) {
-        if (ks * 8 < dim8) {
-          const int key = nb * 8 + g;
-          const uint32_t bh0 = khi[key * kLd + ks * 8 + tg], bh1 = khi[key * kLd + ks * 8 + tg + 4];
-          const uint32_t bl0 = klo[key * kLd + ks * 8 + tg], bl1 = klo[key * kLd + ks * 8 + tg + 4];
-          mma_tf32(c[nb], alo[ks][0], alo[ks][1], alo[ks][2], alo[ks][3], bh0, bh1);
-          mma_tf32(c[nb], ahi[ks][0], ahi[ks][1], ahi[ks][2], ahi[ks][3], bl0, bl1);
-          mma_tf32(c[nb], ahi[ks][0], ahi[ks][1], ahi[ks][2], ahi[ks][3], bh0, bh1);
-        }
-      }
-    }
-    // u = H_j + 2 s x.y for the thread's entries; rows A (c[.][0..1]) and B (c[.][2..3])
-    float tmA = kInitMax, tmB = kInitMax;
-#pragma unroll
-    for (int nb = 0; nb < kKeys / 8; ++nb) {
-      const float H0 = kH[nb * 8 + 2 * tg], H1 = kH[nb * 8 + 2 * tg + 1];
-      c[nb][0] = fmaf(s2, c[nb][0], H0);
-      c[nb][1] = fmaf(s2, c[nb][1], H1);
-      c[nb][2] = fmaf(s2, c[nb][2], H0);
-      c[nb][3] = fmaf(s2, c[nb][3], H1);
-      tmA = fmaxf(tmA, fmaxf(c[nb][0], c[nb][1]));
-      tmB = fmaxf(tmB, fmaxf(c[nb][2], c[nb][3]));
-    }
-    tmA = fmaxf(tmA, __shfl_xor_sync(0xffffffffu, tmA, 1));
-    tmA = fmaxf(tmA, __shfl_xor_sync(0xffffffffu, tmA, 2));
-    tmB = fmaxf(tmB, __shfl_xor_sync(0xffffffffu, tmB, 1));
-    tmB = fmaxf(tmB, __shfl_xor_sync(0xffffffffu, tmB, 2));
-    const float mA = fmaxf(mu[0], tmA), mB = fmaxf(mu[1], tmB);
-    float sA = acc[0] * ex2f(mu[0] - mA), sB = acc[1] * ex2f(mu[1] - mB);
-#pragma unroll
-    for (int nb = 0; nb < kKeys / 8; ++nb) {
-      sA += ex2f(c[nb][0] - mA) + ex2f(c[nb][1] - mA);
-      sB += ex2f(c[nb][2] - mB) + ex2f(c[nb][3] - mB);
-    }
-    mu[0] = mA; mu[1] = mB;
-    acc[0] = sA; acc[1] = sB;
-  }
-  // combine the quad's partial sums (same max in the quad) and write (max + R_i, sum)
-  acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-  acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
-  acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], 1);
-  acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], 2);
-  if (tg == 0) {
-    float* base = part + (size_t)split * 2 * nq;
-    if (rA < nq) { base[rA] = mu[0] + Rr[0]; base[(size_t)nq + rA] = acc[0]; }
-    if (rB < nq) { base[rB] = mu[1] + Rr[1]; base[(size_t)nq + rB] = acc[1]; }
-  }
 }
 
 // Softmin sweep with moments on the tensor cores (dim >= 32, p = 2): the
@@ -408,43 +268,9 @@ __global__ void k_center(const float* x, int n, const float* y, int m, int dim, 
   if (threadIdx.x == 0) center[d] = (float)(sh[0] / (double)(n + m));
 }
 
-size_t mma_smem_bytes() { return sizeof(uint32_t) * 2 * kKeys * kLd + sizeof(float) * kKeys; }
 size_t flash_smem_bytes() { return sizeof(uint32_t) * 2 * kKeys * kLd + sizeof(float) * 2 * kKeys; }
 
 }  // namespace
-
-SweepGeom mma_geom(int nq, int nk) {
-  SweepGeom g{};
-  g.threads = kThreads;
-  g.rows = 1;
-  g.row_blocks = (nq + kRows - 1) / kRows;
-  static int occ = 0;
-  if (occ == 0) {
-    int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sweep_mma, kThreads, (int)mma_smem_bytes()) !=
-            cudaSuccess || v < 1)
-      v = 2;
-    occ = v;
-  }
-  const long long target = (long long)device_sm_count() * occ;
-  const int max_tiles = (nk + kKeys - 1) / kKeys;
-  // key chunks minimising (waves of CTAs) x (tiles per CTA + one tile of fixed cost)
-  double best = 1e300;
-  int best_k = 1;
-  for (int k = 1; k <= 256 && k <= max_tiles; ++k) {
-    const int tiles_per = (max_tiles + k - 1) / k;
-    const int kk = (max_tiles + tiles_per - 1) / tiles_per;
-    if (kk != k) continue;
-    const long long ctas = (long long)g.row_blocks * kk;
-    const long long waves = (ctas + target - 1) / target;
-    const double est = (double)waves * (tiles_per + 1.0);
-    if (est < best * 0.999) { best = est; best_k = kk; }
-  }
-  const int tiles_per = (max_tiles + best_k - 1) / best_k;
-  g.keys_per_split = tiles_per * kKeys;
-  g.splits = (nk + g.keys_per_split - 1) / g.keys_per_split;
-  return g;
-}
 
 cudaError_t launch_center(const float* x, int n, const float* y, int m, int dim, float* center, cudaStream_t st) {
   k_center<<<dim, 256, 0, st>>>(x, n, y, m, dim, center);
@@ -492,22 +318,6 @@ cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, 
   dim3 grid(g.row_blocks, g.splits);
   k_sweep_flash<<<grid, kThreads, smem, st>>>(q, nq, kp, nk, dim, center, l2w, pot, shift, zrow, hk, mk, s, momscale,
                                               g.keys_per_split, part);
-  note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mma_sweep(const SideDesc& q, const SideDesc& k, int dim, const float* center, const float* pot_k,
-                             const double* shift_k, double s, float* part, const SweepGeom& g, cudaStream_t st) {
-  static bool attr_set = false;
-  const size_t smem = mma_smem_bytes();
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  dim3 grid(g.row_blocks, g.splits);
-  k_sweep_mma<<<grid, kThreads, smem, st>>>(q.pts, q.n, k.pts, k.n, dim, center, k.l2w, pot_k, shift_k, s,
-                                            g.keys_per_split, part);
   note_launch();
   return cudaGetLastError();
 }

@@ -92,7 +92,6 @@ constexpr int kTileKeys = 128;  // keys per local-frame tile of the tiled sweep
 inline bool mma_path(const uot_problem& p) {
   return p.cost_kind == UOT_COST_POINTS && p.dim >= 32 && p.p == 2.0f;
 }
-SweepGeom mma_geom(int nq, int nk);
 cudaError_t launch_center(const float* x, int n, const float* y, int m, int dim, float* center, cudaStream_t st);
 
 // True when the tiled (Morton-ordered, local-frame) sweep serves this problem.
@@ -178,9 +177,6 @@ SweepGeom umma_geom(int nq, int nk);
 cudaError_t launch_umma_sweep(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
                               int dim, const float* l2w, const float* pot, const double* shift, double s, float* part,
                               const SweepGeom& g, cudaStream_t st);
-// Tensor-core sweep (dim >= 32, p = 2): centre = common centre of the clouds (dim floats).
-cudaError_t launch_mma_sweep(const SideDesc& q, const SideDesc& k, int dim, const float* center, const float* pot_k,
-                             const double* shift_k, double s, float* part, const SweepGeom& g, cudaStream_t st);
 // Dense cost: axis 0 = rows of C are queries, axis 1 = columns of C are queries.
 cudaError_t launch_dense_sweep(int axis, const float* C, int n, int m, const float* l2w_k,
                                const float* pot_k, const double* shift_k, double s, float* part,
