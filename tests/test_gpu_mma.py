@@ -1,4 +1,5 @@
-"""Tensor-core sweep (dim >= 32: 3xTF32 cross term) against the FP64 oracle."""
+"""Tensor-core sweeps (dim >= 32: 3xTF32 cross term; tcgen05 for the solver and softmin
+sweeps, mma.sync fragments for the moment and adjoint sweeps) against the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -50,6 +51,43 @@ def test_softmin_mma(U, n, m, d, eps, shift):
     C = O.cost_matrix(p.x, p.y)
     assert_close(U.softmin(spec, torch.from_numpy(g).cuda(), 0), O.smin_rows(C, p.b, g, eps), eps, "rows")
     assert_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, p.a, f, eps), eps, "cols")
+
+
+@pytest.mark.parametrize("n,m,d", [(1, 1, 33), (5, 3, 56), (127, 20000, 32), (3000, 129, 64)])
+def test_softmin_tcgen05_edges(U, n, m, d):
+    """One row block against 157 key tiles (152 chunks of one tile and a short last one), a
+    single point, dim not a multiple of 8, fewer keys than one 128-key tile, zero weights."""
+    p = gauss_problem(n, m, d, seed=7 * d + n, eps=0.05, rho=0.5)
+    if n > 4:
+        p.a[::10] = 0.0
+    if m > 4:
+        p.b[::7] = 0.0
+    spec = spec_of(U, p)
+    rng = np.random.default_rng(5)
+    g = (0.3 * rng.standard_normal(m)).astype(np.float32)
+    f = (0.3 * rng.standard_normal(n)).astype(np.float32)
+    C = O.cost_matrix(p.x, p.y)
+    assert_close(U.softmin(spec, torch.from_numpy(g).cuda(), 0), O.smin_rows(C, p.b, g, p.eps), p.eps, "rows")
+    assert_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, p.a, f, p.eps), p.eps, "cols")
+
+
+@pytest.mark.parametrize("method", ["plain", "ti", "g"])
+def test_tcgen05_iterates_match_oracle(U, method):
+    """Ragged D = 40 problem with zero weights and rho1 != rho2: iterate-by-iterate parity of
+    the solvers on the tcgen05 sweeps."""
+    p = gauss_problem(611, 437, 40, seed=21, eps=0.05, rho=0.3)
+    p.rho2 = 2.0
+    p.a[::10] = 0.0
+    spec = spec_of(U, p)
+    C = O.cost_matrix(p.x, p.y)
+    solver = {"plain": O.sinkhorn, "ti": O.ti_sinkhorn, "g": O.g_sinkhorn}[method]
+    for T in (1, 7):
+        r = U.solve(spec, method, max_iter=T)
+        ref = solver(C, p.a, p.b, p.eps, p.rho1, p.rho2, T)
+        assert_close(r.f, ref.f, p.eps, f"{method} f after {T}")
+        assert_close(r.g, ref.g, p.eps, f"{method} g after {T}")
+        if method != "plain":
+            assert abs(r.lam - ref.lam) < 1e-4 * p.eps
 
 
 def test_d64_solve_and_grads_match_oracle(U):
