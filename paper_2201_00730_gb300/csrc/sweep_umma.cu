@@ -16,7 +16,10 @@
 // the MMAs of a tile into a ring of four TMEM accumulators while eight consumer
 // warps read the earlier ones (two threads per row, one per column half; tcgen05.ld),
 // add H_j and keep a running (max, sum of 2^(t - max)) per row.  Output: the
-// (max + R_i, sum) partials per (row, key chunk) of the other sweeps.
+// (max + R_i, sum) partials per (row, key chunk) of the other sweeps.  The
+// grid holds one CTA per SM, each taking an equal contiguous range of the
+// (row block, key tile) units, so that no SM idles when the row blocks do
+// not divide the SM count.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,7 +42,8 @@ constexpr int kTmemCols = kAcc * kAccCols;
 constexpr int kMaxChunk = 4096;               // keys per CTA (H_j kept in shared memory)
 constexpr long long kSpin = 1LL << 24;        // mbarrier polls before giving up
 constexpr uint32_t kIdesc = tc::idesc_tf32(kRows, kKeys);
-constexpr uint32_t kPiece = 16384;            // bytes per bulk copy
+constexpr uint32_t kPiece = 65536;            // bytes per bulk copy
+constexpr size_t kOneCtaSmem = 120 * 1024;
 
 __device__ __forceinline__ float tf32r(float x) { return tc::to_tf32(x); }
 
@@ -78,8 +82,8 @@ struct Bars {
   uint64_t empty[kAcc];       // the 8 consumer warps read an accumulator
   uint32_t tmem;
   int err;
-  float hm[kRows];            // second column half's (max, sum) per row
-  float hs[kRows];
+  float hm[2][kRows];         // second column half's (max, sum) per row, by segment parity
+  float hs[2][kRows];
 };
 
 __device__ __forceinline__ void copy_pieces(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -90,23 +94,34 @@ __device__ __forceinline__ void copy_pieces(void* dst, const void* src, uint32_t
   }
 }
 
+// First CTA whose unit range [c U / G, (c + 1) U / G) holds unit x.
+__host__ __device__ __forceinline__ long long cta_of_unit(long long x, long long U, long long G) {
+  return ((x + 1) * G + U - 1) / U - 1;
+}
+
 // Roles: warps 0..7 read the accumulators (warp w: TMEM lane quarter w % 4,
 // i.e. rows 32 (w % 4) .. + 31, and column half w / 4 of every tile); lane 0
-// of warp 8 issues the copies and the MMAs.  Handoffs: b_full (copies ->
-// issuer), m_done (MMAs -> consumers and the issuer, which then reuses the key
-// stage), empty (consumers -> issuer, accumulator free again).  Every wait is
-// bounded; a wait that gives up sets err, which stops every role, and the
+// of warp 8 issues the copies and the MMAs.  Handoffs: a_full (query rows
+// landed), b_full (key tiles landed), m_done (MMAs -> consumers and the
+// issuer, which then reuses the key stage, or the query rows at a row-block
+// change), empty (consumers -> issuer, accumulator free again).  Every wait
+// is bounded; a wait that gives up sets err, which stops every role, and the
 // issuer then lets every copy and MMA in flight land before the CTA ends.
 constexpr int kConsWarps = 8;
 constexpr int kAllThreads = 32 * (kConsWarps + 1);
 
-// grid: (row blocks of 128, key chunks of kps keys, kps a multiple of 64 and <= kMaxChunk);
-// KS = dim8 / 8 MMA K-steps per pass
+// Work units are the pairs (row block of 128 queries, key tile of 128 keys),
+// numbered row-block-major, U = row blocks x TT of them; CTA c of the G in
+// the grid takes the contiguous units [c U / G, (c + 1) U / G), at most
+// kMaxChunk / kKeys of them.  A row block's units are split over consecutive
+// CTAs; the k-th of them writes its (max, sum) partials to slot k of part, and
+// the last one fills the slots it leaves unused with (kInitMax, 0), which the
+// merge ignores.  KS = dim8 / 8 MMA K-steps per pass.
 template <int KS>
 __global__ void __launch_bounds__(kAllThreads, 1)
 k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int nq, const float* __restrict__ opk,
              const float* __restrict__ nk2, int nk, const float* __restrict__ l2w, const float* __restrict__ pot,
-             const double* __restrict__ shift, double s, int kps, float* __restrict__ part) {
+             const double* __restrict__ shift, double s, int TT, int splits, float* __restrict__ part) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int dim8 = 8 * KS;
   constexpr int KA = 2 * dim8;
@@ -117,12 +132,14 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
   float* Hs = reinterpret_cast<float*>(smraw + bytesA + kStages * bytesB);
   Bars& br = *reinterpret_cast<Bars*>(smraw + bytesA + kStages * bytesB + sizeof(float) * kMaxChunk);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rb = blockIdx.x, split = blockIdx.y;
-  const int j0 = split * kps, j1 = min(nk, j0 + kps);
-  const int T = (j1 - j0 + kKeys - 1) / kKeys;
+  const long long U = (long long)((nq + kRows - 1) / kRows) * TT, G = gridDim.x;
+  const long long u0 = (long long)blockIdx.x * U / G, u1 = ((long long)blockIdx.x + 1) * U / G;
+  const int L = (int)(u1 - u0);
+  const int rb0 = (int)(u0 / TT), t0 = (int)(u0 % TT);
+  // H slots: slot v holds key tile (t0 + v) % TT, and unit u0 + t reads slot t % TT
+  const int nslot = L < TT ? L : TT;
   const float s2 = (float)(2.0 * s);
   const double sh = shift ? *shift : 0.0;
-  const int tile0 = j0 / kKeys;
 
   if (warp == 0) tc::tmem_alloc(&br.tmem, kTmemCols);
   if (tid == 32 * kConsWarps) {
@@ -134,16 +151,16 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
     }
     tc::fence_mbar_init();
     br.err = 0;
-    copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb * bytesA, bytesA, &br.a_full);
-    for (int t = 0; t < T && t < kStages; ++t)
+    copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb0 * bytesA, bytesA, &br.a_full);
+    for (int t = 0; t < L && t < kStages; ++t)
       copy_pieces(reinterpret_cast<char*>(B) + (size_t)t * bytesB,
-                  reinterpret_cast<const char*>(opk) + (size_t)(tile0 + t) * bytesB, bytesB, &br.b_full[t]);
+                  reinterpret_cast<const char*>(opk) + (size_t)((t0 + t) % TT) * bytesB, bytesB, &br.b_full[t]);
   }
-  // key constants H_j = h_j - s |y'_j|^2 of this chunk (zero-weight and padding keys: kZeroW)
-  for (int u = tid; u < T * kKeys; u += kAllThreads) {
-    const int j = j0 + u;
+  // key constants H_j = h_j - s |y'_j|^2 of the CTA's key tiles (zero-weight and padding keys: kZeroW)
+  for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
+    const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
     float H = kZeroW;
-    if (j < j1) {
+    if (j < nk) {
       const float lw = l2w[j];
       if (lw > 0.5f * kZeroW) {
         const double pj = pot ? (double)pot[j] : 0.0;
@@ -162,16 +179,33 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
     // ------------------------------------------------------------------ issuer
     if (lane == 0) {
       int armed[kStages] = {}, used[kStages] = {};
-      for (int t = 0; t < T && t < kStages; ++t) armed[t] = 1;
-      bool a_done = false;
+      for (int t = 0; t < L && t < kStages; ++t) armed[t] = 1;
+      int a_armed = 1, a_used = 0;
       int committed = -1, reused = -1;  // tiles committed; MMAs of tiles <= reused known complete
       // descriptors: one K-step (two 16-byte core-matrix columns, 256 bytes) adds 16 to the start field
       const uint64_t dAh = tc::smem_desc(tc::smem_addr(A), 128, sbo);
       const uint64_t dAl = dAh + (uint64_t)(KS * 16);
-      for (int t = 0; t < T && !*err; ++t) {
+      int rb = rb0, tile = t0;
+      for (int t = 0; t < L && !*err; ++t) {
         const int st = t % kStages, b = t % kAcc;
+        if (t > 0) {
+          if (++tile == TT) { tile = 0; ++rb; }
+          if (tile == 0) {
+            // next row block: its rows replace A once the MMAs of tile t - 1, the last to read A, completed
+            if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), kSpin)) {
+              *err = 1;
+              break;
+            }
+            reused = t - 1;
+            copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb * bytesA, bytesA, &br.a_full);
+            ++a_armed;
+          }
+        }
         bool ok = true;
-        if (!a_done) ok = a_done = tc::mbar_wait(&br.a_full, 0, kSpin);
+        if (a_used < a_armed) {
+          ok = tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), kSpin);
+          if (ok) ++a_used;
+        }
         ok = ok && tc::mbar_wait(&br.b_full[st], (uint32_t)((t / kStages) & 1), kSpin);
         if (ok) ++used[st];
         // accumulator b was last read for tile t - kAcc
@@ -190,20 +224,20 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
         for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAh + 16 * k, dBl + 16 * k, kIdesc, true);
         tc::commit(&br.m_done[b]);
         committed = t;
-        // key stage of tile t - 1 -> tile t - 1 + kStages, once the MMAs of tile t - 1 completed
-        if (t >= 1 && t - 1 + kStages < T) {
+        // key stage of unit t - 1 -> unit t - 1 + kStages, once the MMAs of unit t - 1 completed
+        if (t >= 1 && t - 1 + kStages < L) {
           if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), kSpin)) { *err = 1; break; }
           reused = t - 1;
           const int rs = (t - 1) % kStages;
           copy_pieces(reinterpret_cast<char*>(B) + (size_t)rs * bytesB,
-                      reinterpret_cast<const char*>(opk) + (size_t)(tile0 + t - 1 + kStages) * bytesB, bytesB,
+                      reinterpret_cast<const char*>(opk) + (size_t)((t0 + t - 1 + kStages) % TT) * bytesB, bytesB,
                       &br.b_full[rs]);
           ++armed[rs];
         }
       }
       if (*err) {
         // drain: copies armed but never consumed, MMAs committed but never seen complete (bounded)
-        if (!a_done) (void)tc::mbar_wait(&br.a_full, 0, kSpin);
+        for (; a_used < a_armed; ++a_used) (void)tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), kSpin);
         for (int st = 0; st < kStages; ++st)
           for (; used[st] < armed[st]; ++used[st])
             (void)tc::mbar_wait(&br.b_full[st], (uint32_t)(used[st] & 1), kSpin);
@@ -221,68 +255,87 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
     const int row = 32 * q + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((kKeys / 2) * h);
     float M = kInitMax, S = 0.f;
-    for (int t = 0; t < T; ++t) {
-      const int b = t % kAcc;
-      bool done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), kSpin);
-      done = __all_sync(0xffffffffu, done);  // tcgen05.ld is warp-wide
-      if (!done) {
-        if (lane == 0) *err = 1;
-        break;
-      }
-      tc::fence_after_sync();
-      float v[kKeys / 2];
-      tc::ld64(tl + (uint32_t)(b * kAccCols), v);
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&br.empty[b]);
-      const float* H = Hs + t * kKeys + (kKeys / 2) * h;
-#pragma unroll
-      for (int c0 = 0; c0 < kKeys / 2; c0 += 32) {
-        float* vv = v + c0;
-        const float* HH = H + c0;
-#pragma unroll
-        for (int e = 0; e < 32; e += 4) {
-          const float4 hv = *reinterpret_cast<const float4*>(HH + e);
-          vv[e] = fmaf(s2, vv[e], hv.x);
-          vv[e + 1] = fmaf(s2, vv[e + 1], hv.y);
-          vv[e + 2] = fmaf(s2, vv[e + 2], hv.z);
-          vv[e + 3] = fmaf(s2, vv[e + 3], hv.w);
+    bool dead = false;  // warp-uniform: a wait gave up, the remaining units are skipped
+    int rb = rb0, tile = t0, seg = 0;
+    for (int t = 0; t < L; ++t) {
+      if (t > 0 && ++tile == TT) { tile = 0; ++rb; }
+      if (!dead) {
+        const int b = t % kAcc;
+        bool done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), kSpin);
+        done = __all_sync(0xffffffffu, done);  // tcgen05.ld is warp-wide
+        if (!done) {
+          if (lane == 0) *err = 1;
+          dead = true;
         }
-        float cm = vv[0];
-#pragma unroll
-        for (int e = 1; e < 31; e += 2) cm = max3f(cm, vv[e], vv[e + 1]);
-        cm = fmaxf(cm, vv[31]);
-        const float mn = fmaxf(M, cm);
-        const u64 nm = pk(-mn, -mn);
-        u64 a2[4] = {pk(0.f, 0.f), pk(0.f, 0.f), pk(0.f, 0.f), pk(0.f, 0.f)};
-#pragma unroll
-        for (int e = 0; e < 32; e += 2) {
-          float w0, w1;
-          upk(add2(pk(vv[e], vv[e + 1]), nm), w0, w1);
-          a2[(e >> 1) & 3] = add2(a2[(e >> 1) & 3], pk(ex2f(w0), ex2f(w1)));
-        }
-        float s0, s1;
-        upk(add2(add2(a2[0], a2[1]), add2(a2[2], a2[3])), s0, s1);
-        S = S * ex2f(M - mn) + (s0 + s1);
-        M = mn;
       }
-    }
-    if (h == 1) {
-      br.hm[row] = M;
-      br.hs[row] = S;
-    }
-    // the two column halves of a row meet below
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsWarps) : "memory");
-    if (h == 0) {
-      const float M2 = br.hm[row], S2 = br.hs[row];
-      const float mn = fmaxf(M, M2);
-      const float St = S * ex2f(M - mn) + S2 * ex2f(M2 - mn);
-      const int i = rb * kRows + row;
-      if (i < nq) {
-        float* base = part + (size_t)split * 2 * nq;
-        const bool bad = *err != 0;
-        base[i] = bad ? __int_as_float(0x7fc00000) : mn - (float)s * nq2[i];
-        base[(size_t)nq + i] = bad ? __int_as_float(0x7fc00000) : St;
+      if (!dead) {
+        const int b = t % kAcc;
+        tc::fence_after_sync();
+        float v[kKeys / 2];
+        tc::ld64(tl + (uint32_t)(b * kAccCols), v);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&br.empty[b]);
+        const float* H = Hs + (t % TT) * kKeys + (kKeys / 2) * h;
+#pragma unroll
+        for (int c0 = 0; c0 < kKeys / 2; c0 += 32) {
+          float* vv = v + c0;
+          const float* HH = H + c0;
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            const float4 hv = *reinterpret_cast<const float4*>(HH + e);
+            vv[e] = fmaf(s2, vv[e], hv.x);
+            vv[e + 1] = fmaf(s2, vv[e + 1], hv.y);
+            vv[e + 2] = fmaf(s2, vv[e + 2], hv.z);
+            vv[e + 3] = fmaf(s2, vv[e + 3], hv.w);
+          }
+          float cm = vv[0];
+#pragma unroll
+          for (int e = 1; e < 31; e += 2) cm = max3f(cm, vv[e], vv[e + 1]);
+          cm = fmaxf(cm, vv[31]);
+          const float mn = fmaxf(M, cm);
+          const u64 nm = pk(-mn, -mn);
+          u64 a2[4] = {pk(0.f, 0.f), pk(0.f, 0.f), pk(0.f, 0.f), pk(0.f, 0.f)};
+#pragma unroll
+          for (int e = 0; e < 32; e += 2) {
+            float w0, w1;
+            upk(add2(pk(vv[e], vv[e + 1]), nm), w0, w1);
+            a2[(e >> 1) & 3] = add2(a2[(e >> 1) & 3], pk(ex2f(w0), ex2f(w1)));
+          }
+          float s0, s1;
+          upk(add2(add2(a2[0], a2[1]), add2(a2[2], a2[3])), s0, s1);
+          S = S * ex2f(M - mn) + (s0 + s1);
+          M = mn;
+        }
+      }
+      if (tile == TT - 1 || t == L - 1) {
+        // end of this CTA's part of row block rb: the two column halves of a row meet
+        if (h == 1) {
+          br.hm[seg & 1][row] = M;
+          br.hs[seg & 1][row] = S;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsWarps) : "memory");
+        if (h == 0) {
+          const float M2 = br.hm[seg & 1][row], S2 = br.hs[seg & 1][row];
+          const float mn = fmaxf(M, M2);
+          const float St = S * ex2f(M - mn) + S2 * ex2f(M2 - mn);
+          const int i = rb * kRows + row;
+          if (i < nq) {
+            const int slot = (int)((long long)blockIdx.x - cta_of_unit((long long)rb * TT, U, G));
+            float* base = part + (size_t)slot * 2 * nq;
+            const bool bad = *err != 0;
+            base[i] = bad ? __int_as_float(0x7fc00000) : mn - (float)s * nq2[i];
+            base[(size_t)nq + i] = bad ? __int_as_float(0x7fc00000) : St;
+            if (tile == TT - 1)
+              for (int k = slot + 1; k < splits; ++k) {
+                part[(size_t)k * 2 * nq + i] = kInitMax;
+                part[(size_t)k * 2 * nq + nq + i] = 0.f;
+              }
+          }
+        }
+        M = kInitMax;
+        S = 0.f;
+        ++seg;
       }
     }
   }
@@ -293,7 +346,9 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
 
 size_t umma_smem_bytes(int dim8) {
   const size_t KA = 2 * (size_t)dim8;
-  return 16 * KA * 32 + kStages * (kKeys / 8) * KA * 32 + sizeof(float) * kMaxChunk + sizeof(Bars);
+  const size_t need = 16 * KA * 32 + kStages * (kKeys / 8) * KA * 32 + sizeof(float) * kMaxChunk + sizeof(Bars);
+  // more than half of an SM's shared memory: one CTA per SM, so that no CTA waits for TMEM
+  return need < kOneCtaSmem ? kOneCtaSmem : need;
 }
 
 template <int KS>
@@ -311,9 +366,8 @@ cudaError_t run_umma(const float* opq, const float* nq2, int nq, const float* op
       attr = true;
     }
   }
-  dim3 grid(g.row_blocks, g.splits);
-  k_sweep_umma<KS><<<grid, kAllThreads, smem, st>>>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, g.keys_per_split,
-                                                    part);
+  k_sweep_umma<KS><<<g.ctas, kAllThreads, smem, st>>>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s,
+                                                      g.keys_per_split / kKeys, g.splits, part);
   note_launch();
   return cudaGetLastError();
 }
@@ -341,18 +395,21 @@ SweepGeom umma_geom(int nq, int nk) {
   g.threads = kAllThreads;
   g.rows = 1;
   g.row_blocks = (nq + kRows - 1) / kRows;
-  const int sms = device_sm_count();
-  const int tiles = (nk + kKeys - 1) / kKeys;
-  // one CTA per SM: as many key chunks as keep the row blocks x chunks within one wave,
-  // and at most kMaxChunk keys a chunk
-  int splits = sms / g.row_blocks;
-  if (splits < 1) splits = 1;
-  const int min_splits = (nk + kMaxChunk - 1) / kMaxChunk;
-  if (splits < min_splits) splits = min_splits;
-  if (splits > tiles) splits = tiles;
-  const int tiles_per = (tiles + splits - 1) / splits;
-  g.keys_per_split = tiles_per * kKeys;
-  g.splits = (nk + g.keys_per_split - 1) / g.keys_per_split;
+  const long long TT = (nk + kKeys - 1) / kKeys;
+  g.keys_per_split = (int)TT * kKeys;
+  // the (row block, key tile) units spread evenly over one CTA per SM (a multiple of the
+  // SM count when a CTA would otherwise hold more than kMaxChunk keys of H_j)
+  const long long U = (long long)g.row_blocks * TT;
+  const long long sms = device_sm_count(), per = kMaxChunk / kKeys;
+  long long G = sms * ((U + sms * per - 1) / (sms * per));
+  if (G > U) G = U;
+  g.ctas = (int)G;
+  // partial slots: a bound on the CTAs one row block's TT units are spread over (the first
+  // and the last may hold one unit each, those between at least floor(U / G))
+  const long long lmin = U / G;
+  long long splits = TT < 2 ? 1 : 2 + (TT - 2) / lmin;
+  if (splits > G) splits = G;
+  g.splits = (int)splits;
   return g;
 }
 

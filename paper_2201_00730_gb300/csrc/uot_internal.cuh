@@ -71,8 +71,9 @@ struct SweepGeom {
   int threads;      // CTA size
   int rows;         // rows per thread (R)
   int row_blocks;   // grid.x
-  int splits;       // grid.y (key chunks)
+  int splits;       // grid.y (key chunks); partial slots per query
   int keys_per_split;
+  int ctas;         // persistent unit-range grids: CTAs in the grid (0 elsewhere)
 };
 
 int device_sm_count();
