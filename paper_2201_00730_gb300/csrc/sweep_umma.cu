@@ -6,20 +6,24 @@
 //   H_j = h_j - s |y'_j|^2,  R_i = -s |x'_i|^2,
 //
 // with the dot products x'.y' a dense (rows x dim) x (dim x keys)
-// contraction.  Each coordinate is split into TF32 parts hi + lo and the
-// product is hi.hi + lo.hi + hi.lo (three kind::tf32 MMA passes, about FP32
-// accuracy).  The split operands of both clouds are built once per call in
-// the canonical K-major layout (8-row x 16-byte core matrices, no swizzle),
-// so that a tile of 8k rows is one contiguous block: a CTA copies its 128
-// query rows and each 128-key tile into shared memory with bulk asynchronous
-// copies completing on mbarriers (two key stages); one lane issues
-// the MMAs of a tile into a ring of four TMEM accumulators while eight consumer
-// warps read the earlier ones (two threads per row, one per column half; tcgen05.ld),
-// add H_j and keep a running (max, sum of 2^(t - max)) per row.  Output: the
+// contraction.  Each coordinate, scaled by a power of two 2^e common to both
+// clouds (so that the largest is below 2^15), is split into FP16 parts
+// hi + lo, and the product is hi.hi + lo.hi + hi.lo (three kind::f16 MMA
+// passes with FP32 accumulation; hi and lo carry 11 significant bits each,
+// the dropped lo.lo is below 2^-22 of |x'||y'|), rescaled by 2^-2e.  The
+// split operands of both clouds are built once per call in the canonical
+// K-major layout (8-row x 16-byte core matrices, no swizzle), so that a tile
+// of 8k rows is one contiguous block: a CTA copies its 128 query rows and
+// each 128-key tile into shared memory with bulk asynchronous copies
+// completing on mbarriers (four key stages); one lane issues the MMAs of a
+// tile into a ring of four TMEM accumulators while eight consumer warps read
+// the earlier ones (two threads per row, one per column half; tcgen05.ld), add
+// H_j and keep a running (max, sum of 2^(t - max)) per row.  Output: the
 // (max + R_i, sum) partials per (row, key chunk) of the other sweeps.  The
 // grid holds one CTA per SM, each taking an equal contiguous range of the
 // (row block, key tile) units, so that no SM idles when the row blocks do
 // not divide the SM count.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -35,41 +39,78 @@ using namespace simd;
 
 constexpr int kRows = 128;                    // MMA M
 constexpr int kKeys = 128;                    // MMA N (keys per tile)
-constexpr int kStages = 2;                    // key-tile buffers
+constexpr int kStages = 4;                    // key-tile buffers
 constexpr int kAccCols = kKeys;               // TMEM columns per accumulator (N fp32)
 constexpr int kAcc = 4;                       // accumulators in TMEM (a ring)
 constexpr int kTmemCols = kAcc * kAccCols;
 constexpr int kMaxChunk = 4096;               // keys per CTA (H_j kept in shared memory)
 constexpr long long kSpin = 1LL << 24;        // mbarrier polls before giving up
-constexpr uint32_t kIdesc = tc::idesc_tf32(kRows, kKeys);
+constexpr uint32_t kIdesc = tc::idesc_f16(kRows, kKeys);
 constexpr uint32_t kPiece = 65536;            // bytes per bulk copy
 constexpr size_t kOneCtaSmem = 120 * 1024;
 
-__device__ __forceinline__ float tf32r(float x) { return tc::to_tf32(x); }
+// Byte offset of element (r, k) of a 2-byte K-major operand with SBO bytes
+// between 8-row groups: core matrices of 8 rows x 8 elements, 128 bytes each.
+__host__ __device__ constexpr int kmajor_offset_h(int r, int k, int sbo) {
+  return (r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
 
-// Operand matrix of one cloud: row r, split coordinates of r - c as
-// [hi (dim8) | lo (dim8)] in the canonical K-major layout, KA = 2 dim8 values a
-// row, rows padded with zeros to a multiple of 128; norm2[r] = |x'_r|^2.
-__global__ void k_umma_operand(const float* __restrict__ pts, int n, int npad, int dim, int dim8,
-                               const float* __restrict__ center, float* __restrict__ op, float* __restrict__ norm2) {
-  const int KA = 2 * dim8;
-  const int sbo = KA * 32;
+// 2^e as a float / double (|e| well inside the normal range).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// Scale exponent e of the split: the largest |x - c| (its bit pattern, a
+// non-negative float) times 2^e lies in [2^14, 2^15); e within [-40, 40].
+__device__ __forceinline__ int scale_exp(int maxbits) {
+  if (maxbits <= 0) return 0;
+  const int E = ((maxbits >> 23) & 255) - 127;
+  const int e = 14 - E;
+  return e < -40 ? -40 : (e > 40 ? 40 : e);
+}
+
+// Largest |x_rd - c_d| over both clouds, as the bit pattern of a non-negative
+// float (ordered like the value) in *maxbits (zeroed by the caller).
+__global__ void k_umma_maxabs(const float* __restrict__ x, int n, const float* __restrict__ y, int m, int dim,
+                              const float* __restrict__ center, int* maxbits) {
+  float mx = 0.f;
+  const long long tx = (long long)n * dim, total = tx + (long long)m * dim;
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+       u += (long long)gridDim.x * blockDim.x) {
+    const float v = u < tx ? x[u] - center[u % dim] : y[u - tx] - center[(u - tx) % dim];
+    mx = fmaxf(mx, fabsf(v));
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(maxbits, __float_as_int(mx));
+}
+
+// Operand matrix of one cloud: row r, the split scaled coordinates of r - c as
+// [hi (dim16) | lo (dim16)] FP16 in the canonical K-major layout, KA = 2 dim16
+// values a row, rows padded with zeros to a multiple of 128; norm2[r] = |w_r|^2
+// with w = (hi + lo) 2^-e, the coordinates the products see.
+__global__ void k_umma_operand(const float* __restrict__ pts, int n, int npad, int dim, int dim16,
+                               const float* __restrict__ center, const int* __restrict__ maxbits,
+                               __half* __restrict__ op, float* __restrict__ norm2) {
+  const int KA = 2 * dim16;
+  const int sbo = KA * 16;
+  const int e = scale_exp(*maxbits);
+  const float sc = pow2f(e), isc = pow2f(-e);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < npad; r += gridDim.x * blockDim.x) {
     float acc = 0.f;
-    for (int d0 = 0; d0 < dim8; d0 += 4) {
-      float hi[4], lo[4];
+    for (int d0 = 0; d0 < dim16; d0 += 8) {
+      __align__(16) __half hi[8];
+      __align__(16) __half lo[8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int d = d0 + e;
-        const float v = (r < n && d < dim) ? pts[(size_t)r * dim + d] - center[d] : 0.f;
-        hi[e] = tf32r(v);
-        lo[e] = tf32r(v - hi[e]);
-        const float w = hi[e] + lo[e];
+      for (int j = 0; j < 8; ++j) {
+        const int d = d0 + j;
+        const float v = (r < n && d < dim) ? (pts[(size_t)r * dim + d] - center[d]) * sc : 0.f;
+        hi[j] = __float2half_rn(v);
+        lo[j] = __float2half_rn(v - __half2float(hi[j]));
+        const float w = (__half2float(hi[j]) + __half2float(lo[j])) * isc;
         acc = fmaf(w, w, acc);
       }
       char* base = reinterpret_cast<char*>(op);
-      *reinterpret_cast<float4*>(base + tc::kmajor_offset(r, d0, sbo)) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<float4*>(base + tc::kmajor_offset(r, dim8 + d0, sbo)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(base + kmajor_offset_h(r, d0, sbo)) = *reinterpret_cast<const uint4*>(hi);
+      *reinterpret_cast<uint4*>(base + kmajor_offset_h(r, dim16 + d0, sbo)) = *reinterpret_cast<const uint4*>(lo);
     }
     if (r < n) norm2[r] = acc;
   }
@@ -116,19 +157,20 @@ constexpr int kAllThreads = 32 * (kConsWarps + 1);
 // kMaxChunk / kKeys of them.  A row block's units are split over consecutive
 // CTAs; the k-th of them writes its (max, sum) partials to slot k of part, and
 // the last one fills the slots it leaves unused with (kInitMax, 0), which the
-// merge ignores.  KS = dim8 / 8 MMA K-steps per pass.
+// merge ignores.  KS = dim16 / 16 MMA K-steps per pass.
 template <int KS>
 __global__ void __launch_bounds__(kAllThreads, 1)
-k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int nq, const float* __restrict__ opk,
+k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int nq, const __half* __restrict__ opk,
              const float* __restrict__ nk2, int nk, const float* __restrict__ l2w, const float* __restrict__ pot,
-             const double* __restrict__ shift, double s, int TT, int splits, float* __restrict__ part) {
+             const double* __restrict__ shift, double s, const int* __restrict__ maxbits, int TT, int splits,
+             float* __restrict__ part) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  constexpr int dim8 = 8 * KS;
-  constexpr int KA = 2 * dim8;
-  const uint32_t sbo = (uint32_t)KA * 32u;
+  constexpr int dim16 = 16 * KS;
+  constexpr int KA = 2 * dim16;  // FP16 values a row
+  const uint32_t sbo = (uint32_t)KA * 16u;
   const uint32_t bytesA = 16u * sbo, bytesB = (uint32_t)(kKeys / 8) * sbo;
-  float* A = reinterpret_cast<float*>(smraw);
-  float* B = reinterpret_cast<float*>(smraw + bytesA);  // [kStages][kKeys x KA]
+  unsigned char* A = smraw;
+  unsigned char* B = smraw + bytesA;  // [kStages][kKeys x KA]
   float* Hs = reinterpret_cast<float*>(smraw + bytesA + kStages * bytesB);
   Bars& br = *reinterpret_cast<Bars*>(smraw + bytesA + kStages * bytesB + sizeof(float) * kMaxChunk);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -138,7 +180,7 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
   const int rb0 = (int)(u0 / TT), t0 = (int)(u0 % TT);
   // H slots: slot v holds key tile (t0 + v) % TT, and unit u0 + t reads slot t % TT
   const int nslot = L < TT ? L : TT;
-  const float s2 = (float)(2.0 * s);
+  const float s2 = (float)(2.0 * s * pow2d(-2 * scale_exp(*maxbits)));  // products carry 2^2e
   const double sh = shift ? *shift : 0.0;
 
   if (warp == 0) tc::tmem_alloc(&br.tmem, kTmemCols);
@@ -182,7 +224,8 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
       for (int t = 0; t < L && t < kStages; ++t) armed[t] = 1;
       int a_armed = 1, a_used = 0;
       int committed = -1, reused = -1;  // tiles committed; MMAs of tiles <= reused known complete
-      // descriptors: one K-step (two 16-byte core-matrix columns, 256 bytes) adds 16 to the start field
+      // descriptors: one K-step (16 values: two 16-byte core-matrix columns, 256 bytes) adds 16 to the
+      // start field, the lo parts start dim16 / 8 core-matrix columns (16 KS in the field) further
       const uint64_t dAh = tc::smem_desc(tc::smem_addr(A), 128, sbo);
       const uint64_t dAl = dAh + (uint64_t)(KS * 16);
       int rb = rb0, tile = t0;
@@ -217,11 +260,11 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
         const uint64_t dBl = dBh + (uint64_t)(KS * 16);
         // hi.hi, then lo.hi (lo parts of x), then hi.lo (lo parts of y)
 #pragma unroll
-        for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAh + 16 * k, dBh + 16 * k, kIdesc, k > 0);
+        for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBh + 16 * k, kIdesc, k > 0);
 #pragma unroll
-        for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAl + 16 * k, dBh + 16 * k, kIdesc, true);
+        for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAl + 16 * k, dBh + 16 * k, kIdesc, true);
 #pragma unroll
-        for (int k = 0; k < KS; ++k) tc::mma_tf32(d, dAh + 16 * k, dBl + 16 * k, kIdesc, true);
+        for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBl + 16 * k, kIdesc, true);
         tc::commit(&br.m_done[b]);
         committed = t;
         // key stage of unit t - 1 -> unit t - 1 + kStages, once the MMAs of unit t - 1 completed
@@ -344,18 +387,18 @@ k_sweep_umma(const float* __restrict__ opq, const float* __restrict__ nq2, int n
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-size_t umma_smem_bytes(int dim8) {
-  const size_t KA = 2 * (size_t)dim8;
-  const size_t need = 16 * KA * 32 + kStages * (kKeys / 8) * KA * 32 + sizeof(float) * kMaxChunk + sizeof(Bars);
+size_t umma_smem_bytes(int dim16) {
+  const size_t KA = 2 * (size_t)dim16;
+  const size_t need = 16 * KA * 16 + kStages * (kKeys / 8) * KA * 16 + sizeof(float) * kMaxChunk + sizeof(Bars);
   // more than half of an SM's shared memory: one CTA per SM, so that no CTA waits for TMEM
   return need < kOneCtaSmem ? kOneCtaSmem : need;
 }
 
 template <int KS>
-cudaError_t run_umma(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
-                     const float* l2w, const float* pot, const double* shift, double s, float* part,
-                     const SweepGeom& g, cudaStream_t st) {
-  const size_t smem = umma_smem_bytes(8 * KS);
+cudaError_t run_umma(const __half* opq, const float* nq2, int nq, const __half* opk, const float* nk2, int nk,
+                     const float* l2w, const float* pot, const double* shift, double s, const int* maxbits,
+                     float* part, const SweepGeom& g, cudaStream_t st) {
+  const size_t smem = umma_smem_bytes(16 * KS);
   static std::mutex mu;
   static bool attr = false;
   {
@@ -366,7 +409,7 @@ cudaError_t run_umma(const float* opq, const float* nq2, int nq, const float* op
       attr = true;
     }
   }
-  k_sweep_umma<KS><<<g.ctas, kAllThreads, smem, st>>>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s,
+  k_sweep_umma<KS><<<g.ctas, kAllThreads, smem, st>>>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, maxbits,
                                                       g.keys_per_split / kKeys, g.splits, part);
   note_launch();
   return cudaGetLastError();
@@ -374,18 +417,32 @@ cudaError_t run_umma(const float* opq, const float* nq2, int nq, const float* op
 
 }  // namespace
 
-int umma_dim8(int dim) { return (dim + 7) & ~7; }
+int umma_dim16(int dim) { return (dim + 15) & ~15; }
 
 size_t umma_operand_floats(int n, int dim) {
+  // FP16 hi and lo parts: dim16 floats' worth of bytes a row
   const size_t npad = ((size_t)n + kRows - 1) / kRows * kRows;
-  return npad * 2 * (size_t)umma_dim8(dim);
+  return npad * (size_t)umma_dim16(dim);
 }
 
-cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, float* op, float* norm2,
-                                cudaStream_t st) {
+cudaError_t launch_umma_scale(const float* x, int n, const float* y, int m, int dim, const float* center,
+                              int* maxbits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const long long total = ((long long)n + m) * dim;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4 * (long long)device_sm_count()) blocks = 4 * (long long)device_sm_count();
+  k_umma_maxabs<<<(int)blocks, 256, 0, st>>>(x, n, y, m, dim, center, maxbits);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, const int* maxbits,
+                                void* op, float* norm2, cudaStream_t st) {
   const int npad = (n + kRows - 1) / kRows * kRows;
   const int blocks = (npad + 255) / 256;
-  k_umma_operand<<<blocks, 256, 0, st>>>(pts, n, npad, dim, umma_dim8(dim), center, op, norm2);
+  k_umma_operand<<<blocks, 256, 0, st>>>(pts, n, npad, dim, umma_dim16(dim), center, maxbits,
+                                         static_cast<__half*>(op), norm2);
   note_launch();
   return cudaGetLastError();
 }
@@ -413,16 +470,15 @@ SweepGeom umma_geom(int nq, int nk) {
   return g;
 }
 
-cudaError_t launch_umma_sweep(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
-                              int dim, const float* l2w, const float* pot, const double* shift, double s, float* part,
-                              const SweepGeom& g, cudaStream_t st) {
-  const int dim8 = umma_dim8(dim);
-  switch (dim8 / 8) {
-    case 4: return run_umma<4>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
-    case 5: return run_umma<5>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
-    case 6: return run_umma<6>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
-    case 7: return run_umma<7>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
-    default: return run_umma<8>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, part, g, st);
+cudaError_t launch_umma_sweep(const void* opq, const float* nq2, int nq, const void* opk, const float* nk2, int nk,
+                              int dim, const float* l2w, const float* pot, const double* shift, double s,
+                              const int* maxbits, float* part, const SweepGeom& g, cudaStream_t st) {
+  const __half* q = static_cast<const __half*>(opq);
+  const __half* k = static_cast<const __half*>(opk);
+  switch (umma_dim16(dim) / 16) {
+    case 2: return run_umma<2>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, st);
+    case 3: return run_umma<3>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, st);
+    default: return run_umma<4>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, st);
   }
 }
 

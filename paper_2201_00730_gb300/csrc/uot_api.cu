@@ -115,7 +115,7 @@ PartSizes part_sizes(const uot_problem& p) {
 
 struct WsLayout {
   size_t state, ln_a, ln_b, l2_a, l2_b, lo_a, lo_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc, center;
-  size_t op_x, op_y, n2_x, n2_y;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
+  size_t op_x, op_y, n2_x, n2_y, op_sc;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
   size_t sort_tmp_bytes, total;
@@ -146,6 +146,7 @@ WsLayout ws_layout(const uot_problem& p) {
     L.op_y = take(sizeof(float) * umma_operand_floats(p.m, p.dim));
     L.n2_x = take(sizeof(float) * p.n);
     L.n2_y = take(sizeof(float) * p.m);
+    L.op_sc = take(sizeof(int));
   }
   if (tiled_path(p)) {
     const int nmax = p.n > p.m ? p.n : p.m;
@@ -179,6 +180,7 @@ struct Ctx {
   unsigned int* rbc;  // per-row-block counters of the fused sweeps
   float* center;      // common centre of the clouds (tensor-core path)
   float *op_x, *op_y, *n2_x, *n2_y;  // tcgen05 operands and squared norms (dim >= 32)
+  int* op_sc;                        // their power-of-two scale (largest |x - c|, as float bits)
   cudaStream_t st;
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
@@ -227,11 +229,13 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->rbc = reinterpret_cast<unsigned int*>(b + L.rbc);
   c->center = reinterpret_cast<float*>(b + L.center);
   c->op_x = c->op_y = c->n2_x = c->n2_y = nullptr;
+  c->op_sc = nullptr;
   if (mma_path(*prob)) {
     c->op_x = reinterpret_cast<float*>(b + L.op_x);
     c->op_y = reinterpret_cast<float*>(b + L.op_y);
     c->n2_x = reinterpret_cast<float*>(b + L.n2_x);
     c->n2_y = reinterpret_cast<float*>(b + L.n2_y);
+    c->op_sc = reinterpret_cast<int*>(b + L.op_sc);
   }
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
@@ -276,8 +280,9 @@ uot_status prepare(Ctx& c) {
   }
   if (mma_path(c.p)) {
     UOT_CUDA(launch_center(c.p.x, c.p.n, c.p.y, c.p.m, c.p.dim, c.center, c.st));
-    UOT_CUDA(launch_umma_operand(c.p.x, c.p.n, c.p.dim, c.center, c.op_x, c.n2_x, c.st));
-    UOT_CUDA(launch_umma_operand(c.p.y, c.p.m, c.p.dim, c.center, c.op_y, c.n2_y, c.st));
+    UOT_CUDA(launch_umma_scale(c.p.x, c.p.n, c.p.y, c.p.m, c.p.dim, c.center, c.op_sc, c.st));
+    UOT_CUDA(launch_umma_operand(c.p.x, c.p.n, c.p.dim, c.center, c.op_sc, c.op_x, c.n2_x, c.st));
+    UOT_CUDA(launch_umma_operand(c.p.y, c.p.m, c.p.dim, c.center, c.op_sc, c.op_y, c.n2_y, c.st));
   }
   UOT_CUDA(launch_log_weights(c.pa, c.p.n, c.ln_a, c.l2_a, c.lo_a, &c.state->status, c.st));
   UOT_CUDA(launch_log_weights(c.pb, c.p.m, c.ln_b, c.l2_b, c.lo_b, &c.state->status, c.st));
@@ -359,7 +364,7 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       *splits = g.splits;
       UOT_CUDA(launch_umma_sweep(axis == 0 ? c.op_x : c.op_y, axis == 0 ? c.n2_x : c.n2_y, q.n,
                                  axis == 0 ? c.op_y : c.op_x, axis == 0 ? c.n2_y : c.n2_x, k.n, p.dim, k.l2w, pot,
-                                 shift, c.s, part, g, c.st));
+                                 shift, c.s, c.op_sc, part, g, c.st));
     } else if (mma_path(p)) {
       // gradient sweep with moments: dC/dx = 2 (x - y)
       SweepGeom g = flash_geom(q.n, k.n);

@@ -89,7 +89,7 @@ int max_splits_for(const uot_problem& p);
 constexpr int kMaxBlocks = 4096;
 constexpr int kTileKeys = 128;  // keys per local-frame tile of the tiled sweep
 
-// True when the tensor-core sweep (3xTF32 cross term) serves this problem.
+// True when the tensor-core sweep (split-FP16 cross term) serves this problem.
 inline bool mma_path(const uot_problem& p) {
   return p.cost_kind == UOT_COST_POINTS && p.dim >= 32 && p.p == 2.0f;
 }
@@ -168,16 +168,19 @@ cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, 
                                const float* hk, const float* mk, double s, float momscale, float* part,
                                const SweepGeom& g, cudaStream_t st);
 // tcgen05 sweep (dim >= 32, p = 2): the operand matrices of both clouds (split
-// TF32 coordinates relative to the common centre, canonical K-major layout,
-// rows padded to 128) and their squared norms, built once per call.
-int umma_dim8(int dim);
+// FP16 coordinates relative to the common centre, scaled by a power of two
+// from the largest |x - c| in *maxbits, canonical K-major layout, rows padded
+// to 128) and their squared norms, built once per call.
+int umma_dim16(int dim);
 size_t umma_operand_floats(int n, int dim);
-cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, float* op, float* norm2,
-                                cudaStream_t st);
+cudaError_t launch_umma_scale(const float* x, int n, const float* y, int m, int dim, const float* center,
+                              int* maxbits, cudaStream_t st);
+cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, const int* maxbits,
+                                void* op, float* norm2, cudaStream_t st);
 SweepGeom umma_geom(int nq, int nk);
-cudaError_t launch_umma_sweep(const float* opq, const float* nq2, int nq, const float* opk, const float* nk2, int nk,
-                              int dim, const float* l2w, const float* pot, const double* shift, double s, float* part,
-                              const SweepGeom& g, cudaStream_t st);
+cudaError_t launch_umma_sweep(const void* opq, const float* nq2, int nq, const void* opk, const float* nk2, int nk,
+                              int dim, const float* l2w, const float* pot, const double* shift, double s,
+                              const int* maxbits, float* part, const SweepGeom& g, cudaStream_t st);
 // Dense cost: axis 0 = rows of C are queries, axis 1 = columns of C are queries.
 cudaError_t launch_dense_sweep(int axis, const float* C, int n, int m, const float* l2w_k,
                                const float* pot_k, const double* shift_k, double s, float* part,

@@ -53,10 +53,12 @@ def test_softmin_mma(U, n, m, d, eps, shift):
     assert_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, p.a, f, eps), eps, "cols")
 
 
-@pytest.mark.parametrize("n,m,d", [(1, 1, 33), (5, 3, 56), (127, 20000, 32), (3000, 129, 64)])
+@pytest.mark.parametrize("n,m,d", [(1, 1, 33), (5, 3, 56), (127, 20000, 32), (3000, 129, 64), (1300, 4100, 64),
+                                   (2900, 2100, 32)])
 def test_softmin_tcgen05_edges(U, n, m, d):
-    """One row block against 157 key tiles (152 chunks of one tile and a short last one), a
-    single point, dim not a multiple of 8, fewer keys than one 128-key tile, zero weights."""
+    """One row block against 157 key tiles (one or two units a CTA, a short last tile), a
+    single point, dim not a multiple of 8, fewer keys than one 128-key tile, CTAs whose unit
+    ranges cross a row-block boundary (11 x 33 and 23 x 17 units over the SMs), zero weights."""
     p = gauss_problem(n, m, d, seed=7 * d + n, eps=0.05, rho=0.5)
     if n > 4:
         p.a[::10] = 0.0
