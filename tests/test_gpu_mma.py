@@ -1,5 +1,5 @@
-"""Tensor-core sweeps (dim >= 32: 3xTF32 cross term; tcgen05 for the solver and softmin
-sweeps, mma.sync fragments for the moment and adjoint sweeps) against the FP64 oracle."""
+"""Tensor-core sweeps (dim >= 32: split-FP16 cross term on tcgen05 for the solver and softmin
+sweeps, 3xTF32 mma.sync fragments for the moment and adjoint sweeps) against the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -68,6 +68,25 @@ def test_softmin_tcgen05_edges(U, n, m, d):
     rng = np.random.default_rng(5)
     g = (0.3 * rng.standard_normal(m)).astype(np.float32)
     f = (0.3 * rng.standard_normal(n)).astype(np.float32)
+    C = O.cost_matrix(p.x, p.y)
+    assert_close(U.softmin(spec, torch.from_numpy(g).cuda(), 0), O.smin_rows(C, p.b, g, p.eps), p.eps, "rows")
+    assert_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, p.a, f, p.eps), p.eps, "cols")
+
+
+@pytest.mark.parametrize("scale,shift", [(1e-3, 0.0), (1e3, 5e3), (1.0, 40.0)])
+def test_softmin_tcgen05_coordinate_scales(U, scale, shift):
+    """The power-of-two scaling of the FP16 split: clouds far below and far above unit size,
+    and clouds far from the origin (the common centre comes off first); eps scales with the
+    squared size so that the softmins stay comparable."""
+    n, m, d = 700, 900, 48
+    eps = 0.05 * scale * scale
+    p = gauss_problem(n, m, d, seed=97, eps=eps, rho=0.5 * scale * scale)
+    p.x = (p.x * scale + shift).astype(np.float32)
+    p.y = (p.y * scale + shift).astype(np.float32)
+    spec = spec_of(U, p)
+    rng = np.random.default_rng(11)
+    g = (0.3 * eps * rng.standard_normal(m)).astype(np.float32)
+    f = (0.3 * eps * rng.standard_normal(n)).astype(np.float32)
     C = O.cost_matrix(p.x, p.y)
     assert_close(U.softmin(spec, torch.from_numpy(g).cuda(), 0), O.smin_rows(C, p.b, g, p.eps), p.eps, "rows")
     assert_close(U.softmin(spec, torch.from_numpy(f).cuda(), 1), O.smin_cols(C, p.a, f, p.eps), p.eps, "cols")
