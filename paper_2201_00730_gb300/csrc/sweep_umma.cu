@@ -14,9 +14,9 @@
 // split operands of both clouds are built once per call in the canonical
 // K-major layout (8-row x 16-byte core matrices, no swizzle), so that a tile
 // of 8k rows is one contiguous block: a CTA copies its 128 query rows and
-// each 128-key tile into shared memory with bulk asynchronous copies
-// completing on mbarriers (four key stages); one lane issues the MMAs of a
-// tile into a ring of four TMEM accumulators while eight consumer warps read
+// each 256-key tile into shared memory with bulk asynchronous copies
+// completing on mbarriers (two key stages); one lane issues the MMAs of a
+// tile (N = 256) into a pair of TMEM accumulators while eight consumer warps read
 // the earlier ones (two threads per row, one per column half; tcgen05.ld), add
 // H_j and keep a running (max, sum of 2^(t - max)) per row.  Output: the
 // (max + R_i, sum) partials per (row, key chunk) of the other sweeps.  The
@@ -38,14 +38,15 @@ namespace {
 using namespace simd;
 
 constexpr int kRows = 128;                    // MMA M
-constexpr int kKeys = 128;                    // MMA N (keys per tile)
-constexpr int kStages = 4;                    // key-tile buffers
+constexpr int kKeys = 256;                    // MMA N (keys per tile)
+constexpr int kPad = 256;                     // operand rows padded to a multiple of this
+constexpr int kStages = 2;                    // key-tile buffers
 constexpr int kAccCols = kKeys;               // TMEM columns per accumulator (N fp32)
-constexpr int kAcc = 4;                       // accumulators in TMEM (a ring)
+constexpr int kAcc = 2;                       // accumulators in TMEM (a ring)
 constexpr int kTmemCols = kAcc * kAccCols;
 constexpr int kMaxChunk = 4096;               // keys per CTA (H_j kept in shared memory)
 constexpr long long kSpin = 1LL << 24;        // mbarrier polls before giving up
-constexpr uint32_t kIdesc = tc::idesc_f16(kRows, kKeys);
+constexpr uint32_t kIdesc = tc::idesc_f16(kRows, kKeys);  // N = 256, the largest for M = 128
 constexpr uint32_t kPiece = 65536;            // bytes per bulk copy
 constexpr size_t kOneCtaSmem = 120 * 1024;
 
@@ -85,7 +86,7 @@ __global__ void k_umma_maxabs(const float* __restrict__ x, int n, const float* _
 
 // Operand matrix of one cloud: row r, the split scaled coordinates of r - c as
 // [hi (dim16) | lo (dim16)] FP16 in the canonical K-major layout, KA = 2 dim16
-// values a row, rows padded with zeros to a multiple of 128; norm2[r] = |w_r|^2
+// values a row, rows padded with zeros to a multiple of 256; norm2[r] = |w_r|^2
 // with w = (hi + lo) 2^-e, the coordinates the products see.
 __global__ void k_umma_operand(const float* __restrict__ pts, int n, int npad, int dim, int dim16,
                                const float* __restrict__ center, const int* __restrict__ maxbits,
@@ -151,7 +152,7 @@ __host__ __device__ __forceinline__ long long cta_of_unit(long long x, long long
 constexpr int kConsWarps = 8;
 constexpr int kAllThreads = 32 * (kConsWarps + 1);
 
-// Work units are the pairs (row block of 128 queries, key tile of 128 keys),
+// Work units are the pairs (row block of 128 queries, key tile of 256 keys),
 // numbered row-block-major, U = row blocks x TT of them; CTA c of the G in
 // the grid takes the contiguous units [c U / G, (c + 1) U / G), at most
 // kMaxChunk / kKeys of them.  A row block's units are split over consecutive
@@ -314,14 +315,19 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
       if (!dead) {
         const int b = t % kAcc;
         tc::fence_after_sync();
-        float v[kKeys / 2];
-        tc::ld64(tl + (uint32_t)(b * kAccCols), v);
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&br.empty[b]);
-        const float* H = Hs + (t % TT) * kKeys + (kKeys / 2) * h;
+        // this thread's half of the tile's columns, 64 at a time
+#pragma unroll 1
+        for (int part = 0; part < kKeys / 128; ++part) {
+        float v[64];
+        tc::ld64(tl + (uint32_t)(b * kAccCols + 64 * part), v);
+        if (part == kKeys / 128 - 1) {
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&br.empty[b]);
+        }
+        const float* H = Hs + (t % TT) * kKeys + (kKeys / 2) * h + 64 * part;
 #pragma unroll
-        for (int c0 = 0; c0 < kKeys / 2; c0 += 32) {
+        for (int c0 = 0; c0 < 64; c0 += 32) {
           float* vv = v + c0;
           const float* HH = H + c0;
 #pragma unroll
@@ -349,6 +355,7 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
           upk(add2(add2(a2[0], a2[1]), add2(a2[2], a2[3])), s0, s1);
           S = S * ex2f(M - mn) + (s0 + s1);
           M = mn;
+        }
         }
       }
       if (tile == TT - 1 || t == L - 1) {
@@ -421,7 +428,7 @@ int umma_dim16(int dim) { return (dim + 15) & ~15; }
 
 size_t umma_operand_floats(int n, int dim) {
   // FP16 hi and lo parts: dim16 floats' worth of bytes a row
-  const size_t npad = ((size_t)n + kRows - 1) / kRows * kRows;
+  const size_t npad = ((size_t)n + kPad - 1) / kPad * kPad;
   return npad * (size_t)umma_dim16(dim);
 }
 
@@ -439,7 +446,7 @@ cudaError_t launch_umma_scale(const float* x, int n, const float* y, int m, int 
 
 cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, const int* maxbits,
                                 void* op, float* norm2, cudaStream_t st) {
-  const int npad = (n + kRows - 1) / kRows * kRows;
+  const int npad = (n + kPad - 1) / kPad * kPad;
   const int blocks = (npad + 255) / 256;
   k_umma_operand<<<blocks, 256, 0, st>>>(pts, n, npad, dim, umma_dim16(dim), center, maxbits,
                                          static_cast<__half*>(op), norm2);
