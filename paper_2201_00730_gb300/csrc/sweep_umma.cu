@@ -16,8 +16,8 @@
 // of 8k rows is one contiguous block: a CTA copies its 128 query rows and
 // each 256-key tile into shared memory with bulk asynchronous copies
 // completing on mbarriers (two key stages); one lane issues the MMAs of a
-// tile (N = 256) into a pair of TMEM accumulators while eight consumer warps read
-// the earlier ones (two threads per row, one per column half; tcgen05.ld), add
+// tile (N = 256) into a pair of TMEM accumulators while sixteen consumer warps read
+// the earlier ones (four threads per row, one per column quarter; tcgen05.ld), add
 // H_j and keep a running (max, sum of 2^(t - max)) per row.  Output: the
 // (max + R_i, sum) partials per (row, key chunk) of the other sweeps.  The
 // grid holds one CTA per SM, each taking an equal contiguous range of the
@@ -124,8 +124,8 @@ struct Bars {
   uint64_t empty[kAcc];       // the 8 consumer warps read an accumulator
   uint32_t tmem;
   int err;
-  float hm[2][kRows];         // second column half's (max, sum) per row, by segment parity
-  float hs[2][kRows];
+  float hm[2][3][kRows];      // column quarters 1..3: (max, sum) per row, by segment parity
+  float hs[2][3][kRows];
 };
 
 __device__ __forceinline__ void copy_pieces(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -141,15 +141,16 @@ __host__ __device__ __forceinline__ long long cta_of_unit(long long x, long long
   return ((x + 1) * G + U - 1) / U - 1;
 }
 
-// Roles: warps 0..7 read the accumulators (warp w: TMEM lane quarter w % 4,
-// i.e. rows 32 (w % 4) .. + 31, and column half w / 4 of every tile); lane 0
-// of warp 8 issues the copies and the MMAs.  Handoffs: a_full (query rows
+// Roles: warps 0..15 read the accumulators (warp w: TMEM lane quarter w % 4,
+// i.e. rows 32 (w % 4) .. + 31, and column quarter w / 4 of every tile, one
+// 64-column TMEM load a tile); lane 0 of warp 16 issues the copies and the
+// MMAs.  Handoffs: a_full (query rows
 // landed), b_full (key tiles landed), m_done (MMAs -> consumers and the
 // issuer, which then reuses the key stage, or the query rows at a row-block
 // change), empty (consumers -> issuer, accumulator free again).  Every wait
 // is bounded; a wait that gives up sets err, which stops every role, and the
 // issuer then lets every copy and MMA in flight land before the CTA ends.
-constexpr int kConsWarps = 8;
+constexpr int kConsWarps = 16;
 constexpr int kAllThreads = 32 * (kConsWarps + 1);
 
 // Work units are the pairs (row block of 128 queries, key tile of 256 keys),
@@ -295,9 +296,9 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
     __syncwarp();
   } else {
     // --------------------------------------------------------------- consumers
-    const int q = warp & 3, h = warp >> 2;
+    const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, column quarter
     const int row = 32 * q + lane;
-    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((kKeys / 2) * h);
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((kKeys / 4) * h);
     float M = kInitMax, S = 0.f;
     bool dead = false;  // warp-uniform: a wait gave up, the remaining units are skipped
     int rb = rb0, tile = t0, seg = 0;
@@ -315,17 +316,13 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
       if (!dead) {
         const int b = t % kAcc;
         tc::fence_after_sync();
-        // this thread's half of the tile's columns, 64 at a time
-#pragma unroll 1
-        for (int part = 0; part < kKeys / 128; ++part) {
-        float v[64];
-        tc::ld64(tl + (uint32_t)(b * kAccCols + 64 * part), v);
-        if (part == kKeys / 128 - 1) {
-          tc::fence_before_sync();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&br.empty[b]);
-        }
-        const float* H = Hs + (t % TT) * kKeys + (kKeys / 2) * h + 64 * part;
+        // this thread's quarter of the tile's columns
+        float v[kKeys / 4];
+        tc::ld64(tl + (uint32_t)(b * kAccCols), v);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&br.empty[b]);
+        const float* H = Hs + (t % TT) * kKeys + (kKeys / 4) * h;
 #pragma unroll
         for (int c0 = 0; c0 < 64; c0 += 32) {
           float* vv = v + c0;
@@ -356,19 +353,21 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
           S = S * ex2f(M - mn) + (s0 + s1);
           M = mn;
         }
-        }
       }
       if (tile == TT - 1 || t == L - 1) {
-        // end of this CTA's part of row block rb: the two column halves of a row meet
-        if (h == 1) {
-          br.hm[seg & 1][row] = M;
-          br.hs[seg & 1][row] = S;
+        // end of this CTA's part of row block rb: the four column quarters of a row meet
+        if (h > 0) {
+          br.hm[seg & 1][h - 1][row] = M;
+          br.hs[seg & 1][h - 1][row] = S;
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsWarps) : "memory");
         if (h == 0) {
-          const float M2 = br.hm[seg & 1][row], S2 = br.hs[seg & 1][row];
-          const float mn = fmaxf(M, M2);
-          const float St = S * ex2f(M - mn) + S2 * ex2f(M2 - mn);
+          float mn = M;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) mn = fmaxf(mn, br.hm[seg & 1][k][row]);
+          float St = S * ex2f(M - mn);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) St += br.hs[seg & 1][k][row] * ex2f(br.hm[seg & 1][k][row] - mn);
           const int i = rb * kRows + row;
           if (i < nq) {
             const int slot = (int)((long long)blockIdx.x - cta_of_unit((long long)rb * TT, U, G));
