@@ -301,6 +301,50 @@ UOT_API size_t uot_batch_workspace_size(const uot_batch* batch);
 UOT_API uot_status uot_sinkhorn_batched(const uot_batch* batch, const uot_options* opt, int32_t ti, float* f,
                                         float* g, uot_result* results, void* ws, size_t ws_bytes, void* stream);
 
+/* 1-D unregularised UOT (eps = 0, rho_i KL penalties) by Frank-Wolfe on the
+ * translation-invariant functional H_0 (Sec. 4, Alg. 2) for a batch of
+ * independent problems.  Each step computes lambda*(fb, gb) (Prop. 2), the
+ * re-weighted histograms a~ = a e^{-(fb + lambda*)/rho1},
+ * b~ = b e^{-(gb - lambda*)/rho2} (Eq. fw-updated-histo, equal masses by
+ * Prop. 1), the exact balanced 1-D OT duals (r, s) between them by one walk
+ * over the sorted points (SolveOT1D, Alg. 1, read as the north-west corner
+ * rule: the point whose remaining mass is smaller is exhausted first), and
+ * (fb, gb) <- (1 - gamma_t)(fb, gb) + gamma_t (r, s) with gamma_t = 2/(2 + t),
+ * from (fb, gb) = 0.  Outputs the translated pair (fb + lambda*, gb - lambda*).
+ * Cost |x_i - y_j|^p.  All arithmetic is FP64 on the device; one warp runs
+ * one problem. */
+typedef struct {
+  int32_t count;          /* number of problems >= 1                                      */
+  int32_t n_iter;         /* Frank-Wolfe steps >= 1                                       */
+  double p;               /* cost exponent, finite and >= 1, shared by the batch          */
+  const int32_t* n;       /* host [count]: N_k >= 1                                        */
+  const int32_t* m;       /* host [count]: M_k >= 1                                        */
+  const int64_t* x_off;   /* host [count]: first point of problem k in x, a and f (>= 0)   */
+  const int64_t* y_off;   /* host [count]: first point of problem k in y, b and g (>= 0)   */
+  const double* rho1;     /* host [count]: finite, > 0                                     */
+  const double* rho2;     /* host [count]: finite, > 0                                     */
+  const float* x;         /* device, packed; ascending within each problem                */
+  const float* a;         /* device, packed weights >= 0, positive total per problem      */
+  const float* y;
+  const float* b;
+} uot_fw1d_batch;
+
+/* Workspace bytes for uot_fw1d_batched on `batch` (0 if the batch is invalid;
+ * uot_last_error() says why). */
+UOT_API size_t uot_fw1d_workspace_size(const uot_fw1d_batch* batch);
+
+/* Runs batch->n_iter Frank-Wolfe steps on every problem.  f, g: device FP64
+ * outputs indexed like a and b (problems must not overlap there).  status:
+ * optional host [count], per problem UOT_OK, UOT_ERR_INVALID_ARG (points not
+ * ascending or not finite) or UOT_ERR_NONFINITE (a weight negative or not
+ * finite, or a side's total mass zero); such a problem's outputs are NaN.
+ * Host-side checks (sizes, parameters, pointers, workspace: 256-byte aligned,
+ * at least uot_fw1d_workspace_size bytes) fail before any device work.
+ * Synchronises the stream; returns UOT_OK when every problem is valid, else
+ * the first failing problem's status. */
+UOT_API uot_status uot_fw1d_batched(const uot_fw1d_batch* batch, double* f, double* g, int32_t* status,
+                                    void* ws, size_t ws_bytes, void* stream);
+
 /* Message describing the last error of the calling thread ("" if none). */
 UOT_API const char* uot_last_error(void);
 

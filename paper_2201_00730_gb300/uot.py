@@ -58,6 +58,13 @@ class Batch(C.Structure):
                 ("x", C.c_void_p), ("y", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p)]
 
 
+class FW1DBatch(C.Structure):
+    _fields_ = [("count", C.c_int32), ("n_iter", C.c_int32), ("p", C.c_double),
+                ("n", C.c_void_p), ("m", C.c_void_p), ("x_off", C.c_void_p), ("y_off", C.c_void_p),
+                ("rho1", C.c_void_p), ("rho2", C.c_void_p),
+                ("x", C.c_void_p), ("a", C.c_void_p), ("y", C.c_void_p), ("b", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -94,6 +101,10 @@ def lib() -> C.CDLL:
         L.uot_sinkhorn_batched.argtypes = [C.POINTER(Batch), C.POINTER(Options), C.c_int32, V, V,
                                            C.POINTER(Result), V, S, V]
         L.uot_sinkhorn_batched.restype = C.c_int
+        L.uot_fw1d_workspace_size.argtypes = [C.POINTER(FW1DBatch)]
+        L.uot_fw1d_workspace_size.restype = S
+        L.uot_fw1d_batched.argtypes = [C.POINTER(FW1DBatch), V, V, C.POINTER(C.c_int32), V, S, V]
+        L.uot_fw1d_batched.restype = C.c_int
         L.uot_kernel_launches.argtypes = []
         L.uot_kernel_launches.restype = C.c_uint64
         L.uot_profile_begin.argtypes = []
@@ -424,6 +435,52 @@ def solve_batched(problems, method: str = "ti", max_iter: int = 20000, tol: floa
     gs = [G[bo[k]:bo[k] + m[k]] for k in range(cnt)]
     return BatchOut(fs, gs, [r.iters for r in res], [bool(r.converged) for r in res],
                     [r.residual for r in res], [r.lambda_ for r in res], st)
+
+
+@dataclass
+class FW1DOut:
+    f: list            # per-problem translated potentials (device FP64 views into one packed buffer)
+    g: list
+    status: list       # per-problem status codes
+    code: int          # return code of the call
+
+
+def fw1d_batched(problems, n_iter: int, p: float = 2.0, device="cuda:0", check: bool = True) -> FW1DOut:
+    """1-D unregularised UOT by Frank-Wolfe on H_0 (Sec. 4, Alg. 2) for many problems in one call.
+
+    `problems`: sequence of objects with 1-D arrays x (n, ascending), a (n), y (m, ascending), b (m) and
+    floats rho1, rho2.  Inputs are packed into device arrays here (marshalling only).  With check=False a
+    failing problem is reported in `status` instead of raising.
+    """
+    import numpy as np
+    dev = torch.device(device)
+    cnt = len(problems)
+    n = np.array([np.asarray(q.x).size for q in problems], dtype=np.int32)
+    m = np.array([np.asarray(q.y).size for q in problems], dtype=np.int32)
+    xo = np.concatenate([[0], np.cumsum(n.astype(np.int64))[:-1]]).astype(np.int64)
+    yo = np.concatenate([[0], np.cumsum(m.astype(np.int64))[:-1]]).astype(np.int64)
+    r1 = np.array([q.rho1 for q in problems], dtype=np.float64)
+    r2 = np.array([q.rho2 for q in problems], dtype=np.float64)
+    cat = lambda vs: torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [np.asarray(v, dtype=np.float32).ravel() for v in vs]))).to(dev)
+    X, A = cat([q.x for q in problems]), cat([q.a for q in problems])
+    Y, B = cat([q.y for q in problems]), cat([q.b for q in problems])
+    host = [n, m, xo, yo, r1, r2]
+    bt = FW1DBatch(cnt, int(n_iter), float(p), *[h.ctypes.data for h in host],
+                   X.data_ptr(), A.data_ptr(), Y.data_ptr(), B.data_ptr())
+    nbytes = lib().uot_fw1d_workspace_size(C.byref(bt))
+    if nbytes == 0:
+        raise UOTError(1, lib().uot_last_error().decode())
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    F = torch.empty(X.numel(), dtype=torch.float64, device=dev)
+    G = torch.empty(Y.numel(), dtype=torch.float64, device=dev)
+    stat = (C.c_int32 * cnt)()
+    code = lib().uot_fw1d_batched(C.byref(bt), _ptr(F), _ptr(G), stat, _ptr(ws), ws.numel(), _stream())
+    if check:
+        _check(code)
+    fs = [F[xo[k]:xo[k] + n[k]] for k in range(cnt)]
+    gs = [G[yo[k]:yo[k] + m[k]] for k in range(cnt)]
+    return FW1DOut(fs, gs, list(stat), code)
 
 
 def version() -> str:

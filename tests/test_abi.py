@@ -97,3 +97,53 @@ def test_argument_errors_without_device_work(L):
     assert L.uot_workspace_size(C.byref(dense_unaligned)) == 0
     assert b"16-byte" in L.uot_last_error()
     assert L.uot_version().startswith(b"uot")
+
+
+def test_fw1d_layout_and_argument_errors(L):
+    """uot_fw1d_batch agrees between header and binding; bad batches fail on the host."""
+    import numpy as np
+    from paper_2201_00730_gb300 import uot
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "uot.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(uot_fw1d_batch), offsetof(uot_fw1d_batch, p), offsetof(uot_fw1d_batch, rho2),
+         offsetof(uot_fw1d_batch, b));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    B = uot.FW1DBatch
+    assert vals == [C.sizeof(B), B.p.offset, B.rho2.offset, B.b.offset]
+
+    n = np.array([3, 4], dtype=np.int32)
+    m = np.array([2, 5], dtype=np.int32)
+    xo = np.array([0, 3], dtype=np.int64)
+    yo = np.array([0, 2], dtype=np.int64)
+    r1 = np.array([1.0, 0.5])
+    r2 = np.array([1.0, 2.0])
+    host = [n, m, xo, yo, r1, r2]
+    ok = B(2, 10, 2.0, *[h.ctypes.data for h in host], 256, 256, 256, 256)
+    nbytes = L.uot_fw1d_workspace_size(C.byref(ok))
+    assert nbytes >= 6 * 8 * 7  # six FP64 working vectors over 7 points a side
+    assert L.uot_fw1d_workspace_size(None) == 0
+    for field, val, msg in [("count", 0, b"count"), ("n_iter", 0, b"n_iter"), ("p", 0.5, b"p must")]:
+        bad = B(2, 10, 2.0, *[h.ctypes.data for h in host], 256, 256, 256, 256)
+        setattr(bad, field, val)
+        assert L.uot_fw1d_workspace_size(C.byref(bad)) == 0 and msg in L.uot_last_error()
+    r_bad = np.array([1.0, -1.0])
+    bad = B(2, 10, 2.0, n.ctypes.data, m.ctypes.data, xo.ctypes.data, yo.ctypes.data, r1.ctypes.data,
+            r_bad.ctypes.data, 256, 256, 256, 256)
+    assert L.uot_fw1d_workspace_size(C.byref(bad)) == 0 and b"rho" in L.uot_last_error()
+    st = L.uot_fw1d_batched(C.byref(ok), None, 256, None, 256, 1 << 30, None)
+    assert st == 1 and b"f and g" in L.uot_last_error()
+    st = L.uot_fw1d_batched(C.byref(ok), 256, 256, None, None, 1 << 30, None)
+    assert st == 2
+    st = L.uot_fw1d_batched(C.byref(ok), 256, 256, None, 256, nbytes - 1, None)
+    assert st == 2 and b"too small" in L.uot_last_error()
