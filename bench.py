@@ -338,12 +338,14 @@ def run_gpu(args):
         out["time_to_tol"] = time_to_tol(U, W, dev, args)
         out["roofline_dense"] = dense_roofline(U, W, dev, p)
         out["batched"] = batched_leg(U, W)
+        out["fw1d"] = fw1d_leg(U, W)
         out["workloads"] = workload_legs(U, W, dev)
     if rank == 0 and world == 1 and not args.no_extras:
         rate, dt, it, ns = oracle_sample_rate(p)
         out["cpu_baseline"] = {"value": round(rate, 5), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                                "sample": f"FP64 oracle H-Sinkhorn iterations on the first {ns} points of each cloud "
-                                         f"({it} iterations, {dt:.1f} s)"}
+                                         f"({it} iterations, {dt:.1f} s)",
+                               "fw1d": oracle_fw1d_rate(W)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -376,6 +378,46 @@ def time_to_tol(U, W, dev, args):
             row["speedup"] = f"> {row['plain']['seconds'] / row['ti']['seconds']:.1f} (plain not converged at cap)"
         res[f"rho={rho:g}"] = row
     return res
+
+
+def fw1d_leg(U, W, steps: int = 1000):
+    """1-D unregularised UOT by Frank-Wolfe on H_0 (uot_fw1d_batched): 1024 problems with N = M = 200,
+    rho = 1.  Device time of `steps` steps = CUDA-event time of a (200 + steps)-step call minus that of a
+    200-step call (the binding packs the inputs on every call; the difference leaves the steps alone)."""
+    import torch
+    probs = W.config_fw1d()
+    U.fw1d_batched(probs[:32], 5, 2.0)
+    torch.cuda.synchronize()
+
+    def timed(k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        U.fw1d_batched(probs, k, 2.0)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    base = timed(200)
+    dt = timed(200 + steps) - base
+    pts = 2 * 200
+    return {"workload": f"1024 problems, N = M = 200, rho = 1, p = 2, {steps} FW steps (2/(2+t)), sorted "
+                        "synthetic 1-D mixtures", "seconds": round(dt, 4), "seconds_200_steps_call": round(base, 4),
+            "problem_steps_per_s": round(len(probs) * steps / dt, 1),
+            "us_per_step": round(dt / steps * 1e6, 2),
+            "walk_points_per_s_M": round(len(probs) * steps * pts / dt / 1e6, 1)}
+
+
+def oracle_fw1d_rate(W, k: int = 30):
+    """Problem-steps/s of the FP64 Frank-Wolfe oracle on one problem of the fw1d workload (one host core)."""
+    import numpy as np
+    from oracle import fw1d as FW
+    q = W.config_fw1d(count=1)[0]
+    f64 = lambda v: np.asarray(v, dtype=np.float64)
+    t0 = time.perf_counter()
+    FW.fw_uot_1d(f64(q.x), f64(q.a), f64(q.y), f64(q.b), q.rho1, q.rho2, k, 2.0)
+    dt = time.perf_counter() - t0
+    return {"value": round(k / dt, 2), "unit": "problem-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle fw_uot_1d on problem 0 of the fw1d workload, {k} steps, {dt:.2f} s"}
 
 
 def batched_leg(U, W):

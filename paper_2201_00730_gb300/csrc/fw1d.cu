@@ -23,7 +23,8 @@
 namespace uot {
 namespace {
 
-constexpr int kFWWarps = 4;  // problems per CTA
+constexpr int kFWWarps = 4;         // problems per CTA
+constexpr int kFWSmemPoints = 1536;  // a problem with N + M <= this keeps a~, b~ in shared memory
 
 struct FWProb {
   long long xo, yo;
@@ -63,6 +64,7 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
        const float* __restrict__ a, const float* __restrict__ y, const float* __restrict__ b, double* fb_all,
        double* gb_all, double* at_all, double* bt_all, double* r_all, double* s_all, double* __restrict__ f,
        double* __restrict__ g, int* __restrict__ status) {
+  extern __shared__ double fw_smem[];
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * kFWWarps + (threadIdx.x >> 5);
   if (k >= count) return;  // whole warp
@@ -71,6 +73,11 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
   const float *X = x + P.xo, *A = a + P.xo, *Y = y + P.yo, *B = b + P.yo;
   double *FB = fb_all + P.xo, *AT = at_all + P.xo, *R = r_all + P.xo, *F = f + P.xo;
   double *GB = gb_all + P.yo, *BT = bt_all + P.yo, *S = s_all + P.yo, *G = g + P.yo;
+  if (n + m <= kFWSmemPoints) {
+    // the walk reads a~ and b~ right after the other lanes wrote them: keep them on chip
+    AT = fw_smem + (threadIdx.x >> 5) * kFWSmemPoints;
+    BT = AT + n;
+  }
 
   // inputs: weights finite and >= 0 with positive totals, points finite and ascending
   bool bad_w = false, bad_x = false;
@@ -230,7 +237,7 @@ uot_status uot_fw1d_batched(const uot_fw1d_batch* b, double* f, double* g, int32
   int* d_status = reinterpret_cast<int*>(base + L.status);
   FWCUDA(cudaMemcpyAsync(d_probs, probs.data(), sizeof(FWProb) * count, cudaMemcpyHostToDevice, st));
   const int blocks = (count + kFWWarps - 1) / kFWWarps;
-  k_fw1d<<<blocks, 32 * kFWWarps, 0, st>>>(
+  k_fw1d<<<blocks, 32 * kFWWarps, sizeof(double) * kFWWarps * kFWSmemPoints, st>>>(
       d_probs, count, b->n_iter, b->p, b->x, b->a, b->y, b->b, reinterpret_cast<double*>(base + L.fb),
       reinterpret_cast<double*>(base + L.gb), reinterpret_cast<double*>(base + L.at),
       reinterpret_cast<double*>(base + L.bt), reinterpret_cast<double*>(base + L.r),

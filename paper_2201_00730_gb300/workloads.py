@@ -132,6 +132,25 @@ def config4(count: int = 4096, lo: int = 64, hi: int = 4096, seed: int = 1004):
     return out
 
 
+def config_fw1d(count: int = 1024, n: int = 200, seed: int = 1006, rho: float = 1.0):
+    """`count` independent 1-D problems of the size of the paper's FW-vs-Sinkhorn comparison
+    (Sec. 4: N = M = 200 histograms, rho = 1): sorted points, x from a two-component Gaussian
+    mixture, y from a shifted one, Exp(1) weights rescaled to masses 1 and 1.5.  Each entry has
+    x, a, y, b (float32, x and y ascending) and rho1 = rho2 = rho."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        cx = rng.choice([-0.5, 0.5], size=n) + 0.2 * rng.standard_normal(n)
+        cy = rng.choice([-0.2, 0.8], size=n) + 0.25 * rng.standard_normal(n)
+        a = rng.exponential(1.0, n)
+        b = rng.exponential(1.0, n)
+        out.append(SimpleNamespace(x=np.sort(cx).astype(np.float32), a=(a / a.sum()).astype(np.float32),
+                                   y=np.sort(cy).astype(np.float32), b=(1.5 * b / b.sum()).astype(np.float32),
+                                   rho1=rho, rho2=rho))
+    return out
+
+
 def config5(n: int = 262144) -> Problem:
     """3-D uniform points in the unit cube, N = M = 262144, masses 1.0 / 1.3, eps = 1e-3,
     rho1 = rho2 = 1."""

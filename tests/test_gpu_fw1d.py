@@ -41,13 +41,14 @@ def scale(q, p):
 
 
 BATCH = [(1, 1, 1.0, 1.0), (1, 7, 0.5, 2.0), (9, 1, 1.0, 0.3), (40, 33, 0.1, 1.0), (200, 200, 1.0, 1.0),
-         (5, 300, 3.0, 0.7), (257, 31, 10.0, 10.0)]
+         (5, 300, 3.0, 0.7), (257, 31, 10.0, 10.0), (1000, 700, 1.0, 2.0)]
 
 
 @pytest.mark.parametrize("p", [2.0, 1.0, 1.5])
 @pytest.mark.parametrize("T", [1, 3, 25])
 def test_fw1d_iterates_match_oracle(U, p, T):
-    """A ragged batch (single points, one-sided singletons, zero weights, rho1 != rho2) after T steps."""
+    """A ragged batch (single points, one-sided singletons, zero weights, rho1 != rho2, one problem too
+    large for the on-chip histograms) after T steps."""
     probs = [make(n, m, seed=100 * k + int(10 * p), rho1=r1, rho2=r2) for k, (n, m, r1, r2) in enumerate(BATCH)]
     out = U.fw1d_batched(probs, T, p)
     assert out.status == [0] * len(probs)
