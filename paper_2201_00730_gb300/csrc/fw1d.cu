@@ -8,8 +8,8 @@
 // reached point's potential is the current pair's cost minus the other side's
 // current potential), and all lanes take the step
 //   (fb, gb) <- (1 - gamma_t)(fb, gb) + gamma_t (r, s),  gamma_t = 2 / (2 + t).
-// The walk is sequential by nature (O(N + M) dependent steps); the batch
-// supplies the parallelism.  Working vectors live in the workspace, indexed by
+// The walk is sequential by nature (O(N + M) dependent steps, one FP64 add each;
+// the potentials in float pairs); the batch supplies the parallelism.  Working vectors live in the workspace, indexed by
 // the problems' offsets.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "ffloat.cuh"
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -54,9 +55,13 @@ __device__ double log_dot_exp_neg(const float* __restrict__ w, const double* v, 
   return mx + log(sm);
 }
 
-__device__ __forceinline__ double cost_p(double d, double p) {
-  d = fabs(d);
-  return p == 2.0 ? d * d : (p == 1.0 ? d : pow(d, p));
+// |x - y|^p as a float pair: x - y exactly (two_sum), then its square (p = 2),
+// its magnitude (p = 1), or an FP64 power for other p
+__device__ __forceinline__ ffl::ff cost_ff(float xi, float yj, double p) {
+  const ffl::ff d = ffl::two_sum(xi, -yj);
+  if (p == 2.0) return ffl::mul(d, d);
+  if (p == 1.0) return d.hi < 0.f ? ffl::neg(d) : d;
+  return ffl::from_double(pow(fabs((double)d.hi + (double)d.lo), p));
 }
 
 __global__ void __launch_bounds__(32 * kFWWarps)
@@ -115,35 +120,48 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
     for (int j = lane; j < m; j += 32) BT[j] = B[j] > 0.f ? (double)B[j] * exp(-(GB[j] - lam) / r2) : 0.0;
     __syncwarp();
     if (lane == 0) {
-      // SolveOT1D: duals of the north-west corner coupling
+      // SolveOT1D, the duals of the north-west corner coupling.  The masses not yet
+      // transported enter only through dm = fl(m_j - m_i): "point i is exhausted first"
+      // is m_i <= m_j, i.e. dm >= 0, and the next dm is fl(dm - a~_{i+1}) after i moves,
+      // fl(dm + b~_{j+1}) after j moves, the same roundings as tracking (m_i, m_j) in FP64,
+      // so the walk takes the same branches with one dependent FP64 add a step.  The
+      // potentials run in float pairs on the FP32 pipes; the next point and mass of both
+      // sides are loaded ahead of each decision.
+      float2* R2 = reinterpret_cast<float2*>(R);
+      float2* S2 = reinterpret_cast<float2*>(S);
       int i = 0, j = 0;
-      double xi = X[0], yj = Y[0];
-      double ri = 0.0, sj = cost_p(xi - yj, p);
-      R[0] = ri;
-      S[0] = sj;
-      double ma = AT[0], mb = BT[0];  // masses of points i and j not yet transported
+      float xi = X[0], yj = Y[0];
+      ffl::ff ri{0.f, 0.f}, sj = cost_ff(xi, yj, p);
+      R2[0] = make_float2(0.f, 0.f);
+      S2[0] = make_float2(sj.hi, sj.lo);
+      double dm = BT[0] - AT[0];
+      double na = n > 1 ? AT[1] : 0.0, nb = m > 1 ? BT[1] : 0.0;
+      float nx = n > 1 ? X[1] : 0.f, ny = m > 1 ? Y[1] : 0.f;
       while (i < n - 1 || j < m - 1) {
-        if ((ma <= mb && i < n - 1) || j == m - 1) {
-          mb -= ma;
+        // dm is never -0 (masses are >= +0), so its sign bit decides dm >= 0 without an FP64 compare
+        if ((__double_as_longlong(dm) >= 0 && i < n - 1) || j == m - 1) {
           ++i;
-          xi = X[i];
-          ri = cost_p(xi - yj, p) - sj;
-          R[i] = ri;
-          ma = AT[i];
+          dm -= na;
+          xi = nx;
+          if (i + 1 < n) { na = AT[i + 1]; nx = X[i + 1]; }
+          ri = ffl::add(cost_ff(xi, yj, p), ffl::neg(sj));
+          R2[i] = make_float2(ri.hi, ri.lo);
         } else {
-          ma -= mb;
           ++j;
-          yj = Y[j];
-          sj = cost_p(xi - yj, p) - ri;
-          S[j] = sj;
-          mb = BT[j];
+          dm += nb;
+          yj = ny;
+          if (j + 1 < m) { nb = BT[j + 1]; ny = Y[j + 1]; }
+          sj = ffl::add(cost_ff(xi, yj, p), ffl::neg(ri));
+          S2[j] = make_float2(sj.hi, sj.lo);
         }
       }
     }
     __syncwarp();
     const double gm = 2.0 / (2.0 + (double)t);
-    for (int i = lane; i < n; i += 32) FB[i] = (1.0 - gm) * FB[i] + gm * R[i];
-    for (int j = lane; j < m; j += 32) GB[j] = (1.0 - gm) * GB[j] + gm * S[j];
+    const float2* R2 = reinterpret_cast<const float2*>(R);
+    const float2* S2 = reinterpret_cast<const float2*>(S);
+    for (int i = lane; i < n; i += 32) FB[i] = (1.0 - gm) * FB[i] + gm * ((double)R2[i].x + (double)R2[i].y);
+    for (int j = lane; j < m; j += 32) GB[j] = (1.0 - gm) * GB[j] + gm * ((double)S2[j].x + (double)S2[j].y);
     __syncwarp();
   }
   for (int i = lane; i < n; i += 32) F[i] = FB[i] + lam;
