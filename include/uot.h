@@ -311,8 +311,10 @@ UOT_API uot_status uot_sinkhorn_batched(const uot_batch* batch, const uot_option
  * rule: the point whose remaining mass is smaller is exhausted first), and
  * (fb, gb) <- (1 - gamma_t)(fb, gb) + gamma_t (r, s) with gamma_t = 2/(2 + t),
  * from (fb, gb) = 0.  Outputs the translated pair (fb + lambda*, gb - lambda*).
- * Cost |x_i - y_j|^p.  All arithmetic is FP64 on the device; one warp runs
- * one problem. */
+ * Cost |x_i - y_j|^p.  lambda*, the histograms, the walk's mass bookkeeping
+ * (hence its branches) and the step are FP64 on the device; the walk's
+ * potentials are float pairs (about 2^-44 relative per operation).  One warp
+ * runs one problem. */
 typedef struct {
   int32_t count;          /* number of problems >= 1                                      */
   int32_t n_iter;         /* Frank-Wolfe steps >= 1                                       */
