@@ -1,7 +1,9 @@
 /*
  * uot.h -- C ABI of libuot: entropic unbalanced optimal transport with
  * rho*KL marginal penalties on one GB300 (sm_103a), solved by log-domain
- * Sinkhorn and by translation-invariant Sinkhorn (H-Sinkhorn).
+ * Sinkhorn and by translation-invariant Sinkhorn (H-Sinkhorn, also G-Sinkhorn
+ * and Anderson extrapolation), and, for 1-D problems at eps = 0, by
+ * Frank-Wolfe on the translation-invariant functional (uot_fw1d_batched).
  *
  * Method: Sejourne, Vialard, Peyre, "Faster Unbalanced Optimal Transport:
  * Translation invariant Sinkhorn and 1-D Frank-Wolfe" (AISTATS 2022).
