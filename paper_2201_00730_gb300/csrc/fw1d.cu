@@ -1,5 +1,6 @@
 // 1-D unregularised UOT by Frank-Wolfe on H_0 (Sec. 4, Alg. 2), batched: one
-// warp per problem, FP64 throughout.  Per step the warp computes
+// warp per problem; FP64 except the walk's potentials (float pairs).  Per step
+// the warp computes
 //   lambda* = rho1 rho2 / (rho1 + rho2) (log<a, e^{-fb/rho1}> - log<b, e^{-gb/rho2}>)   (Prop. 2)
 //   a~ = a e^{-(fb + lambda*)/rho1},  b~ = b e^{-(gb - lambda*)/rho2}              (Eq. fw-updated-histo)
 // with all lanes, then lane 0 walks the two sorted point lists once to get the
@@ -8,9 +9,10 @@
 // reached point's potential is the current pair's cost minus the other side's
 // current potential), and all lanes take the step
 //   (fb, gb) <- (1 - gamma_t)(fb, gb) + gamma_t (r, s),  gamma_t = 2 / (2 + t).
-// The walk is sequential by nature (O(N + M) dependent steps, one FP64 add each;
-// the potentials in float pairs); the batch supplies the parallelism.  Working vectors live in the workspace, indexed by
-// the problems' offsets.
+// The walk is sequential by nature (O(N + M) dependent steps, one FP64 add
+// each); the batch supplies the parallelism.  Working vectors live in the
+// workspace, indexed by the problems' offsets (a~ and b~ in shared memory when
+// the problem is small enough).
 #include <cuda_runtime.h>
 #include <math.h>
 
