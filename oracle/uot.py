@@ -202,6 +202,39 @@ def primal_value(C, a, b, pi, eps: float, rho1: float, rho2: float) -> torch.Ten
             + rho1 * kl_div(pi.sum(1), a) + rho2 * kl_div(pi.sum(0), b))
 
 
+def dual_from_softmin(a, b, f, g, S, eps: float, rho1: float, rho2: float) -> torch.Tensor:
+    """F_eps(f, g) of Eq. (eq-dual-uot-kl) from the row softmins S_i = Smin_b^eps(C(x_i, .) - g).
+
+    The double sum of the dual collapses over j by the definition of Smin (Sec. 3):
+    sum_j b_j e^{(g_j - C_ij)/eps} = e^{-S_i/eps}, so
+        F = <a, rho1 (1 - e^{-f/rho1})> + <b, rho2 (1 - e^{-g/rho2})>
+            - eps sum_i a_i e^{(f_i - S_i)/eps} + eps m(a) m(b).
+    Only O(N + M) work once S is known, for problems whose N x M cost cannot be formed.
+    """
+    a, b, f, g, S = map(_t, (a, b, f, g, S))
+    t1 = (a * rho1 * (1.0 - torch.exp(-f / rho1))).sum()
+    t2 = (b * rho2 * (1.0 - torch.exp(-g / rho2))).sum()
+    t3 = eps * ((a * torch.exp((f - S) / eps)).sum() - a.sum() * b.sum())
+    return t1 + t2 - t3
+
+
+def primal_from_softmins(a, b, f, g, S, Sp, eps: float, rho1: float, rho2: float) -> torch.Tensor:
+    """Objective of Eq. (eq-primal-uot-kl) at the plan pi_ij = a_i b_j e^{(f_i + g_j - C_ij)/eps}
+    from the row and column softmins S_i = Smin_b^eps(C(x_i, .) - g), S'_j = Smin_a^eps(C(., y_j) - f).
+
+    Its marginals are pi1_i = a_i e^{(f_i - S_i)/eps} and pi2_j = b_j e^{(g_j - S'_j)/eps}
+    (definition of Smin), and log(pi_ij / (a_i b_j)) = (f_i + g_j - C_ij)/eps turns
+    <pi, C> + eps KL(pi | a(x)b) into <pi1, f> + <pi2, g> - eps m(pi) + eps m(a) m(b), so
+        P = <pi1, f> + <pi2, g> - eps m(pi) + eps m(a) m(b) + rho1 KL(pi1 | a) + rho2 KL(pi2 | b).
+    """
+    a, b, f, g, S, Sp = map(_t, (a, b, f, g, S, Sp))
+    pi1 = a * torch.exp((f - S) / eps)
+    pi2 = b * torch.exp((g - Sp) / eps)
+    mpi = pi1.sum()
+    return ((pi1 * f).sum() + (pi2 * g).sum() - eps * mpi + eps * a.sum() * b.sum()
+            + rho1 * kl_div(pi1, a) + rho2 * kl_div(pi2, b))
+
+
 def fixed_point_residual(C, a, b, f, g, eps: float, rho1: float, rho2: float) -> torch.Tensor:
     """Sup-norm violation of the F-Sinkhorn fixed-point equations by (f, g):
 

@@ -208,6 +208,16 @@ __device__ __forceinline__ ffl::ff scale2(ffl::ff a, int k) {
   return ffl::ff{a.hi * sc, a.lo * sc};
 }
 
+// Adds the mass term 2^y (y a float pair, |y| < 1e9) to the accumulator: the sum
+// is kept against the integer reference ceil(y) of its largest term, so every
+// rescaling is by an exact power of two.
+__device__ __forceinline__ void mass_add(RowAcc& a, const ffl::ff& y, const ffl::Exp2Table& tab) {
+  const int yr = (int)ceilf(y.hi);
+  if (a.ref == INT_MIN) a.ref = yr;
+  else if (yr > a.ref) { a.sum = scale2(a.sum, yr - a.ref); a.ref = yr; }
+  a.sum = ffl::add(a.sum, ffl::exp2(ffl::add(y, (float)(-a.ref)), tab));
+}
+
 // Half-step of one query row from its merged log-sum-exp M + L (log2 units).
 __device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int i, float M, float L, const Pre& p,
                                        RowAcc& a) {
@@ -239,10 +249,7 @@ __device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int 
       a.bad = 1;
       return;
     }
-    const int yr = (int)ceilf(y.hi);
-    if (a.ref == INT_MIN) a.ref = yr;
-    else if (yr > a.ref) { a.sum = scale2(a.sum, yr - a.ref); a.ref = yr; }
-    a.sum = add(a.sum, exp2(add(y, (float)(-a.ref)), *c.tab));
+    mass_add(a, y, *c.tab);
   }
 }
 

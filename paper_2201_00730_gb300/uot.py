@@ -392,14 +392,33 @@ class BatchOut:
     residual: list
     lam: list
     status: int
+    device_s: float | None = None   # CUDA-event time of the library call on its stream (timing=True)
+
+
+_side_streams = {}
+
+
+def _graph_stream(dev):
+    """A non-default stream for calls that capture CUDA graphs (capture is impossible on the legacy
+    default stream): the current stream if it is not the default one, else one side stream per device."""
+    cur = torch.cuda.current_stream(dev)
+    if cur.cuda_stream != 0:
+        return cur
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    if key not in _side_streams:
+        _side_streams[key] = torch.cuda.Stream(device=dev)
+    return _side_streams[key]
 
 
 def solve_batched(problems, method: str = "ti", max_iter: int = 20000, tol: float = 1e-6,
-                  check_every: int = 10, device="cuda:0") -> BatchOut:
+                  check_every: int = 10, device="cuda:0", graph: bool = True, timing: bool = False) -> BatchOut:
     """Solve many independent point-cloud problems in one batched call.
 
     `problems`: sequence of objects with numpy/torch arrays x (n x d), y (m x d), a (n), b (m) and floats
     eps, rho1, rho2 (d in 1..3, p = 2).  Inputs are packed into device arrays here (marshalling only).
+    graph=True runs the call on a non-default stream, where the library captures each chunk of
+    check_every iterations once as a CUDA graph and replays it; graph=False passes the legacy default
+    stream, on which the library launches every half-step itself (same kernels, same results).
     """
     import numpy as np
     dev = torch.device(device)
@@ -428,13 +447,32 @@ def solve_batched(problems, method: str = "ti", max_iter: int = 20000, tol: floa
     G = torch.empty(B.numel(), dtype=torch.float32, device=dev)
     res = (Result * cnt)()
     opt = Options(int(max_iter), int(check_every), float(tol), 0, 0, None)
+    cur = torch.cuda.current_stream(dev)
+    if graph:
+        side = _graph_stream(dev)
+        side.wait_stream(cur)
+        handle = C.c_void_p(side.cuda_stream)
+    else:
+        side = torch.cuda.default_stream(dev)
+        handle = C.c_void_p(0)
+    if timing:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(side)
     st = lib().uot_sinkhorn_batched(C.byref(bt), C.byref(opt), 1 if method == "ti" else 0, _ptr(F), _ptr(G),
-                                    res, _ptr(ws), ws.numel(), _stream())
+                                    res, _ptr(ws), ws.numel(), handle)
+    if timing:
+        ev1.record(side)
+    if side is not cur:
+        cur.wait_stream(side)
     _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
     fs = [F[ao[k]:ao[k] + n[k]] for k in range(cnt)]
     gs = [G[bo[k]:bo[k] + m[k]] for k in range(cnt)]
+    dsec = None
+    if timing:
+        ev1.synchronize()
+        dsec = ev0.elapsed_time(ev1) * 1e-3
     return BatchOut(fs, gs, [r.iters for r in res], [bool(r.converged) for r in res],
-                    [r.residual for r in res], [r.lambda_ for r in res], st)
+                    [r.residual for r in res], [r.lambda_ for r in res], st, dsec)
 
 
 @dataclass

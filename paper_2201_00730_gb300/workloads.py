@@ -176,3 +176,21 @@ def dense_cost_f32(x: np.ndarray, y: np.ndarray) -> np.ndarray:
         d = xi[:, None, :] - yy[None, :, :]
         out[i0:i0 + step] = (d * d).sum(-1)
     return out
+
+
+def dense_cost_f32_device(x: np.ndarray, y: np.ndarray, device, rows_per_block: int = 2048):
+    """dense_cost_f32 built on `device` (a torch device) for matrices too large to build on the
+    host quickly: the same squared distances, each coordinate difference and square in float64,
+    summed over the coordinates in order, rounded once to float32."""
+    import torch
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(device=device, dtype=torch.float64)
+    yd = torch.from_numpy(np.ascontiguousarray(y)).to(device=device, dtype=torch.float64)
+    out = torch.empty((x.shape[0], y.shape[0]), dtype=torch.float32, device=device)
+    for i0 in range(0, x.shape[0], rows_per_block):
+        xi = xd[i0:i0 + rows_per_block]
+        acc = torch.zeros((xi.shape[0], yd.shape[0]), dtype=torch.float64, device=device)
+        for k in range(x.shape[1]):
+            d = xi[:, k:k + 1] - yd[None, :, k]
+            acc += d * d
+        out[i0:i0 + rows_per_block] = acc.to(torch.float32)
+    return out

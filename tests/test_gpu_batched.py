@@ -90,3 +90,25 @@ def test_batched_reports_bad_weights(U):
     with pytest.raises(U.UOTError) as ei:
         U.solve_batched(probs, "ti", max_iter=5)
     assert ei.value.status == 4
+
+
+def test_batched_graph_replay_matches_plain_launches(U):
+    """The CUDA-graph path (a non-default stream: each chunk of check_every iterations captured once
+    and replayed) against the plain-launch path (legacy default stream), on the same batch: same
+    iteration counts, same potentials within the potentials' tolerance; also under a caller's
+    torch.cuda.Stream."""
+    probs = W.config4(count=40, lo=64, hi=2048, seed=77)
+    rg = U.solve_batched(probs, "ti", max_iter=20000, tol=1e-6, check_every=10, graph=True)
+    rp = U.solve_batched(probs, "ti", max_iter=20000, tol=1e-6, check_every=10, graph=False)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rs = U.solve_batched(probs, "ti", max_iter=20000, tol=1e-6, check_every=10)
+    torch.cuda.synchronize()
+    assert all(rg.converged) and all(rp.converged) and all(rs.converged)
+    for k, p in enumerate(probs):
+        assert rg.iters[k] == rp.iters[k] == rs.iters[k], (k, rg.iters[k], rp.iters[k], rs.iters[k])
+        for other in (rp, rs):
+            ok, e = close(rg.f[k], other.f[k].double().cpu(), p.eps)
+            assert ok, (k, "f", e)
+            ok, e = close(rg.g[k], other.g[k].double().cpu(), p.eps)
+            assert ok, (k, "g", e)

@@ -42,6 +42,13 @@ def spec_of(U, p, dense=False, ordering=0):
 ORDERINGS = pytest.mark.parametrize("ordering", [1, 3, 2, 0], ids=["tiled", "tiled_tc", "direct", "auto"])
 
 
+def lam_tol(eps, ordering, T):
+    """Bound on |lambda_gpu - lambda_oracle| after T iterations: 1e-4 eps on the CUDA-core
+    sweeps; on the tensor-core sweep (ordering 3) 1e-4 eps per 60 iterations, for the
+    translation drift of the pair (fb, gb) that lambda* absorbs (Sec. 3, translation invariance)."""
+    return 1e-4 * eps * (max(1.0, T / 60) if ordering == 3 else 1.0)
+
+
 def pot_tol(eps, ref):
     ref = torch.as_tensor(ref, dtype=torch.float64)
     return 1e-4 * eps + 2.0 * 2.0 ** -23 * ref.abs()
@@ -134,10 +141,12 @@ def test_config1_1000_iterations_match_golden(U, method, ordering):
         # lambda* of Prop. 2 is defined on the pair (fb, gb), which H-Sinkhorn fixes only up to a
         # common translation that the iteration neither damps nor amplifies: rounding moves it a
         # little every iteration and lambda* absorbs the move, while Phi(fb, gb) = (f, g) stays put.
-        # After 1000 iterations lambda is therefore compared at 1e-4 eps per 60 iterations (the
-        # iterate tests compare it at 1e-4 eps up to T = 60), and the translated pair must satisfy
-        # the mass equality of Prop. 1 that lambda* exists to enforce.
-        assert abs(r.lam - d["ti"]["lambda"]) < 1e-4 * pr.eps * (1000 / 60)
+        # On the CUDA-core sweeps that drift stays below 1e-4 eps after 1000 iterations; the
+        # tensor-core sweep (ordering 3) rounds its exponents differently and drifts further, so
+        # there lambda is compared at 1e-4 eps per 60 iterations (the iterate tests compare it at
+        # 1e-4 eps up to T = 60).  On every path the translated pair must satisfy the mass
+        # equality of Prop. 1 that lambda* exists to enforce.
+        assert abs(r.lam - d["ti"]["lambda"]) < lam_tol(pr.eps, ordering, 1000)
         f, g = r.f.double().cpu(), r.g.double().cpu()
         A = (O._t(pr.a) * torch.exp(-f / pr.rho1)).sum().item()
         B = (O._t(pr.b) * torch.exp(-g / pr.rho2)).sum().item()
@@ -159,7 +168,7 @@ def test_config1_g_sinkhorn_1000_iterations(U, ordering):
     assert r.iters == 1000
     assert_pot_close(r.f, ref.f, pr.eps, "g-sinkhorn f")
     assert_pot_close(r.g, ref.g, pr.eps, "g-sinkhorn g")
-    assert abs(r.lam - ref.lam) < 1e-4 * pr.eps * (1000 / 60)
+    assert abs(r.lam - ref.lam) < lam_tol(pr.eps, ordering, 1000)
     f, g = r.f.double().cpu(), r.g.double().cpu()
     A = (O._t(pr.a) * torch.exp(-f / pr.rho1)).sum().item()
     B = (O._t(pr.b) * torch.exp(-g / pr.rho2)).sum().item()

@@ -82,6 +82,51 @@ def test_kl_and_primal_brute_force():
     assert O.kl_div([0.1], [0.0]).item() == math.inf
 
 
+def test_dual_and_primal_from_softmins_brute_force():
+    """The O(N + M) forms of the dual (Eq. eq-dual-uot-kl) and of the primal (Eq. eq-primal-uot-kl)
+    at an arbitrary pair (f, g), not an optimum, against the double sums written out term by term."""
+    p, C, a, b = tiny(n=5, m=4, eps=0.3, rho1=0.7, rho2=1.9)
+    f = [0.11, -0.32, 0.05, 0.4, -0.07]
+    g = [-0.2, 0.15, 0.33, -0.01]
+    eps, r1, r2 = p.eps, p.rho1, p.rho2
+    A, B = [float(v) for v in a], [float(v) for v in b]
+    Cl = [[float(C[i, j]) for j in range(4)] for i in range(5)]
+    # dual: sum_i a_i phi-part + sum_j b_j phi-part - eps sum_ij a_i b_j (e^{(f_i + g_j - C_ij)/eps} - 1)
+    ref = (sum(A[i] * r1 * (1 - math.exp(-f[i] / r1)) for i in range(5))
+           + sum(B[j] * r2 * (1 - math.exp(-g[j] / r2)) for j in range(4))
+           - eps * sum(A[i] * B[j] * (math.exp((f[i] + g[j] - Cl[i][j]) / eps) - 1)
+                       for i in range(5) for j in range(4)))
+    S = O.smin_rows(C, b, g, eps)
+    Sp = O.smin_cols(C, a, f, eps)
+    assert abs(O.dual_from_softmin(a, b, f, g, S, eps, r1, r2).item() - ref) < 1e-13
+    # primal at the plan pi_ij = a_i b_j e^{(f_i + g_j - C_ij)/eps}: <pi, C> + eps KL(pi|ab) + rho KLs
+    pi = [[A[i] * B[j] * math.exp((f[i] + g[j] - Cl[i][j]) / eps) for j in range(4)] for i in range(5)]
+
+    def kl(mu, nu):
+        return sum(m * math.log(m / n) for m, n in zip(mu, nu) if m > 0) - sum(mu) + sum(nu)
+
+    flat = [pi[i][j] for i in range(5) for j in range(4)]
+    ab = [A[i] * B[j] for i in range(5) for j in range(4)]
+    row = [sum(pi[i]) for i in range(5)]
+    col = [sum(pi[i][j] for i in range(5)) for j in range(4)]
+    pref = (sum(pi[i][j] * Cl[i][j] for i in range(5) for j in range(4)) + eps * kl(flat, ab)
+            + r1 * kl(row, A) + r2 * kl(col, B))
+    got = O.primal_from_softmins(a, b, f, g, S, Sp, eps, r1, r2).item()
+    assert abs(got - pref) < 1e-12 * max(1.0, abs(pref))
+
+
+def test_dual_and_primal_from_softmins_zero_gap_at_newton_optimum():
+    """At the maximiser of F_eps found by the independent damped-Newton solver both O(N + M) forms
+    give the same value (zero duality gap, T4)."""
+    p, C, a, b = tiny(6, 5, 2, 7, 0.2, 0.6, 1.4)
+    fN, gN = newton_dual(C, a, b, p.eps, p.rho1, p.rho2)
+    S = O.smin_rows(C, b, gN, p.eps)
+    Sp = O.smin_cols(C, a, fN, p.eps)
+    D = O.dual_from_softmin(a, b, fN, gN, S, p.eps, p.rho1, p.rho2).item()
+    P = O.primal_from_softmins(a, b, fN, gN, S, Sp, p.eps, p.rho1, p.rho2).item()
+    assert abs(D - P) < 1e-11 * max(1.0, abs(D))
+
+
 # ------------------------------------------------------------ N = M = 1 (T1)
 
 def n1_closed_form(a, b, c, eps, rho1, rho2):
