@@ -218,9 +218,10 @@ __device__ __forceinline__ void mass_add(RowAcc& a, const ffl::ff& y, const ffl:
   a.sum = ffl::add(a.sum, ffl::exp2(ffl::add(y, (float)(-a.ref)), tab));
 }
 
-// Half-step of one query row from its merged log-sum-exp M + L (log2 units).
-__device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int i, float M, float L, const Pre& p,
-                                       RowAcc& a) {
+// Half-step of one query row from its merged log-sum-exp M + L (log2 units);
+// returns the value stored in the output vector.
+__device__ __forceinline__ float row_ff(const EpiParams& e, const Consts& c, int i, float M, float L, const Pre& p,
+                                        RowAcc& a) {
   using namespace ffl;
   const ff lse = two_sum(M, L);
   if (!(lse.hi > 0.25f * kZeroW)) a.bad = 1;  // every key had zero weight (or NaN)
@@ -247,10 +248,11 @@ __device__ __forceinline__ void row_ff(const EpiParams& e, const Consts& c, int 
     const ff y = add(ff{p.lwh, p.lwl}, neg(mul(v, c.RL)));
     if (!(fabsf(y.hi) < 1e9f)) {
       a.bad = 1;
-      return;
+      return vo;
     }
     mass_add(a, y, *c.tab);
   }
+  return vo;
 }
 
 // The old per-row interface (merge + half-step), used by the combine kernel.

@@ -95,8 +95,10 @@ PartSizes part_sizes(const uot_problem& p) {
     if (tiled_path(p)) {
       upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
       upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
-      upd(ps.rows, (size_t)tc_geom(p.n, p.m, p.dim).splits * 2 * p.n);
-      upd(ps.cols, (size_t)tc_geom(p.m, p.n, p.dim).splits * 2 * p.m);
+      if (tc3_fits(p.n, p.m)) {
+        upd(ps.rows, (size_t)tc3_geom(p.n, p.m).splits * 2 * p.n);
+        upd(ps.cols, (size_t)tc3_geom(p.m, p.n).splits * 2 * p.m);
+      }
     }
     if (mma_path(p)) {
       upd(ps.rows, (size_t)umma_geom(p.n, p.m).splits * 2 * p.n);
@@ -118,6 +120,7 @@ struct WsLayout {
   size_t op_x, op_y, n2_x, n2_y, op_sc;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
+  size_t tc_bx, tc_by, tc_hbx, tc_hby;  // key operands of the tensor-core tiled sweeps
   size_t sort_tmp_bytes, total;
 };
 
@@ -167,6 +170,12 @@ WsLayout ws_layout(const uot_problem& p) {
     L.idx_in = take(sizeof(int) * nmax);
     L.sort_tmp_bytes = sort_temp_bytes(nmax);
     L.sort_tmp = take(L.sort_tmp_bytes);
+    if (tc3_fits(p.n, p.m)) {
+      L.tc_bx = take(sizeof(float) * tc3_operand_floats(p.n));
+      L.tc_by = take(sizeof(float) * tc3_operand_floats(p.m));
+      L.tc_hbx = take(sizeof(float) * ((p.n + kTileKeys - 1) / kTileKeys));
+      L.tc_hby = take(sizeof(float) * ((p.m + kTileKeys - 1) / kTileKeys));
+    }
   }
   L.total = off;
   return L;
@@ -185,7 +194,8 @@ struct Ctx {
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
   bool tiled;
-  bool tc;  // the solver's tiled sweeps run on the tensor cores (ordering == 3)
+  bool tc3;  // the solver's tiled half-steps run on the tensor cores (ordering != 3)
+  float *tc_bx, *tc_by, *tc_hbx, *tc_hby;  // their key operands and tile maxima
   const float *px, *py, *pa, *pb;
   int *perm_x, *perm_y;
   float4 *cen_x, *cen_y;
@@ -240,7 +250,8 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
-  c->tc = c->tiled && prob->ordering == 3;
+  c->tc3 = c->tiled && prob->ordering != 3 && tc3_fits(prob->n, prob->m);
+  c->tc_bx = c->tc_by = c->tc_hbx = c->tc_hby = nullptr;
   c->px = prob->x; c->py = prob->y; c->pa = prob->a; c->pb = prob->b;
   c->perm_x = c->perm_y = nullptr;
   c->cen_x = c->cen_y = nullptr;
@@ -265,6 +276,12 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
     c->osc.temp = b + L.sort_tmp;
     c->osc.temp_bytes = L.sort_tmp_bytes;
     c->px = c->xs; c->py = c->ys; c->pa = c->as; c->pb = c->bs;
+    if (c->tc3) {
+      c->tc_bx = reinterpret_cast<float*>(b + L.tc_bx);
+      c->tc_by = reinterpret_cast<float*>(b + L.tc_by);
+      c->tc_hbx = reinterpret_cast<float*>(b + L.tc_hbx);
+      c->tc_hby = reinterpret_cast<float*>(b + L.tc_hby);
+    }
   }
   return UOT_OK;
 }
@@ -340,13 +357,14 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
     SideDesc X{c.px, c.l2_a, c.ln_a, p.n}, Y{c.py, c.l2_b, c.ln_b, p.m};
     const SideDesc& q = axis == 0 ? X : Y;
     const SideDesc& k = axis == 0 ? Y : X;
-    if (c.tiled && !moments && epi && epi->allow_tc && epi->lse_buf && c.tc && tc_sweep_fits(q.n)) {
-      SweepGeom g = tc_geom(q.n, k.n, p.dim);
+    if (c.tiled && !moments && epi && c.tc3) {
+      SweepGeom g = tc3_geom(q.n, k.n);
       *splits = g.splits;
       epi->nq = q.n; epi->splits = g.splits; epi->part = part; epi->rb_counter = c.rbc; epi->moments = 0;
       epi->key_shift = shift;
       *fused = true;
-      UOT_CUDA(launch_tc_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, c.s, part, g, *epi, c.st));
+      UOT_CUDA(launch_tc3_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, axis == 0 ? c.tc_by : c.tc_bx,
+                                axis == 0 ? c.tc_hby : c.tc_hbx, c.s, part, g, *epi, c.st));
     } else if (c.tiled && !moments) {
       SweepGeom g = tile_geom(q.n, k.n, p.dim);
       *splits = g.splits;
@@ -433,6 +451,12 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
   else if (c.tiled) UOT_CUDA(launch_gather_vec(f, c.perm_x, p.n, fst, c.st));
   UOT_CUDA(cudaMemsetAsync(gbuf[0], 0, sizeof(float) * p.m, c.st));
   if (ti) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
+  if (c.tc3) {
+    // key operands of the tensor-core half-steps: coordinates for the whole solve, H of the
+    // initial f (the g side's H comes from the first g half-step's epilogue)
+    UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, fst, c.s, c.tc_bx, c.tc_hbx, true, c.st));
+    UOT_CUDA(launch_tc3_keys(c.ys, p.m, p.dim, c.cen_y, c.l2_b, nullptr, c.s, c.tc_by, c.tc_hby, true, c.st));
+  }
   const int mode = variant == 1 ? EPI_TI : variant == 2 ? EPI_G : EPI_PLAIN;
   int t = 0, status = 0;
   float r = NAN;
@@ -470,7 +494,8 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
     e.old_out = (t >= 1) ? gbuf[si] : nullptr; e.out = gbuf[so];
     e.resid_hist = opt->residual_history; e.hist_index = t;
     e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
-    e.lse_buf = lse_g; e.lse_policy = opt->lse_reference; e.allow_tc = t >= 1;
+    e.lse_buf = lse_g; e.lse_policy = opt->lse_reference;
+    if (c.tc3) { e.tc_b_out = c.tc_by; e.tc_hb_out = c.tc_hby; e.tc_cen_out = c.cen_y; e.tc_pts_out = c.ys; }
     v = sweep(c, 1, fst, ti ? &c.state->slot[si].cf : nullptr, false, &splits, &e, &fused);
     if (v != UOT_OK) return v;
     e.splits = splits;
@@ -488,6 +513,7 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
     ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = fst; ef.resid_hist = nullptr;
     ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
     ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r; ef.lse_buf = lse_f;
+    if (c.tc3) { ef.tc_b_out = c.tc_bx; ef.tc_hb_out = c.tc_hbx; ef.tc_cen_out = c.cen_x; ef.tc_pts_out = c.xs; }
     v = sweep(c, 0, gbuf[so], ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
     if (v != UOT_OK) return v;
     ef.splits = splits;
@@ -504,6 +530,8 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
                                              variant == 2 ? sl : nullptr, &c.state->status, c.st));
         // H: the new fb is held in full (cf = 0); its Smin_a^rho1 for the next g half-step
         if (variant == 1) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st, t & 1));
+        // the extrapolated iterate replaces f: the x side's key constants follow it
+        if (c.tc3) UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, fst, c.s, c.tc_bx, c.tc_hbx, false, c.st));
       }
     }
   }

@@ -147,16 +147,20 @@ SweepGeom tile_geom(int nq, int nk, int dim);
 cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
                               const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
                               const struct EpiParams* epi, cudaStream_t st);
-// Tensor-core tiled sweep (sorted clouds, dim <= 3, p = 2) with the fused
-// half-step epilogue; centers_k = 128-point tile centres of the key side.
-// Needs ceil(nq / 128) <= kMaxBlocks.
-bool tc_sweep_fits(int nq);
-SweepGeom tc_geom(int nq, int nk, int dim);
-// Requires epi.lse_buf holding every row's previous log-sum-exp (the solver's
-// second and later sweeps of a side).
-cudaError_t launch_tc_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
-                            const float* pot_k, double s, float* part, const SweepGeom& g,
-                            const struct EpiParams& epi, cudaStream_t st);
+// Tensor-core tiled half-step sweep (sorted clouds, dim <= 3, p = 2) with the
+// fused epilogue (sweep_tc3.cu).  Each side has a key operand of
+// tc3_operand_floats(n) floats (16-byte aligned) and one float per 128-point
+// tile (Hbar): launch_tc3_keys builds it (full: coordinate parts too) from a
+// potential (nullable: 0); afterwards the epilogue of every half-step that
+// writes that side's potential keeps its H parts current (epi.tc_* fields).
+bool tc3_fits(int nq, int nk);
+size_t tc3_operand_floats(int n);
+SweepGeom tc3_geom(int nq, int nk);
+cudaError_t launch_tc3_keys(const float* pts, int n, int dim, const float4* cen, const float* l2w, const float* pot,
+                            double s, float* Bop, float* hb, bool full, cudaStream_t st);
+cudaError_t launch_tc3_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
+                             const float* pot_k, const float* Bk, const float* hbk, double s, float* part,
+                             const SweepGeom& g, const struct EpiParams& epi, cudaStream_t st);
 // Tensor-core sweep with moments (dim >= 32, p = 2): partials [splits][2 + dim][nq]
 // (max, sum of mult_j 2^(t - max), momscale * the moments of (x_i - y_j)).
 // Forward gradient sweep: l2w, pot, shift of the keys, zrow = hk = mk = null,
@@ -232,7 +236,13 @@ struct EpiParams {
   int lse_policy;       // 0: reference after a small change, 2: whenever one is stored
   const float* l2w_o;   // TI: log2 weights of the output side as float pairs (hi, lo)
   const float* l2lo_o;
-  int allow_tc;         // host hint: lse_buf holds this side's previous row values (tensor-core sweep allowed)
+  // tensor-core tiled sweeps (nullable): the output side's key operand, whose
+  // H parts the epilogue rewrites from the new potential, with its tiles'
+  // Hbar, tile centres and points (Morton order)
+  float* tc_b_out;
+  float* tc_hb_out;
+  const float4* tc_cen_out;
+  const float* tc_pts_out;
 };
 // Fills the constants of an EpiParams that depend only on s, eps and the rhos
 // (call after setting s, eps, rho_o, rho_i).

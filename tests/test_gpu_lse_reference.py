@@ -28,8 +28,8 @@ def spec_of(U, p, ordering=1):
     return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), p=p.p, ordering=ordering)
 
 
-# Morton tiles on CUDA cores (1) and with the solver's half-steps on the tensor cores (3)
-TILED = pytest.mark.parametrize("ordering", [1, 3], ids=["cc", "tc"])
+# Morton tiles with the solver's half-steps on the tensor cores (1) and on CUDA cores only (3)
+TILED = pytest.mark.parametrize("ordering", [1, 3], ids=["tc", "cc"])
 
 
 def assert_pot_close(got, ref, eps, what=""):
