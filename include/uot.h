@@ -226,6 +226,45 @@ UOT_API uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* o
 UOT_API uot_status uot_g_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
                           uot_result* result, void* ws, size_t ws_bytes, void* stream);
 
+/* Plans: a solve with no host synchronisation, capturable in a CUDA graph.
+ *
+ * uot_plan_create fixes a problem (its sizes, parameters and device pointers),
+ * its options and the variant (0: plain F-Sinkhorn as uot_sinkhorn, 1:
+ * H-Sinkhorn as uot_ti_sinkhorn, 2: G-Sinkhorn as uot_g_sinkhorn; Sec. 3).
+ * uot_plan_solve then enqueues the whole solve on `stream` and returns at
+ * once: the iterations run as a CUDA graph whose loop is a conditional while
+ * node, the stopping rule of uot_sinkhorn (residual tested every check_every
+ * iterations and at max_iter) evaluated on the device after each g half-step,
+ * so the host never waits.  The same iterates, residual and result as the
+ * host-driven entry points (equal within rounding of the same kernels).
+ *  - res_dev: DEVICE memory for one uot_result, written at the end of the
+ *    solve (read it after synchronising the stream); its status field holds
+ *    the solve's uot_status (UOT_OK, UOT_NOT_CONVERGED, UOT_ERR_NONFINITE,
+ *    UOT_ERR_TIMEOUT).  The call's own return value reports argument and CUDA
+ *    errors only.
+ *  - If `stream` is being captured (cudaStreamBeginCapture), the solve is
+ *    added to the caller's graph (with its conditional nodes) and replays with
+ *    it.  Otherwise the library captures the solve once per set of (f, g,
+ *    res_dev, ws) pointers into an executable graph kept in the plan (the last
+ *    four) and launches it.  Buffers are read when the solve runs, so their
+ *    contents may change between solves; the problem's device pointers must
+ *    stay valid while the plan is used.
+ *  - Workspace: uot_plan_workspace_size(plan) bytes, as for uot_workspace_size.
+ *  - Anderson extrapolation (options.anderson_k) is host-driven and rejected
+ *    here with UOT_ERR_UNSUPPORTED; options.residual_history works (entry t is
+ *    written by the solve on the device).
+ *  - A plan belongs to the device that was current at creation; calls on one
+ *    plan are serialised (a mutex) and solves sharing a workspace must not
+ *    overlap on the GPU.  uot_plan_create allocates host memory and three CUDA
+ *    streams, no device memory; uot_plan_destroy releases them. */
+typedef struct uot_plan uot_plan;
+UOT_API uot_status uot_plan_create(const uot_problem* prob, const uot_options* opt, int32_t variant,
+                                   uot_plan** out);
+UOT_API void uot_plan_destroy(uot_plan* plan);
+UOT_API size_t uot_plan_workspace_size(const uot_plan* plan);
+UOT_API uot_status uot_plan_solve(uot_plan* plan, float* f, float* g, uot_result* res_dev, void* ws,
+                                  size_t ws_bytes, void* stream);
+
 /* Dual objective F_eps(f, g) (Sec. 1, Eq. eq-dual-uot-kl), FP64, written to
  * out[0] (device).  If out has room for 3 doubles (want_primal != 0) it also
  * writes out[1] = primal objective (Eq. eq-primal-uot-kl) of the plan

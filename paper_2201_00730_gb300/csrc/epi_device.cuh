@@ -371,7 +371,7 @@ __device__ inline void finalize(const EpiParams& e, const Part& t, const ffl::Ex
     }
     if (e.old_out) {
       st->resid = t.r;
-      if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+      if (e.resid_hist) e.resid_hist[e.loop_ctl ? st->loop_t : e.hist_index] = t.r;
     }
     st->status = status;
     if (!e.ff_only) {
@@ -401,7 +401,7 @@ __device__ inline void finalize(const EpiParams& e, const Part& t, const ffl::Ex
     }
     if (e.old_out) {
       st->resid = t.r;
-      if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+      if (e.resid_hist) e.resid_hist[e.loop_ctl ? st->loop_t : e.hist_index] = t.r;
     }
     st->status = status;
     if (!e.ff_only) {
@@ -411,7 +411,7 @@ __device__ inline void finalize(const EpiParams& e, const Part& t, const ffl::Ex
   } else {
     if (e.old_out) {
       st->resid = t.r;
-      if (e.resid_hist) e.resid_hist[e.hist_index] = t.r;
+      if (e.resid_hist) e.resid_hist[e.loop_ctl ? st->loop_t : e.hist_index] = t.r;
     }
     st->status = status;
   }
@@ -420,6 +420,20 @@ __device__ inline void finalize(const EpiParams& e, const Part& t, const ffl::Ex
     const int side = e.out_is_f;
     st->lse_ok[side] = (e.lse_policy == 2) || (e.lse_policy == 0 && t.gap <= (float)kLseGate);
     st->lse_ready[side] = 1;
+  }
+  if (e.loop_ctl == 1) {
+    st->loop_t += 1;
+  } else if (e.loop_ctl == 2) {
+    // the host driver's stopping rule at iterate loop_t, whose residual this g half-step measured:
+    // tested at every check_every-th iterate and at max_iter; a non-finite state also stops
+    const int it = st->loop_t;
+    const bool last = it >= e.loop_max_iter;
+    bool stop = false;
+    if (it >= 1 && (last || (e.loop_tol > 0.0 && it % e.loop_check_every == 0)))
+      stop = st->status != 0 || isnan(t.r) || last || (double)t.r <= e.loop_tol;
+    st->loop_done = stop ? 1 : 0;
+    if (e.cond_while) cudaGraphSetConditional(e.cond_while, stop ? 0u : 1u);
+    if (e.cond_if) cudaGraphSetConditional(e.cond_if, stop ? 0u : 1u);
   }
 }
 

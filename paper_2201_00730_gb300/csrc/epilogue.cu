@@ -379,3 +379,69 @@ cudaError_t launch_mass(const float* w, int n, double* blk, DevState* s, int idx
 }
 
 }  // namespace uot
+
+namespace uot {
+namespace {
+
+// Phi of the iterate that a device-driven loop stopped at (index state->loop_t,
+// or state->iters after the resident solver; its scalars in the slot and its g
+// in g0 or g1 of that index's parity).
+__global__ void k_finalize_loop(int ti, const float* f_hat, const float* g0, const float* g1, float* f, float* g,
+                                int n, int m, const DevState* st, const int* pf, const int* pg, int small) {
+  const int slot = (small ? st->iters : st->loop_t) & 1;
+  const float* g_hat = slot ? g1 : g0;
+  const Slot& s = st->slot[slot];
+  const double sf = ti == 1 ? s.cf + s.lam : ti == 2 ? s.lam : 0.0;
+  const double sg = ti == 1 ? s.cg - s.lam : ti == 2 ? -s.lam : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (ti) f[pf ? pf[i] : i] = (float)((double)f_hat[i] + sf);
+      else if (pf || f_hat != f) f[pf ? pf[i] : i] = f_hat[i];
+    } else {
+      const int j = i - n;
+      if (ti) g[pg ? pg[j] : j] = (float)((double)g_hat[j] + sg);
+      else if (pg || g_hat != g) g[pg ? pg[j] : j] = g_hat[j];
+    }
+  }
+}
+
+// The outcome of a solve from the device state, the way the host driver
+// reports it; small = 1 when the resident solver ran the loop (iteration
+// count in st->iters, scalars in slot iters & 1).
+__global__ void k_write_result(const DevState* st, int ti, int small, double tol, uot_result* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int it = small ? st->iters : st->loop_t;
+  const float r = st->resid;
+  const int flags = st->status;
+  const bool conv = !isnan(r) && (double)r <= tol;
+  int code = UOT_OK;
+  if (flags & kStatusTimeout) code = UOT_ERR_TIMEOUT;
+  else if (flags & kStatusBadWeights) code = UOT_ERR_NONFINITE;
+  else if (flags != 0 || isnan(r)) code = UOT_ERR_NONFINITE;
+  else if (tol > 0.0 && !conv) code = UOT_NOT_CONVERGED;
+  out->iters = it;
+  out->converged = conv ? 1 : 0;
+  out->status = code;
+  const unsigned int miss = st->lse_miss;
+  out->lse_misses = (int32_t)(miss > 0x7fffffffu ? 0x7fffffffu : miss);
+  out->residual = (double)r;
+  out->lambda = ti ? st->slot[it & 1].lam : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_finalize_loop(int ti, const float* f_hat, const float* g0, const float* g1, float* f, float* g,
+                                 int n, int m, const DevState* s, const int* perm_f, const int* perm_g, int small,
+                                 cudaStream_t st) {
+  k_finalize_loop<<<grid_for(n + m), kBlk, 0, st>>>(ti, f_hat, g0, g1, f, g, n, m, s, perm_f, perm_g, small);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_result(const DevState* s, int ti, int small, double tol, uot_result* out, cudaStream_t st) {
+  k_write_result<<<1, 32, 0, st>>>(s, ti, small, tol, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace uot

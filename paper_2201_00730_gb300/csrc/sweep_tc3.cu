@@ -66,8 +66,11 @@ constexpr int kRows = 128;              // rows of a block = TMEM lanes = MMA M
 constexpr int kKeys = 128;              // keys of a tile = MMA N = kTileKeys
 constexpr int kK = 16;                  // tf32 values per operand row (two MMAs of K = 8)
 constexpr int kSbo = (kK / 4) * 128;    // bytes between 8-row core-matrix groups
-constexpr int kTileBytes = kKeys * kK * 4;
-constexpr int kStages = 4;              // operand stages = TMEM accumulators
+constexpr int kOpBytes = kKeys * kK * 4;       // operand part of a key tile
+constexpr int kTileBytes = kOpBytes + 128;     // + header {o_T.x, o_T.y, o_T.z, Hbar_T}, padding
+constexpr int kTileFloats = kTileBytes / 4;
+constexpr int kStages = 4;              // row-operand stages = TMEM accumulators
+constexpr int kBStages = 8;             // key-tile stages (copies run kBStages - kStages tiles ahead)
 constexpr int kCols = kStages * kKeys;  // all 512 TMEM columns
 constexpr int kConsWarps = 8;
 constexpr int kBuildWarps = 4;
@@ -80,16 +83,16 @@ constexpr int kQueue = 8;               // row blocks handed to the epilogue war
 constexpr int kBarCons = 1, kBarEpi = 2;
 constexpr uint32_t kIdesc = tc::idesc_tf32(kRows, kKeys);
 constexpr long long kSpin = 1LL << 24;  // mbarrier polls before giving up
-constexpr size_t kSmemBytes = 120 * 1024;  // more than half the SM: one CTA per SM
+constexpr size_t kSmemBytes = 136 * 1024;  // more than half the SM: one CTA per SM
 static_assert(kTileKeys == kKeys, "the key tiles of the ordering step are the MMA tiles");
 
 struct Smem {
   float A[kStages][kRows * kK];
-  float B[kStages][kKeys * kK];
+  float B[kBStages][kTileFloats];
   float2 half[kRows];             // column half 1 of each row -> half 0
   float2 halfc[kRows];            // its compensation (reference mode) / unused
   uint64_t a_full[kStages];       // the builders wrote A of the stage
-  uint64_t b_full[kStages];       // B of the stage landed
+  uint64_t b_full[kBStages];      // the key tile of the stage landed
   uint64_t m_done[kStages];       // the MMAs of the stage completed
   uint64_t acc_empty[kStages];    // the consumers read the accumulator
   uint64_t q_full[kQueue];        // a row block was handed to the epilogue warps
@@ -168,24 +171,26 @@ __device__ __forceinline__ float group_max(float v, const epi::Grp& g, float* sh
 // The H part of the operand rows of key tile T (one thread per key p of the
 // tile, the whole group): Hbar_T = the largest live H (0 if none), the row
 // gets H - Hbar_T in three tf32 parts (dead and padding keys: kZeroW, so that
-// their entries vanish), hb[T] = Hbar_T.
-__device__ __forceinline__ void write_key_h(float* __restrict__ Bop, float* __restrict__ hb, int T, int p, bool live,
-                                            float H, const epi::Grp& g, float* sh) {
+// their entries vanish), and Hbar_T goes into the tile's header.
+__device__ __forceinline__ void write_key_h(float* __restrict__ Bop, int T, int p, bool live, float H,
+                                            const epi::Grp& g, float* sh) {
   float hm = group_max(live ? H : -INFINITY, g, sh);
   if (!(hm > -INFINITY)) hm = 0.f;
   float h0 = kZeroW, h1 = 0.f, h2 = 0.f;
   if (live) split3(H - hm, h0, h1, h2);
-  put4(Bop + (size_t)T * (kKeys * kK), p, 12, h0, h1, h2, 0.f);
-  if (g.tid == 0) hb[T] = hm;
+  float* tile = Bop + (size_t)T * kTileFloats;
+  put4(tile, p, 12, h0, h1, h2, 0.f);
+  if (g.tid == 0) tile[kOpBytes / 4 + 3] = hm;
 }
 
 // Key operand of one side, one CTA (128 threads) per tile: with `full` the
 // coordinate parts [Yh0 Yh0 Yl0 Yh1 | Yh1 Yl1 Yh2 Yh2 | Yl2 1 1 1 | . . . .]
-// of Y_j = 2 s (k_j - o_T), always the H part from pot (null: 0).
+// of Y_j = 2 s (k_j - o_T) and the header's o_T, always the H part from pot
+// (null: 0) and the header's Hbar_T.
 template <int D>
 __global__ void __launch_bounds__(kKeys)
 k_tc3_keys(const float* __restrict__ pts, int n, const float4* __restrict__ cen, const float* __restrict__ l2w,
-           const float* __restrict__ pot, double s, float* __restrict__ Bop, float* __restrict__ hb, int full) {
+           const float* __restrict__ pot, double s, float* __restrict__ Bop, int full) {
   __shared__ float sh[kKeys / 32];
   const int T = blockIdx.x, p = threadIdx.x, j = T * kKeys + p;
   const float sf = (float)s, s2 = (float)(2.0 * s);
@@ -202,8 +207,9 @@ k_tc3_keys(const float* __restrict__ pts, int n, const float4* __restrict__ cen,
       r2 = fmaf(yl, yl, r2);
     }
   }
-  float* tile = Bop + (size_t)T * (kKeys * kK);
+  float* tile = Bop + (size_t)T * kTileFloats;
   if (full) {
+    if (p < 3) tile[kOpBytes / 4 + p] = oc[p];
     float yh[3], yl[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -218,7 +224,7 @@ k_tc3_keys(const float* __restrict__ pts, int n, const float4* __restrict__ cen,
   const bool live = in && lw > 0.5f * kZeroW;
   // H_j = log2 w_j + s pot_j - s |k'_j|^2 in FP32, as the CUDA-core tiled sweep forms it
   const float H = live ? fmaf(-sf, r2, fmaf(sf, pot ? pot[j] : 0.f, lw)) : kZeroW;
-  write_key_h(Bop, hb, T, p, live, H, epi::whole_block(), sh);
+  write_key_h(Bop, T, p, live, H, epi::whole_block(), sh);
 }
 
 // Parameters of one launch (the query side's rows, the key side's operand).
@@ -228,8 +234,7 @@ struct Tc3Args {
   const float4* kcen;   // key tile centres
   const float* kl2w;    // key log2 weights (exact recompute)
   const float* kpot;    // key potential (exact recompute)
-  const float* Bk;      // key operand, [TT tiles][128 x 16] tf32, canonical K-major
-  const float* hbk;     // Hbar of each key tile
+  const float* Bk;      // key tiles: [TT][128 x 16 tf32, canonical K-major | header]
   float* part;          // partials [slots][2][nq]
   int nq, nk, TT;
   double s;
@@ -258,10 +263,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
   if (tid == 32 * kIssueWarp) {
     for (int b = 0; b < kStages; ++b) {
       tc::mbar_init(&sm.a_full[b], kBuildWarps);
-      tc::mbar_init(&sm.b_full[b], 1);
       tc::mbar_init(&sm.m_done[b], 1);
       tc::mbar_init(&sm.acc_empty[b], kConsWarps);
     }
+    for (int b = 0; b < kBStages; ++b) tc::mbar_init(&sm.b_full[b], 1);
     for (int k = 0; k < kQueue; ++k) {
       tc::mbar_init(&sm.q_full[k], 1);
       tc::mbar_init(&sm.q_empty[k], 1);
@@ -277,50 +282,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
 
   if (warp == kIssueWarp) {
     // ------------------------------------------------------------------ copies and MMAs
+    // Key tile of unit t in stage t % kBStages; the copy for unit t + kBStages goes into
+    // that stage once every role is done with unit t (its accumulator was read, which
+    // the MMAs of unit t + kStages wait for anyway).
     if (lane == 0) {
-      int armed[kStages] = {}, used[kStages] = {};
+      int armed[kBStages] = {}, used[kBStages] = {};
       int committed = -1, reused = -1;  // units committed; MMAs of units <= reused seen complete
       auto copy_b = [&](int t) {
-        const int st = t % kStages;
+        const int sb = t % kBStages;
         const int T = (int)((u0 + t) % TT);
-        tc::mbar_arrive_expect_tx(&sm.b_full[st], (uint32_t)kTileBytes);
-        tc::bulk_g2s(sm.B[st], a.Bk + (size_t)T * (kKeys * kK), (uint32_t)kTileBytes, &sm.b_full[st]);
-        ++armed[st];
+        tc::mbar_arrive_expect_tx(&sm.b_full[sb], (uint32_t)kTileBytes);
+        tc::bulk_g2s(sm.B[sb], a.Bk + (size_t)T * kTileFloats, (uint32_t)kTileBytes, &sm.b_full[sb]);
+        ++armed[sb];
       };
-      for (int t = 0; t < L && t < kStages; ++t) copy_b(t);
+      for (int t = 0; t < L && t < kBStages; ++t) copy_b(t);
       for (int t = 0; t < L && !*err; ++t) {
-        const int st = t % kStages;
-        const uint32_t ph = (uint32_t)((t / kStages) & 1);
-        bool ok = tc::mbar_wait(&sm.a_full[st], ph, kSpin);
-        ok = ok && tc::mbar_wait(&sm.b_full[st], ph, kSpin);
-        if (ok) ++used[st];
-        // accumulator st was last read for unit t - kStages
-        ok = ok && (t < kStages ||
-                    tc::mbar_wait(&sm.acc_empty[st], (uint32_t)(((t - kStages) / kStages) & 1), kSpin));
+        const int st = t % kStages, sb = t % kBStages;
+        bool ok = tc::mbar_wait(&sm.a_full[st], (uint32_t)((t / kStages) & 1), kSpin);
+        ok = ok && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), kSpin);
+        if (ok) ++used[sb];
+        if (ok && t >= kStages) {
+          // accumulator st was last read for unit t - kStages: its key stage can take unit t - kStages + kBStages
+          ok = tc::mbar_wait(&sm.acc_empty[st], (uint32_t)(((t - kStages) / kStages) & 1), kSpin);
+          if (ok) {
+            reused = t - kStages;
+            if (t - kStages + kBStages < L) copy_b(t - kStages + kBStages);
+          }
+        }
         if (!ok) { *err = 1; break; }
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(st * kKeys);
         const uint64_t da = tc::smem_desc(tc::smem_addr(sm.A[st]), 128, kSbo);
-        const uint64_t db = tc::smem_desc(tc::smem_addr(sm.B[st]), 128, kSbo);
+        const uint64_t db = tc::smem_desc(tc::smem_addr(sm.B[sb]), 128, kSbo);
         tc::mma_tf32(d, da, db, kIdesc, false);
         tc::mma_tf32(d, da + (256 >> 4), db + (256 >> 4), kIdesc, true);  // K values 8..15
         tc::commit(&sm.m_done[st]);
         committed = t;
-        // the key stage of unit t - 1 takes unit t - 1 + kStages once the MMAs of unit t - 1 completed
-        if (t >= 1 && t - 1 + kStages < L) {
-          if (!tc::mbar_wait(&sm.m_done[(t - 1) % kStages], (uint32_t)(((t - 1) / kStages) & 1), kSpin)) {
-            *err = 1;
-            break;
-          }
-          reused = t - 1;
-          copy_b(t - 1 + kStages);
-        }
       }
       if (*err) {
         // let every copy armed and every MMA committed land before the CTA ends (bounded)
-        for (int st = 0; st < kStages; ++st)
-          for (; used[st] < armed[st]; ++used[st])
-            (void)tc::mbar_wait(&sm.b_full[st], (uint32_t)(used[st] & 1), kSpin);
+        for (int sb = 0; sb < kBStages; ++sb)
+          for (; used[sb] < armed[sb]; ++used[sb])
+            (void)tc::mbar_wait(&sm.b_full[sb], (uint32_t)(used[sb] & 1), kSpin);
         for (int t = reused + 1; t <= committed; ++t) {
           if (t + kStages <= committed) continue;  // only the latest commit of each stage
           (void)tc::mbar_wait(&sm.m_done[t % kStages], (uint32_t)((t / kStages) & 1), kSpin);
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
     float xq[3] = {0.f, 0.f, 0.f}, mref = 0.f;
     for (int t = 0; t < L; ++t) {
       const long long u = u0 + t;
-      const int rbt = (int)(u / TT), T = (int)(u % TT);
+      const int rbt = (int)(u / TT);
       if (rbt != rb) {
         rb = rbt;
         const int i = rb * kRows + p;
@@ -345,22 +348,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
         for (int d = 0; d < 3; ++d) xq[d] = (live && d < D) ? a.q[(size_t)i * D + d] : 0.f;
         mref = (live && use_ref) ? e.lse_buf[i] : 0.f;
       }
-      const float4 o = a.kcen[T];
-      const float hbar = a.hbk[T];
-      const int st = t % kStages;
-      bool ok = !*err;
-      if (ok && t >= kStages) ok = tc::mbar_wait(&sm.m_done[st], (uint32_t)(((t - kStages) / kStages) & 1), kSpin);
+      const int st = t % kStages, sb = t % kBStages;
+      // the tile's header arrives with its copy; the row stage is free once its accumulator was read
+      bool ok = !*err && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), kSpin);
+      if (ok && t >= kStages) ok = tc::mbar_wait(&sm.acc_empty[st], (uint32_t)(((t - kStages) / kStages) & 1), kSpin);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) *err = 1;
         break;
       }
-      const float x0 = xq[0] - o.x, x1 = (D > 1) ? xq[1] - o.y : 0.f, x2 = (D > 2) ? xq[2] - o.z : 0.f;
+      const float4 hd = *reinterpret_cast<const float4*>(sm.B[sb] + kOpBytes / 4);  // {o_T, Hbar_T}
+      const float x0 = xq[0] - hd.x, x1 = (D > 1) ? xq[1] - hd.y : 0.f, x2 = (D > 2) ? xq[2] - hd.z : 0.f;
       float q2 = x0 * x0;
       if (D > 1) q2 = fmaf(x1, x1, q2);
       if (D > 2) q2 = fmaf(x2, x2, q2);
       const float R = -sf * q2;
-      const float c = live ? (use_ref ? R + (hbar - mref) : R) : 0.f;
+      const float c = live ? (use_ref ? R + (hd.w - mref) : R) : 0.f;
       const float h0 = tc::to_tf32(x0), h1 = tc::to_tf32(x1), h2 = tc::to_tf32(x2);
       const float l0 = tc::to_tf32(x0 - h0), l1 = tc::to_tf32(x1 - h1), l2 = tc::to_tf32(x2 - h2);
       float ch, cm, cl;
@@ -395,10 +398,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
     for (int t = 0; t < L; ++t) {
       const long long u = u0 + t;
       const int rb = (int)(u / TT), T = (int)(u % TT);
-      const int st = t % kStages;
-      const float hbar = use_ref ? 0.f : a.hbk[T];
+      const int st = t % kStages, sb = t % kBStages;
+      float hbar = 0.f;
       if (!dead) {
         bool ok = !*err && tc::mbar_wait(&sm.m_done[st], (uint32_t)((t / kStages) & 1), kSpin);
+        // (the tile's copy completed before its MMAs; this wait makes its header visible here)
+        ok = ok && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), kSpin);
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-wide
         if (!ok) {
           if (lane == 0) *err = 1;
@@ -406,6 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
         }
       }
       if (!dead) {
+        hbar = sm.B[sb][kOpBytes / 4 + 3];
         tc::fence_after_sync();
         uint32_t r0[32], r1[32];
         ld32_async(tl + (uint32_t)(st * kKeys), r0);
@@ -567,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
           }
           H = fmaf(-sf, r2, fmaf(sf, vo, lw));
         }
-        write_key_h(e.tc_b_out, e.tc_hb_out, rb, g.tid, live, H, g, sm.hmax);
+        write_key_h(e.tc_b_out, rb, g.tid, live, H, g, sm.hmax);
       }
       epi::block_finish(e, ea, rb, RB, g);
       g.sync();
@@ -598,7 +604,7 @@ bool tc3_fits(int nq, int nk) {
   return nq > 0 && nk > 0 && (nq + kRows - 1) / kRows <= kMaxBlocks && (nk + kKeys - 1) / kKeys <= kMaxBlocks;
 }
 
-size_t tc3_operand_floats(int n) { return (size_t)((n + kKeys - 1) / kKeys) * kKeys * kK; }
+size_t tc3_operand_floats(int n) { return (size_t)((n + kKeys - 1) / kKeys) * kTileFloats; }
 
 // One CTA per SM over the (row block, key tile) units; slots = the most CTAs
 // that one row block's units are spread over.
@@ -623,23 +629,23 @@ SweepGeom tc3_geom(int nq, int nk) {
 }
 
 cudaError_t launch_tc3_keys(const float* pts, int n, int dim, const float4* cen, const float* l2w, const float* pot,
-                            double s, float* Bop, float* hb, bool full, cudaStream_t st) {
+                            double s, float* Bop, bool full, cudaStream_t st) {
   const int tiles = (n + kKeys - 1) / kKeys;
   switch (dim) {
-    case 1: k_tc3_keys<1><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, hb, full ? 1 : 0); break;
-    case 2: k_tc3_keys<2><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, hb, full ? 1 : 0); break;
-    default: k_tc3_keys<3><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, hb, full ? 1 : 0);
+    case 1: k_tc3_keys<1><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, full ? 1 : 0); break;
+    case 2: k_tc3_keys<2><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, full ? 1 : 0); break;
+    default: k_tc3_keys<3><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, full ? 1 : 0);
   }
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc3_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
-                             const float* pot_k, const float* Bk, const float* hbk, double s, float* part,
+                             const float* pot_k, const float* Bk, double s, float* part,
                              const SweepGeom& g, const EpiParams& epi, cudaStream_t st) {
   EpiParams e = epi;
   epi_finish_params(e);
-  Tc3Args a{q.pts, k.pts, centers_k, k.l2w, pot_k, Bk, hbk, part, q.n, k.n, (k.n + kKeys - 1) / kKeys, s};
+  Tc3Args a{q.pts, k.pts, centers_k, k.l2w, pot_k, Bk, part, q.n, k.n, (k.n + kKeys - 1) / kKeys, s};
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -120,7 +121,7 @@ struct WsLayout {
   size_t op_x, op_y, n2_x, n2_y, op_sc;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
-  size_t tc_bx, tc_by, tc_hbx, tc_hby;  // key operands of the tensor-core tiled sweeps
+  size_t tc_bx, tc_by;  // key tiles of the tensor-core tiled sweeps
   size_t sort_tmp_bytes, total;
 };
 
@@ -173,8 +174,6 @@ WsLayout ws_layout(const uot_problem& p) {
     if (tc3_fits(p.n, p.m)) {
       L.tc_bx = take(sizeof(float) * tc3_operand_floats(p.n));
       L.tc_by = take(sizeof(float) * tc3_operand_floats(p.m));
-      L.tc_hbx = take(sizeof(float) * ((p.n + kTileKeys - 1) / kTileKeys));
-      L.tc_hby = take(sizeof(float) * ((p.m + kTileKeys - 1) / kTileKeys));
     }
   }
   L.total = off;
@@ -195,7 +194,7 @@ struct Ctx {
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
   bool tiled;
   bool tc3;  // the solver's tiled half-steps run on the tensor cores (ordering != 3)
-  float *tc_bx, *tc_by, *tc_hbx, *tc_hby;  // their key operands and tile maxima
+  float *tc_bx, *tc_by;  // their key tiles
   const float *px, *py, *pa, *pb;
   int *perm_x, *perm_y;
   float4 *cen_x, *cen_y;
@@ -251,7 +250,7 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
   c->tc3 = c->tiled && prob->ordering != 3 && tc3_fits(prob->n, prob->m);
-  c->tc_bx = c->tc_by = c->tc_hbx = c->tc_hby = nullptr;
+  c->tc_bx = c->tc_by = nullptr;
   c->px = prob->x; c->py = prob->y; c->pa = prob->a; c->pb = prob->b;
   c->perm_x = c->perm_y = nullptr;
   c->cen_x = c->cen_y = nullptr;
@@ -279,8 +278,6 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
     if (c->tc3) {
       c->tc_bx = reinterpret_cast<float*>(b + L.tc_bx);
       c->tc_by = reinterpret_cast<float*>(b + L.tc_by);
-      c->tc_hbx = reinterpret_cast<float*>(b + L.tc_hbx);
-      c->tc_hby = reinterpret_cast<float*>(b + L.tc_hby);
     }
   }
   return UOT_OK;
@@ -364,7 +361,7 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       epi->key_shift = shift;
       *fused = true;
       UOT_CUDA(launch_tc3_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, axis == 0 ? c.tc_by : c.tc_bx,
-                                axis == 0 ? c.tc_hby : c.tc_hbx, c.s, part, g, *epi, c.st));
+                                c.s, part, g, *epi, c.st));
     } else if (c.tiled && !moments) {
       SweepGeom g = tile_geom(q.n, k.n, p.dim);
       *splits = g.splits;
@@ -412,15 +409,31 @@ uot_status read_flags(Ctx& c, int* status, float* resid) {
   return UOT_OK;
 }
 
+// ---- the Sinkhorn loop ---------------------------------------------------------
+// One solve's set-up, shared by the host-driven loop (uot_sinkhorn and
+// friends: the host reads the residual at every check) and the device-driven
+// loop of a plan (the same launches captured in a CUDA graph, the stopping
+// rule evaluated on the device).
+struct Loop {
+  Ctx c;
+  uot_options opt;
+  int variant;  // 0 plain (F-)Sinkhorn, 1 H-Sinkhorn (TI), 2 G-Sinkhorn
+  bool ti;      // slots, key shifts and lambda in use
+  int mode;     // epilogue mode of the half-steps
+  bool small;   // the resident cluster solver runs the whole loop
+  float *f, *g;           // the caller's outputs
+  float* fst;             // f_hat in the sweeps' order
+  float* gbuf[2];         // g_hat by iteration parity
+  float *lse_f, *lse_g;   // per-row log-sum-exps kept between sweeps (tiled path)
+};
+
 // variant: 0 plain (F-)Sinkhorn, 1 H-Sinkhorn (TI), 2 G-Sinkhorn.
-uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, float* f, float* g,
-                 uot_result* res, void* ws, size_t ws_bytes, void* stream) {
-  const bool ti = variant != 0;  // slots, key shifts and lambda in use
+uot_status loop_setup(Loop& L, int variant, const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                      void* ws, size_t ws_bytes, void* stream) {
   uot_status v0 = validate(prob);
   if (v0 != UOT_OK) return v0;
   if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");
-  Ctx c;
-  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &c, 2.0 * opt->max_iter + 1.0);
+  uot_status v = make_ctx(prob, ws, ws_bytes, stream, &L.c, 2.0 * opt->max_iter + 1.0);
   if (v != UOT_OK) return v;
   if (!f || !g) return fail(UOT_ERR_INVALID_ARG, "f and g must be device pointers");
   if (opt->max_iter < 1) return fail(UOT_ERR_INVALID_ARG, "max_iter must be >= 1");
@@ -436,43 +449,137 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
     if (!opt->anderson_buf || (reinterpret_cast<uintptr_t>(opt->anderson_buf) & 15))
       return fail(UOT_ERR_INVALID_ARG, "anderson_buf must be a 16-byte aligned device pointer");
   }
+  L.opt = *opt;
+  L.variant = variant;
+  L.ti = variant != 0;
+  L.mode = variant == 1 ? EPI_TI : variant == 2 ? EPI_G : EPI_PLAIN;
+  Ctx& c = L.c;
   const uot_problem& p = c.p;
+  L.small = p.ordering == 0 && small_path(p) && AK == 0;
+  L.f = f;
+  L.g = g;
   // tiled path: every row's log-sum-exp is kept between the sweeps of a side
   // (the temporaries, which a solve does not otherwise use), for the fixed
-  // reference (lse_reference != 1) and the tensor-core sweeps' exponent shift
-  float* lse_g = c.tiled ? c.g_tmp : nullptr;
-  float* lse_f = c.tiled ? c.f_tmp : nullptr;
-  v = prepare(c);
+  // reference (lse_reference != 1)
+  L.lse_g = c.tiled ? c.g_tmp : nullptr;
+  L.lse_f = c.tiled ? c.f_tmp : nullptr;
+  L.fst = c.tiled ? c.fs : f;
+  L.gbuf[0] = c.tiled ? c.gs : g;
+  L.gbuf[1] = c.g_alt;
+  return UOT_OK;
+}
+
+// Everything before the first half-step: state, ordering, log weights, the
+// initial iterate and its scalars, the tensor-core key operands.
+uot_status loop_prologue(Loop& L) {
+  Ctx& c = L.c;
+  const uot_problem& p = c.p;
+  uot_status v = prepare(c);
   if (v != UOT_OK) return v;
-  // iteration state in the sweeps' order: f_hat and the two g buffers
-  float* fst = c.tiled ? c.fs : f;
-  float* gbuf[2] = {c.tiled ? c.gs : g, c.g_alt};
-  if (!opt->warm_start) UOT_CUDA(cudaMemsetAsync(fst, 0, sizeof(float) * p.n, c.st));
-  else if (c.tiled) UOT_CUDA(launch_gather_vec(f, c.perm_x, p.n, fst, c.st));
-  UOT_CUDA(cudaMemsetAsync(gbuf[0], 0, sizeof(float) * p.m, c.st));
-  if (ti) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
-  if (c.tc3) {
+  if (!L.opt.warm_start) UOT_CUDA(cudaMemsetAsync(L.fst, 0, sizeof(float) * p.n, c.st));
+  else if (c.tiled) UOT_CUDA(launch_gather_vec(L.f, c.perm_x, p.n, L.fst, c.st));
+  UOT_CUDA(cudaMemsetAsync(L.gbuf[0], 0, sizeof(float) * p.m, c.st));
+  if (L.ti) UOT_CUDA(launch_ti_init(L.fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
+  if (c.tc3 && !L.small) {
     // key operands of the tensor-core half-steps: coordinates for the whole solve, H of the
     // initial f (the g side's H comes from the first g half-step's epilogue)
-    UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, fst, c.s, c.tc_bx, c.tc_hbx, true, c.st));
-    UOT_CUDA(launch_tc3_keys(c.ys, p.m, p.dim, c.cen_y, c.l2_b, nullptr, c.s, c.tc_by, c.tc_hby, true, c.st));
+    UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, true, c.st));
+    UOT_CUDA(launch_tc3_keys(c.ys, p.m, p.dim, c.cen_y, c.l2_b, nullptr, c.s, c.tc_by, true, c.st));
   }
-  const int mode = variant == 1 ? EPI_TI : variant == 2 ? EPI_G : EPI_PLAIN;
+  return UOT_OK;
+}
+
+// Device-driven loop control of a half-step (see EpiParams::loop_ctl).
+struct LoopCtl {
+  int ctl = 0;
+  unsigned long long cond_while = 0, cond_if = 0;
+};
+
+// g half-step of iteration t + 1: column sweep over x with fb_t = f_hat + cf.
+uot_status g_half(Loop& L, int t, const LoopCtl& lc) {
+  Ctx& c = L.c;
+  const uot_problem& p = c.p;
+  const int so = (t + 1) & 1, si = t & 1;
+  int splits = 0;
+  bool fused = false;
+  EpiParams e{};
+  e.mode = L.mode; e.nq = p.m; e.moments = 0; e.s = c.s;
+  e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1; e.out_is_f = 0; e.lnw_o = c.ln_b;
+  e.l2w_o = c.l2_b; e.l2lo_o = c.lo_b;
+  e.old_out = (t >= 1) ? L.gbuf[si] : nullptr; e.out = L.gbuf[so];
+  e.resid_hist = L.opt.residual_history; e.hist_index = t;
+  e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
+  e.lse_buf = L.lse_g; e.lse_policy = L.opt.lse_reference;
+  if (c.tc3) { e.tc_b_out = c.tc_by; e.tc_cen_out = c.cen_y; e.tc_pts_out = c.ys; }
+  e.loop_ctl = lc.ctl;
+  e.loop_max_iter = L.opt.max_iter; e.loop_check_every = L.opt.check_every; e.loop_tol = L.opt.tol;
+  e.cond_while = lc.cond_while; e.cond_if = lc.cond_if;
+  uot_status v = sweep(c, 1, L.fst, L.ti ? &c.state->slot[si].cf : nullptr, false, &splits, &e, &fused);
+  if (v != UOT_OK) return v;
+  e.splits = splits;
+  if (!fused) UOT_CUDA(launch_combine(e, c.st));
+  return UOT_OK;
+}
+
+// f half-step of iteration t + 1: row sweep over y with gb_{t+1} = g_hat + cg.
+uot_status f_half(Loop& L, int t, const LoopCtl& lc) {
+  Ctx& c = L.c;
+  const uot_problem& p = c.p;
+  const int so = (t + 1) & 1;
+  int splits = 0;
+  bool fused = false;
+  EpiParams ef{};
+  ef.mode = L.mode; ef.nq = p.n; ef.moments = 0; ef.s = c.s;
+  ef.eps = p.eps; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1; ef.lnw_o = c.ln_a;
+  ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
+  ef.old_out = nullptr; ef.out = L.fst;
+  ef.resid_hist = nullptr; ef.hist_index = t;
+  ef.slot_in = so; ef.slot_out = so; ef.state = c.state; ef.part = c.part_r; ef.blk = c.blk;
+  ef.lse_buf = L.lse_f; ef.lse_policy = L.opt.lse_reference;
+  if (c.tc3) { ef.tc_b_out = c.tc_bx; ef.tc_cen_out = c.cen_x; ef.tc_pts_out = c.xs; }
+  ef.loop_ctl = lc.ctl;
+  uot_status v = sweep(c, 0, L.gbuf[so], L.ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
+  if (v != UOT_OK) return v;
+  ef.splits = splits;
+  if (!fused) UOT_CUDA(launch_combine(ef, c.st));
+  return UOT_OK;
+}
+
+// The resident cluster solver: the whole loop in one launch.
+uot_status small_loop(Loop& L) {
+  Ctx& c = L.c;
+  const uot_problem& p = c.p;
+  EpiParams eg{};
+  eg.mode = L.mode; eg.nq = p.m; eg.moments = 0; eg.s = c.s;
+  eg.eps = p.eps; eg.rho_o = p.rho2; eg.rho_i = p.rho1; eg.out_is_f = 0; eg.lnw_o = c.ln_b;
+  eg.l2w_o = c.l2_b; eg.l2lo_o = c.lo_b;
+  eg.resid_hist = L.opt.residual_history; eg.state = c.state; eg.blk = c.blk; eg.lse_policy = 1;
+  EpiParams ef = eg;
+  ef.nq = p.n; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
+  ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = L.fst; ef.resid_hist = nullptr;
+  ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
+  UOT_CUDA(launch_small_solve(c.px, c.py, c.l2_a, c.l2_b, p.n, p.m, p.dim, L.ti ? 1 : 0, L.opt.max_iter,
+                              L.opt.check_every, L.opt.tol, c.s, L.fst, L.gbuf[0], L.gbuf[1], eg, ef, c.st));
+  return UOT_OK;
+}
+
+// Host-driven solve: the host reads the residual at every check and decides.
+uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, float* f, float* g,
+                 uot_result* res, void* ws, size_t ws_bytes, void* stream) {
+  Loop L;
+  uot_status v = loop_setup(L, variant, prob, opt, f, g, ws, ws_bytes, stream);
+  if (v != UOT_OK) return v;
+  Ctx& c = L.c;
+  const uot_problem& p = c.p;
+  const int AK = opt->anderson_k;
+  v = loop_prologue(L);
+  if (v != UOT_OK) return v;
+  const LoopCtl host{};
   int t = 0, status = 0;
   float r = NAN;
-  if (p.ordering == 0 && small_path(p) && AK == 0) {
-    // the whole loop in one launch of one thread-block cluster (small problems are latency bound)
-    EpiParams eg{};
-    eg.mode = mode; eg.nq = p.m; eg.moments = 0; eg.s = c.s;
-    eg.eps = p.eps; eg.rho_o = p.rho2; eg.rho_i = p.rho1; eg.out_is_f = 0; eg.lnw_o = c.ln_b;
-    eg.l2w_o = c.l2_b; eg.l2lo_o = c.lo_b;
-    eg.resid_hist = opt->residual_history; eg.state = c.state; eg.blk = c.blk; eg.lse_policy = 1;
-    EpiParams ef = eg;
-    ef.nq = p.n; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
-    ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = fst; ef.resid_hist = nullptr;
-    ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
-    UOT_CUDA(launch_small_solve(c.px, c.py, c.l2_a, c.l2_b, p.n, p.m, p.dim, ti ? 1 : 0, opt->max_iter,
-                                opt->check_every, opt->tol, c.s, fst, gbuf[0], gbuf[1], eg, ef, c.st));
+  if (L.small) {
+    v = small_loop(L);
+    if (v != UOT_OK) return v;
     int iters = 0;
     UOT_CUDA(cudaMemcpyAsync(&iters, &c.state->iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     v = read_flags(c, &status, &r);
@@ -481,25 +588,10 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
   } else for (;;) {
     if (AK && t == 0) {
       UOT_CUDA(anderson_reset(opt->anderson_buf, p.n, AK, c.st));
-      UOT_CUDA(launch_anderson_store(fst, p.n, AK, 0, variant, &c.state->slot[0], opt->anderson_buf, c.st));
+      UOT_CUDA(launch_anderson_store(L.fst, p.n, AK, 0, variant, &c.state->slot[0], opt->anderson_buf, c.st));
     }
-    // g half-step of iteration t+1: column sweep over x with fb_t = f_hat + cf
-    const int so = (t + 1) & 1, si = t & 1;
-    int splits = 0;
-    bool fused = false;
-    EpiParams e{};
-    e.mode = mode; e.nq = p.m; e.moments = 0; e.s = c.s;
-    e.eps = p.eps; e.rho_o = p.rho2; e.rho_i = p.rho1; e.out_is_f = 0; e.lnw_o = c.ln_b;
-    e.l2w_o = c.l2_b; e.l2lo_o = c.lo_b;
-    e.old_out = (t >= 1) ? gbuf[si] : nullptr; e.out = gbuf[so];
-    e.resid_hist = opt->residual_history; e.hist_index = t;
-    e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
-    e.lse_buf = lse_g; e.lse_policy = opt->lse_reference;
-    if (c.tc3) { e.tc_b_out = c.tc_by; e.tc_hb_out = c.tc_hby; e.tc_cen_out = c.cen_y; e.tc_pts_out = c.ys; }
-    v = sweep(c, 1, fst, ti ? &c.state->slot[si].cf : nullptr, false, &splits, &e, &fused);
+    v = g_half(L, t, host);
     if (v != UOT_OK) return v;
-    e.splits = splits;
-    if (!fused) UOT_CUDA(launch_combine(e, c.st));
     const bool last = (t == opt->max_iter);
     if (t >= 1 && (last || (opt->tol > 0.0 && t % opt->check_every == 0))) {
       v = read_flags(c, &status, &r);
@@ -507,35 +599,28 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
       if (status != 0 || isnan(r)) break;
       if (last || r <= opt->tol) break;
     }
-    // f half-step of iteration t+1: row sweep over y with gb_{t+1} = g_hat + cg
-    EpiParams ef = e;
-    ef.nq = p.n; ef.rho_o = p.rho1; ef.rho_i = p.rho2; ef.out_is_f = 1;
-    ef.lnw_o = c.ln_a; ef.old_out = nullptr; ef.out = fst; ef.resid_hist = nullptr;
-    ef.l2w_o = c.l2_a; ef.l2lo_o = c.lo_a;
-    ef.slot_in = so; ef.slot_out = so; ef.part = c.part_r; ef.lse_buf = lse_f;
-    if (c.tc3) { ef.tc_b_out = c.tc_bx; ef.tc_hb_out = c.tc_hbx; ef.tc_cen_out = c.cen_x; ef.tc_pts_out = c.xs; }
-    v = sweep(c, 0, gbuf[so], ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
+    v = f_half(L, t, host);
     if (v != UOT_OK) return v;
-    ef.splits = splits;
-    if (!fused) UOT_CUDA(launch_combine(ef, c.st));
     ++t;
     if (AK) {
       // Anderson: keep x_t; after every AK-th iteration that is neither the last nor a
       // residual check, the last AK + 1 iterates give the next one
       Slot* sl = &c.state->slot[t & 1];
-      UOT_CUDA(launch_anderson_store(fst, p.n, AK, t % (AK + 1), variant, sl, opt->anderson_buf, c.st));
+      UOT_CUDA(launch_anderson_store(L.fst, p.n, AK, t % (AK + 1), variant, sl, opt->anderson_buf, c.st));
       if (t % AK == 0 && t < opt->max_iter && !(opt->tol > 0.0 && t % opt->check_every == 0)) {
         const int p0 = (t - AK) % (AK + 1);
-        UOT_CUDA(launch_anderson_extrapolate(fst, p.n, AK, p0, opt->anderson_reg, opt->anderson_buf,
+        UOT_CUDA(launch_anderson_extrapolate(L.fst, p.n, AK, p0, opt->anderson_reg, opt->anderson_buf,
                                              variant == 2 ? sl : nullptr, &c.state->status, c.st));
         // H: the new fb is held in full (cf = 0); its Smin_a^rho1 for the next g half-step
-        if (variant == 1) UOT_CUDA(launch_ti_init(fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st, t & 1));
+        if (variant == 1) UOT_CUDA(launch_ti_init(L.fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st, t & 1));
         // the extrapolated iterate replaces f: the x side's key constants follow it
-        if (c.tc3) UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, fst, c.s, c.tc_bx, c.tc_hbx, false, c.st));
+        if (c.tc3)
+          UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, false, c.st));
       }
     }
   }
-  UOT_CUDA(launch_finalize(variant, fst, gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y, c.st));
+  UOT_CUDA(launch_finalize(variant, L.fst, L.gbuf[t & 1], f, g, p.n, p.m, c.state, t & 1, c.perm_x, c.perm_y,
+                           c.st));
   Slot slot{};
   unsigned int misses = 0;
   UOT_CUDA(cudaMemcpyAsync(&slot, &c.state->slot[t & 1], sizeof(Slot), cudaMemcpyDeviceToHost, c.st));
@@ -553,11 +638,10 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
     res->status = out;
     res->lse_misses = (int32_t)(misses > 0x7fffffffu ? 0x7fffffffu : misses);
     res->residual = r;
-    res->lambda = ti ? slot.lam : 0.0;
+    res->lambda = L.ti ? slot.lam : 0.0;
   }
   return out;
 }
-
 
 // ---- unrolled backward -------------------------------------------------------
 // Extra workspace of uot_grad_unrolled after the regular layout of the problem.
@@ -817,6 +901,110 @@ uot_status grad_unrolled(const uot_problem* prob, int T, int K, double* value, f
   return UOT_OK;
 }
 
+// ---- device-driven solve (plans) ---------------------------------------------
+// The whole solve as stream work with no host synchronisation: the set-up and
+// the first g half-step, then a conditional while node whose body runs two
+// iterations (the second inside a conditional if node, so that each captured
+// iteration keeps a fixed buffer parity), each g half-step's grid tail
+// evaluating the stopping rule and writing both conditions, then the output
+// map Phi and the device-side uot_result.  `s` must be capturing; `b1` and
+// `b2` are idle streams the two bodies are captured on.
+uot_status emit_solve(Loop& L, cudaStream_t s, cudaStream_t b1, cudaStream_t b2, uot_result* res) {
+  Ctx& c = L.c;
+  const uot_problem& p = c.p;
+  const bool prof = g_prof.open;  // event records cannot enter conditional bodies
+  g_prof.open = false;
+  struct Restore {
+    bool v;
+    ~Restore() { g_prof.open = v; }
+  } restore{prof};
+  c.st = s;
+  uot_status v = loop_prologue(L);
+  if (v != UOT_OK) return v;
+  if (L.small) {
+    v = small_loop(L);
+    if (v != UOT_OK) return v;
+    UOT_CUDA(launch_finalize_loop(L.variant, L.fst, L.gbuf[0], L.gbuf[1], L.f, L.g, p.n, p.m, c.state, c.perm_x,
+                                  c.perm_y, 1, s));
+    UOT_CUDA(launch_write_result(c.state, L.ti ? 1 : 0, 1, L.opt.tol, res, s));
+    return UOT_OK;
+  }
+  const LoopCtl host{};
+  v = g_half(L, 0, host);
+  if (v != UOT_OK) return v;
+  // the while node, after what the stream has captured so far
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  UOT_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+  if (cs != cudaStreamCaptureStatusActive) return fail(UOT_ERR_CUDA, "internal: the solve stream is not capturing");
+  cudaGraphConditionalHandle hw = 0, hi = 0;
+  UOT_CUDA(cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode = nullptr;
+  UOT_CUDA(cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  UOT_CUDA(cudaGraphConditionalHandleCreate(&hi, body, 0, 0));
+  // body: iteration t = 1, 3, 5, ... (f half-step of iteration t, g half-step of iteration t + 1)
+  UOT_CUDA(cudaStreamBeginCaptureToGraph(b1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  c.st = b1;
+  LoopCtl fc;
+  fc.ctl = 1;
+  LoopCtl gc;
+  gc.ctl = 2;
+  gc.cond_while = hw;
+  gc.cond_if = hi;
+  v = f_half(L, 0, fc);
+  if (v == UOT_OK) v = g_half(L, 1, gc);
+  cudaGraphNode_t inode = nullptr;
+  cudaGraphNodeParams ip{};
+  if (v == UOT_OK) {
+    const cudaGraphNode_t* bdeps = nullptr;
+    size_t nbdeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(b1, &cs, nullptr, nullptr, &bdeps, nullptr, &nbdeps);
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&inode, body, bdeps, nullptr, nbdeps, &ip);
+    if (e != cudaSuccess) v = cuda_fail(e, "adding the conditional if node");
+  }
+  if (v == UOT_OK) {
+    // iteration t + 1 = 2, 4, ... in the if body, then back to the while condition
+    cudaError_t e = cudaStreamBeginCaptureToGraph(b2, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) v = cuda_fail(e, "capturing the second iteration");
+    else {
+      c.st = b2;
+      LoopCtl gc2 = gc;
+      v = f_half(L, 1, fc);
+      if (v == UOT_OK) v = g_half(L, 2, gc2);
+      cudaGraph_t tmp = nullptr;
+      e = cudaStreamEndCapture(b2, &tmp);
+      if (v == UOT_OK && e != cudaSuccess) v = cuda_fail(e, "ending the second iteration's capture");
+    }
+    if (v == UOT_OK) {
+      e = cudaStreamUpdateCaptureDependencies(b1, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+      if (e != cudaSuccess) v = cuda_fail(e, "ordering the if node");
+    }
+  }
+  cudaGraph_t tmp = nullptr;
+  const cudaError_t e1 = cudaStreamEndCapture(b1, &tmp);
+  c.st = s;
+  if (v != UOT_OK) return v;
+  if (e1 != cudaSuccess) return cuda_fail(e1, "ending the loop body's capture");
+  UOT_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  UOT_CUDA(launch_finalize_loop(L.variant, L.fst, L.gbuf[0], L.gbuf[1], L.f, L.g, p.n, p.m, c.state, c.perm_x,
+                                c.perm_y, 0, s));
+  UOT_CUDA(launch_write_result(c.state, L.ti ? 1 : 0, 0, L.opt.tol, res, s));
+  return UOT_OK;
+}
+
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -840,6 +1028,41 @@ int device_sm_count() {
 }  // namespace uot
 
 using namespace uot;
+
+// A problem with its options and variant, prepared once: host-side state of
+// uot_plan_solve (private streams for capturing, executable graphs per set of
+// buffers).
+struct uot_plan {
+  uot_problem prob;
+  uot_options opt;
+  int variant;
+  int device;
+  cudaStream_t cap = nullptr, b1 = nullptr, b2 = nullptr;
+  std::mutex mu;
+  struct Exec {
+    float* f;
+    float* g;
+    uot_result* res;
+    void* ws;
+    size_t ws_bytes;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Exec> cache;  // most recent last
+};
+
+namespace {
+constexpr size_t kPlanCache = 4;
+
+void plan_release(uot_plan* P) {
+  if (!P) return;
+  for (auto& x : P->cache) cudaGraphExecDestroy(x.exec);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->b1) cudaStreamDestroy(P->b1);
+  if (P->b2) cudaStreamDestroy(P->b2);
+  delete P;
+}
+}  // namespace
+
 
 extern "C" {
 
@@ -869,6 +1092,11 @@ uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, 
   e.out_is_f = axis == 0; e.lnw_o = axis == 0 ? c.ln_a : c.ln_b; e.out = out; e.state = c.state;
   e.l2w_o = axis == 0 ? c.l2_a : c.l2_b; e.l2lo_o = axis == 0 ? c.lo_a : c.lo_b;
   e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk;
+  if (c.tc3) {
+    // the tensor-core sweep reads the key side's operand: coordinates and H of pot
+    if (axis == 0) UOT_CUDA(launch_tc3_keys(c.ys, c.p.m, c.p.dim, c.cen_y, c.l2_b, pot_i, c.s, c.tc_by, true, c.st));
+    else UOT_CUDA(launch_tc3_keys(c.xs, c.p.n, c.p.dim, c.cen_x, c.l2_a, pot_i, c.s, c.tc_bx, true, c.st));
+  }
   v = sweep(c, axis, pot_i, nullptr, false, &splits, &e, &fused);
   if (v != UOT_OK) return v;
   e.splits = splits;
@@ -995,6 +1223,98 @@ uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* l
   for (cudaEvent_t e : g_prof.ev) cudaEventDestroy(e);
   g_prof.ev.clear();
   g_prof.used = 0;
+  return UOT_OK;
+}
+
+uot_status uot_plan_create(const uot_problem* prob, const uot_options* opt, int32_t variant, uot_plan** out) {
+  if (!out) return fail(UOT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  uot_status v = validate(prob);
+  if (v != UOT_OK) return v;
+  if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");
+  if (variant < 0 || variant > 2) return fail(UOT_ERR_INVALID_ARG, "variant must be 0 (plain), 1 (TI) or 2 (G)");
+  if (opt->max_iter < 1 || opt->check_every < 1) return fail(UOT_ERR_INVALID_ARG, "need max_iter, check_every >= 1");
+  if (!(opt->tol >= 0.0) || !isfinite(opt->tol)) return fail(UOT_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (opt->lse_reference < 0 || opt->lse_reference > 2)
+    return fail(UOT_ERR_INVALID_ARG, "lse_reference must be 0, 1 or 2");
+  if (opt->anderson_k != 0)
+    return fail(UOT_ERR_UNSUPPORTED, "Anderson extrapolation is host-driven: use uot_sinkhorn / uot_ti_sinkhorn / "
+                                     "uot_g_sinkhorn for it");
+  uot_plan* P = new (std::nothrow) uot_plan();
+  if (!P) return fail(UOT_ERR_INVALID_ARG, "out of host memory");
+  P->prob = *prob;
+  P->opt = *opt;
+  P->variant = variant;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->b1, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->b2, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    plan_release(P);
+    return cuda_fail(e, "uot_plan_create");
+  }
+  // launch geometry (occupancy queries) is settled here, outside any capture
+  (void)ws_layout(*prob);
+  *out = P;
+  return UOT_OK;
+}
+
+void uot_plan_destroy(uot_plan* plan) { plan_release(plan); }
+
+size_t uot_plan_workspace_size(const uot_plan* plan) {
+  if (!plan) {
+    fail(UOT_ERR_INVALID_ARG, "plan is NULL");
+    return 0;
+  }
+  return ws_layout(plan->prob).total;
+}
+
+uot_status uot_plan_solve(uot_plan* plan, float* f, float* g, uot_result* res_dev, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (!plan) return fail(UOT_ERR_INVALID_ARG, "plan is NULL");
+  if (!res_dev) return fail(UOT_ERR_INVALID_ARG, "res_dev must be a device pointer");
+  int dev = -1;
+  UOT_CUDA(cudaGetDevice(&dev));
+  if (dev != plan->device) return fail(UOT_ERR_INVALID_ARG, "the plan was created on another device");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  Loop L;
+  uot_status v = loop_setup(L, plan->variant, &plan->prob, &plan->opt, f, g, ws, ws_bytes, stream);
+  if (v != UOT_OK) return v;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  UOT_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusActive) return emit_solve(L, st, plan->b1, plan->b2, res_dev);
+  if (cs != cudaStreamCaptureStatusNone) return fail(UOT_ERR_CUDA, "the stream's capture was invalidated");
+  cudaGraphExec_t exec = nullptr;
+  for (size_t k = 0; k < plan->cache.size(); ++k) {
+    const uot_plan::Exec& x = plan->cache[k];
+    if (x.f == f && x.g == g && x.res == res_dev && x.ws == ws && x.ws_bytes == ws_bytes) {
+      exec = x.exec;
+      uot_plan::Exec keep = x;
+      plan->cache.erase(plan->cache.begin() + (long)k);
+      plan->cache.push_back(keep);
+      break;
+    }
+  }
+  if (!exec) {
+    UOT_CUDA(cudaStreamBeginCapture(plan->cap, cudaStreamCaptureModeThreadLocal));
+    v = emit_solve(L, plan->cap, plan->b1, plan->b2, res_dev);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(plan->cap, &graph);
+    if (v != UOT_OK || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return v != UOT_OK ? v : cuda_fail(ee, "capturing the solve");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_fail(ie, "instantiating the solve graph");
+    if (plan->cache.size() >= kPlanCache) {
+      cudaGraphExecDestroy(plan->cache.front().exec);
+      plan->cache.erase(plan->cache.begin());
+    }
+    plan->cache.push_back(uot_plan::Exec{f, g, res_dev, ws, ws_bytes, exec});
+  }
+  UOT_CUDA(cudaGraphLaunch(exec, st));
   return UOT_OK;
 }
 

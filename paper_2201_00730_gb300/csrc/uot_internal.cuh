@@ -42,6 +42,10 @@ struct DevState {
   int lse_ok[2];         // the next launch of the side takes them as exponent reference
   unsigned int lse_miss; // rows recomputed because the reference was too far off
   int iters;             // iterations done by the resident small-problem solver
+  // device-driven iteration (uot_plan_solve): index t of the latest f half-step's
+  // iterate, and whether the latest check stopped the loop
+  int loop_t;
+  int loop_done;
 };
 
 // Resident solver for small point problems (dim <= 3, p = 2, N M <= 2^20, both
@@ -148,18 +152,19 @@ cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4
                               const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
                               const struct EpiParams* epi, cudaStream_t st);
 // Tensor-core tiled half-step sweep (sorted clouds, dim <= 3, p = 2) with the
-// fused epilogue (sweep_tc3.cu).  Each side has a key operand of
-// tc3_operand_floats(n) floats (16-byte aligned) and one float per 128-point
-// tile (Hbar): launch_tc3_keys builds it (full: coordinate parts too) from a
-// potential (nullable: 0); afterwards the epilogue of every half-step that
-// writes that side's potential keeps its H parts current (epi.tc_* fields).
+// fused epilogue (sweep_tc3.cu).  Each side has key tiles of
+// tc3_operand_floats(n) floats in all (16-byte aligned; per 128-point tile the
+// operand rows and a header with the tile's centre and largest key constant):
+// launch_tc3_keys builds them (full: coordinate parts too) from a potential
+// (nullable: 0); afterwards the epilogue of every half-step that writes that
+// side's potential keeps their H parts current (epi.tc_* fields).
 bool tc3_fits(int nq, int nk);
 size_t tc3_operand_floats(int n);
 SweepGeom tc3_geom(int nq, int nk);
 cudaError_t launch_tc3_keys(const float* pts, int n, int dim, const float4* cen, const float* l2w, const float* pot,
-                            double s, float* Bop, float* hb, bool full, cudaStream_t st);
+                            double s, float* Bop, bool full, cudaStream_t st);
 cudaError_t launch_tc3_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
-                             const float* pot_k, const float* Bk, const float* hbk, double s, float* part,
+                             const float* pot_k, const float* Bk, double s, float* part,
                              const SweepGeom& g, const struct EpiParams& epi, cudaStream_t st);
 // Tensor-core sweep with moments (dim >= 32, p = 2): partials [splits][2 + dim][nq]
 // (max, sum of mult_j 2^(t - max), momscale * the moments of (x_i - y_j)).
@@ -236,13 +241,20 @@ struct EpiParams {
   int lse_policy;       // 0: reference after a small change, 2: whenever one is stored
   const float* l2w_o;   // TI: log2 weights of the output side as float pairs (hi, lo)
   const float* l2lo_o;
-  // tensor-core tiled sweeps (nullable): the output side's key operand, whose
-  // H parts the epilogue rewrites from the new potential, with its tiles'
-  // Hbar, tile centres and points (Morton order)
+  // tensor-core tiled sweeps (nullable): the output side's key tiles, whose
+  // H parts and Hbar the epilogue rewrites from the new potential, with the
+  // side's tile centres and points (Morton order)
   float* tc_b_out;
-  float* tc_hb_out;
   const float4* tc_cen_out;
   const float* tc_pts_out;
+  // device-driven iteration (a solve captured in a CUDA graph, the loop a
+  // conditional while node): 1 = this f half-step advances state->loop_t; 2 =
+  // this g half-step evaluates the stopping rule of the host driver at iterate
+  // loop_t and writes "go on" into the conditional handles (0 = not set)
+  int loop_ctl;
+  int loop_max_iter, loop_check_every;
+  double loop_tol;
+  unsigned long long cond_while, cond_if;
 };
 // Fills the constants of an EpiParams that depend only on s, eps and the rhos
 // (call after setting s, eps, rho_o, rho_i).
@@ -272,6 +284,14 @@ cudaError_t launch_anderson_extrapolate(float* f, int n, int K, int p0, double r
 cudaError_t launch_finalize(int ti, const float* f_hat, const float* g_hat, float* f, float* g, int n,
                             int m, const DevState* st_dev, int slot, const int* perm_f, const int* perm_g,
                             cudaStream_t st);
+// The same for a device-driven loop: the iterate index and slot come from
+// state->loop_t (small: state->iters), its g from g0 or g1 by parity.
+cudaError_t launch_finalize_loop(int ti, const float* f_hat, const float* g0, const float* g1, float* f, float* g,
+                                 int n, int m, const DevState* s, const int* perm_f, const int* perm_g, int small,
+                                 cudaStream_t st);
+// uot_result of a finished solve from the device state, written to device memory
+// (small = the resident solver ran the loop).
+cudaError_t launch_write_result(const DevState* s, int ti, int small, double tol, uot_result* out, cudaStream_t st);
 // log weights (natural FP64, log2 FP32 and, if l2lo is not null, the FP32
 // remainder log2 w - l2w); negative / non-finite weights set kStatusBadWeights
 // in *flags (nullable).

@@ -105,6 +105,14 @@ def lib() -> C.CDLL:
         L.uot_fw1d_workspace_size.restype = S
         L.uot_fw1d_batched.argtypes = [C.POINTER(FW1DBatch), V, V, C.POINTER(C.c_int32), V, S, V]
         L.uot_fw1d_batched.restype = C.c_int
+        L.uot_plan_create.argtypes = [P, C.POINTER(Options), C.c_int32, C.POINTER(C.c_void_p)]
+        L.uot_plan_create.restype = C.c_int
+        L.uot_plan_destroy.argtypes = [V]
+        L.uot_plan_destroy.restype = None
+        L.uot_plan_workspace_size.argtypes = [V]
+        L.uot_plan_workspace_size.restype = S
+        L.uot_plan_solve.argtypes = [V, V, V, V, V, S, V]
+        L.uot_plan_solve.restype = C.c_int
         L.uot_kernel_launches.argtypes = []
         L.uot_kernel_launches.restype = C.c_uint64
         L.uot_profile_begin.argtypes = []
@@ -282,6 +290,63 @@ def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0
     st = fn(C.byref(pr), C.byref(opt), _ptr(f), _ptr(g), C.byref(res), _ptr(ws), ws.numel(), _stream())
     _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
     return SolveOut(f, g, res.iters, bool(res.converged), st, res.residual, res.lambda_, hist, res.lse_misses)
+
+
+VARIANTS = {"plain": 0, "ti": 1, "g": 2}
+
+
+class Plan:
+    """A solve prepared once and run without host synchronisation (uot_plan_create / uot_plan_solve).
+
+    solve() enqueues the whole solve on the current stream and returns at once; inside a
+    torch.cuda.graph capture it becomes part of the captured graph.  The outcome is written to a
+    device-side uot_result (result() reads it, synchronising).  Inputs are the Spec's tensors,
+    which must stay alive; f, g and the workspace belong to the plan object.
+    """
+
+    def __init__(self, spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0,
+                 check_every: int = 10, lse_reference: str = "auto", warm_start: bool = False,
+                 history: bool = False):
+        if method not in VARIANTS:
+            raise ValueError("method must be 'ti', 'plain' or 'g'")
+        self.spec = spec
+        dev = spec.a.device
+        self._pr = spec.struct()
+        self.history = (torch.full((max_iter + 1,), float("nan"), dtype=torch.float32, device=dev)
+                        if history else None)
+        self._opt = Options(int(max_iter), int(check_every), float(tol), 1 if warm_start else 0,
+                            LSE_REFERENCE[lse_reference], None if self.history is None else self.history.data_ptr(),
+                            0, 0.0, None)
+        h = C.c_void_p()
+        _check(lib().uot_plan_create(C.byref(self._pr), C.byref(self._opt), VARIANTS[method], C.byref(h)))
+        self._h = h
+        nbytes = int(lib().uot_plan_workspace_size(h))
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.f = torch.zeros(spec.n, dtype=torch.float32, device=dev)
+        self.g = torch.zeros(spec.m, dtype=torch.float32, device=dev)
+        self.res = torch.zeros(C.sizeof(Result), dtype=torch.uint8, device=dev)
+
+    def solve(self):
+        """Enqueue the solve on the current stream (f is read first when warm_start was set)."""
+        _check(lib().uot_plan_solve(self._h, _ptr(self.f), _ptr(self.g), _ptr(self.res), _ptr(self.ws),
+                                    self.ws.numel(), _stream()))
+        return self
+
+    def result(self) -> Result:
+        """The device-side uot_result of the latest solve (synchronises with it)."""
+        return Result.from_buffer_copy(bytes(self.res.cpu().numpy()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize(self.spec.a.device)  # no solve of this plan is still running
+            lib().uot_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dual_value(spec: Spec, f: torch.Tensor, g: torch.Tensor, primal: bool = False,

@@ -147,3 +147,17 @@ int main(void) {
     assert st == 2
     st = L.uot_fw1d_batched(C.byref(ok), 256, 256, None, 256, nbytes - 1, None)
     assert st == 2 and b"too small" in L.uot_last_error()
+
+
+def test_plan_rejects_anderson_and_bad_variant(L):
+    """Plans run the stopping rule on the device; Anderson extrapolation stays host-driven and is
+    rejected before any CUDA call, as is an unknown variant."""
+    from paper_2201_00730_gb300 import uot
+    pr = uot.Problem(10, 12, 2, 0, 2.0, 0, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
+    h = C.c_void_p()
+    opt = uot.Options(10, 5, 0.0, 0, 0, None, 4, 1e-7, 256)
+    assert L.uot_plan_create(C.byref(pr), C.byref(opt), 1, C.byref(h)) == 7
+    assert b"Anderson" in L.uot_last_error() and not h.value
+    opt = uot.Options(10, 5, 0.0, 0, 0, None, 0, 0.0, None)
+    assert L.uot_plan_create(C.byref(pr), C.byref(opt), 5, C.byref(h)) == 1
+    assert L.uot_plan_workspace_size(None) == 0
