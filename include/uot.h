@@ -298,6 +298,18 @@ UOT_API uot_status uot_grad(const uot_problem* prob, const float* f, const float
  * sweep launches seen in *launches.  Events are created at begin and destroyed
  * at end.  Returns UOT_ERR_INVALID_ARG when no profile is open. */
 UOT_API uint64_t uot_kernel_launches(void);
+/* Test hook (no counterpart in the paper): caps the number of polls of the
+ * main-loop mbarrier waits of the tensor-core sweeps (dim <= 3 tiled solver
+ * half-steps, dim >= 32 sweeps) at `polls` (0 restores the default, about
+ * 1.7e7; a negative value allows no poll at all), process-wide, for launches
+ * made afterwards.  With no poll allowed every such wait gives up at once
+ * (with one poll, only those whose condition is not met within the first
+ * poll's wait window): the sweep then stops its roles, lets every
+ * copy and MMA in flight land (those waits keep the default limit), frees its
+ * tensor memory and reports a timeout, so that the solver returns
+ * UOT_ERR_TIMEOUT and the CUDA context stays usable.  This is how the timeout
+ * path is tested without faulting or hanging a GPU. */
+UOT_API void uot_test_set_wait_limit(int64_t polls);
 UOT_API uot_status uot_profile_begin(void);
 UOT_API uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* launches);
 
@@ -401,6 +413,55 @@ UOT_API size_t uot_fw1d_workspace_size(const uot_fw1d_batch* batch);
  * the first failing problem's status. */
 UOT_API uot_status uot_fw1d_batched(const uot_fw1d_batch* batch, double* f, double* g, int32_t* status,
                                     void* ws, size_t ws_bytes, void* stream);
+
+/* 1-D unbalanced multi-marginal OT and barycenters (Sec. 5): K measures
+ * (x_k, alpha_k) on the line per problem, barycentric weights omega_k > 0
+ * summing to one, rho KL penalties (rho_k = omega_k rho in the dual) and the
+ * squared-distance cost, whose multi-marginal form is
+ *   C(z_1..z_K) = sum_k omega_k (z_k - B(z))^2,  B(z) = sum_k omega_k z_k.
+ * Frank-Wolfe on the translation-invariant functional H: each step computes
+ * the optimal translation lambda (Sec. 5, rho KL setting:
+ * lambda_k = omega_k rho q_k - omega_k sum_l omega_l rho q_l / sum_l omega_l,
+ * q_k = log <alpha_k, e^{-fb_k/(omega_k rho)}>), the re-weighted measures
+ * alpha~_k = alpha_k e^{-(fb_k + lambda_k)/(omega_k rho)}, the balanced
+ * multi-marginal duals r between them by one pass over the sorted points
+ * (SolveMOT, Alg. 3: the measure with the least remaining mass among those
+ * not at their last point moves, lowest index on ties; the last index tuple
+ * takes the mass left), and fb <- (1 - tau_t) fb + tau_t r, tau_t = 2/(2+t),
+ * from fb = 0.  Outputs the translated potentials f_k = fb_k + lambda_k and the
+ * barycenter of Prop. prop:barycentermulti: the points B(tuple) of the plan
+ * SolveMOT returns at the final iterate (tuples of positive mass, in plan
+ * order) with those masses as weights.  FP64 throughout; one warp runs one
+ * problem. */
+typedef struct {
+  int32_t count;          /* number of problems >= 1                                           */
+  int32_t n_iter;         /* Frank-Wolfe steps >= 1                                            */
+  int32_t K;              /* measures per problem, 2..8, shared by the batch                    */
+  int32_t reserved;
+  const int32_t* n;       /* host [count * K]: points of measure k of problem p at [p * K + k]  */
+  const int64_t* off;     /* host [count * K]: first point of that measure in x, alpha and f    */
+  const double* rho;      /* host [count]: finite, > 0                                         */
+  const double* omega;    /* host [count * K]: barycentric weights > 0, summing to one          */
+  const float* x;         /* device, packed points, ascending within each measure             */
+  const float* alpha;     /* device, packed weights >= 0, positive total per measure          */
+} uot_mmot1d_batch;
+
+/* Workspace bytes of uot_mmot1d_batched (0 if the batch is invalid), and the
+ * length of the barycenter output arrays: the sum over problems of their
+ * points, problem p's barycenter starting after those of problems 0..p-1. */
+UOT_API size_t uot_mmot1d_workspace_size(const uot_mmot1d_batch* batch);
+UOT_API size_t uot_mmot1d_barycenter_size(const uot_mmot1d_batch* batch);
+
+/* Runs batch->n_iter Frank-Wolfe steps on every problem.  f: device FP64,
+ * indexed like x.  bary_x, bary_w: device FP64 of uot_mmot1d_barycenter_size
+ * entries; bary_len: optional host [count], the number of barycenter points of
+ * each problem.  status: optional host [count], per problem UOT_OK,
+ * UOT_ERR_INVALID_ARG (points not ascending or not finite) or
+ * UOT_ERR_NONFINITE (a weight negative or not finite, or a measure of zero
+ * mass).  Synchronises the stream; returns UOT_OK when every problem is valid,
+ * else the first failing problem's status. */
+UOT_API uot_status uot_mmot1d_batched(const uot_mmot1d_batch* batch, double* f, double* bary_x, double* bary_w,
+                                      int32_t* bary_len, int32_t* status, void* ws, size_t ws_bytes, void* stream);
 
 /* Message describing the last error of the calling thread ("" if none). */
 UOT_API const char* uot_last_error(void);

@@ -69,8 +69,11 @@ constexpr int kSbo = (kK / 4) * 128;    // bytes between 8-row core-matrix group
 constexpr int kOpBytes = kKeys * kK * 4;       // operand part of a key tile
 constexpr int kTileBytes = kOpBytes + 128;     // + header {o_T.x, o_T.y, o_T.z, Hbar_T}, padding
 constexpr int kTileFloats = kTileBytes / 4;
-constexpr int kStages = 4;              // row-operand stages = TMEM accumulators
-constexpr int kBStages = 8;             // key-tile stages (copies run kBStages - kStages tiles ahead)
+constexpr int kStages = 4;              // TMEM accumulators
+constexpr int kAStages = 8;             // row-operand stages (the builders run up to 8 tiles ahead)
+constexpr int kBStages = 12;            // key-tile stages
+constexpr int kLag = 4;                 // a key stage is refilled kLag units after its MMAs were issued
+static_assert(kLag < kAStages && kLag < kBStages, "refill lag");
 constexpr int kCols = kStages * kKeys;  // all 512 TMEM columns
 constexpr int kConsWarps = 8;
 constexpr int kBuildWarps = 4;
@@ -82,16 +85,17 @@ constexpr int kThreads = kEpiBase + 32 * kEpiWarps;
 constexpr int kQueue = 8;               // row blocks handed to the epilogue warps, in flight
 constexpr int kBarCons = 1, kBarEpi = 2;
 constexpr uint32_t kIdesc = tc::idesc_tf32(kRows, kKeys);
-constexpr long long kSpin = 1LL << 24;  // mbarrier polls before giving up
-constexpr size_t kSmemBytes = 136 * 1024;  // more than half the SM: one CTA per SM
+constexpr long long kSpin = kWaitPolls;  // drain, hand-off and epilogue waits: polls before giving up
+constexpr size_t kSmemBytes = 184 * 1024;  // more than half the SM: one CTA per SM
 static_assert(kTileKeys == kKeys, "the key tiles of the ordering step are the MMA tiles");
 
 struct Smem {
-  float A[kStages][kRows * kK];
+  float A[kAStages][kRows * kK];
   float B[kBStages][kTileFloats];
   float2 half[kRows];             // column half 1 of each row -> half 0
   float2 halfc[kRows];            // its compensation (reference mode) / unused
-  uint64_t a_full[kStages];       // the builders wrote A of the stage
+  uint64_t a_full[kAStages];      // the builders wrote A of the stage
+  uint64_t a_free[kAStages];      // the MMAs that read A of the stage (and every earlier MMA) completed
   uint64_t b_full[kBStages];      // the key tile of the stage landed
   uint64_t m_done[kStages];       // the MMAs of the stage completed
   uint64_t acc_empty[kStages];    // the consumers read the accumulator
@@ -171,16 +175,20 @@ __device__ __forceinline__ float group_max(float v, const epi::Grp& g, float* sh
 // The H part of the operand rows of key tile T (one thread per key p of the
 // tile, the whole group): Hbar_T = the largest live H (0 if none), the row
 // gets H - Hbar_T in three tf32 parts (dead and padding keys: kZeroW, so that
-// their entries vanish), and Hbar_T goes into the tile's header.
-__device__ __forceinline__ void write_key_h(float* __restrict__ Bop, int T, int p, bool live, float H,
-                                            const epi::Grp& g, float* sh) {
+// their entries vanish), and Hbar_T goes into the tile's header (for the row
+// builders) and into hb[T] (for the consumers).
+__device__ __forceinline__ void write_key_h(float* __restrict__ Bop, float* __restrict__ hb, int T, int p, bool live,
+                                            float H, const epi::Grp& g, float* sh) {
   float hm = group_max(live ? H : -INFINITY, g, sh);
   if (!(hm > -INFINITY)) hm = 0.f;
   float h0 = kZeroW, h1 = 0.f, h2 = 0.f;
   if (live) split3(H - hm, h0, h1, h2);
   float* tile = Bop + (size_t)T * kTileFloats;
   put4(tile, p, 12, h0, h1, h2, 0.f);
-  if (g.tid == 0) tile[kOpBytes / 4 + 3] = hm;
+  if (g.tid == 0) {
+    tile[kOpBytes / 4 + 3] = hm;
+    hb[T] = hm;
+  }
 }
 
 // Key operand of one side, one CTA (128 threads) per tile: with `full` the
@@ -190,7 +198,7 @@ __device__ __forceinline__ void write_key_h(float* __restrict__ Bop, int T, int 
 template <int D>
 __global__ void __launch_bounds__(kKeys)
 k_tc3_keys(const float* __restrict__ pts, int n, const float4* __restrict__ cen, const float* __restrict__ l2w,
-           const float* __restrict__ pot, double s, float* __restrict__ Bop, int full) {
+           const float* __restrict__ pot, double s, float* __restrict__ Bop, float* __restrict__ hb, int full) {
   __shared__ float sh[kKeys / 32];
   const int T = blockIdx.x, p = threadIdx.x, j = T * kKeys + p;
   const float sf = (float)s, s2 = (float)(2.0 * s);
@@ -224,7 +232,7 @@ k_tc3_keys(const float* __restrict__ pts, int n, const float4* __restrict__ cen,
   const bool live = in && lw > 0.5f * kZeroW;
   // H_j = log2 w_j + s pot_j - s |k'_j|^2 in FP32, as the CUDA-core tiled sweep forms it
   const float H = live ? fmaf(-sf, r2, fmaf(sf, pot ? pot[j] : 0.f, lw)) : kZeroW;
-  write_key_h(Bop, T, p, live, H, epi::whole_block(), sh);
+  write_key_h(Bop, hb, T, p, live, H, epi::whole_block(), sh);
 }
 
 // Parameters of one launch (the query side's rows, the key side's operand).
@@ -235,9 +243,11 @@ struct Tc3Args {
   const float* kl2w;    // key log2 weights (exact recompute)
   const float* kpot;    // key potential (exact recompute)
   const float* Bk;      // key tiles: [TT][128 x 16 tf32, canonical K-major | header]
+  const float* hbk;     // Hbar of each key tile (also in the headers)
   float* part;          // partials [slots][2][nq]
   int nq, nk, TT;
   double s;
+  long long spin;       // polls of a main-loop wait before it gives up
 };
 
 template <int D>
@@ -256,15 +266,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
   const long long U = (long long)RB * TT, G = gridDim.x;
   const long long u0 = (long long)blockIdx.x * U / G, u1 = ((long long)blockIdx.x + 1) * U / G;
   const int L = (int)(u1 - u0);
+  const int rb0 = (int)(u0 / TT), T0 = (int)(u0 % TT);  // the range's first unit (units advance tile-major)
   const float sf = (float)a.s;
   const bool use_ref = e.lse_buf != nullptr && e.state->lse_ok[e.out_is_f] != 0;
 
   if (warp == 0) tc::tmem_alloc(&sm.tmem, kCols);
   if (tid == 32 * kIssueWarp) {
-    for (int b = 0; b < kStages; ++b) {
+    for (int b = 0; b < kAStages; ++b) {
       tc::mbar_init(&sm.a_full[b], kBuildWarps);
+      tc::mbar_init(&sm.a_free[b], 1);
+    }
+    for (int b = 0; b < kStages; ++b) {
       tc::mbar_init(&sm.m_done[b], 1);
-      tc::mbar_init(&sm.acc_empty[b], kConsWarps);
+      tc::mbar_init(&sm.acc_empty[b], kConsWarps / 2);  // the group that takes the unit
     }
     for (int b = 0; b < kBStages; ++b) tc::mbar_init(&sm.b_full[b], 1);
     for (int k = 0; k < kQueue; ++k) {
@@ -282,76 +296,84 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
 
   if (warp == kIssueWarp) {
     // ------------------------------------------------------------------ copies and MMAs
-    // Key tile of unit t in stage t % kBStages; the copy for unit t + kBStages goes into
-    // that stage once every role is done with unit t (its accumulator was read, which
-    // the MMAs of unit t + kStages wait for anyway).
+    // Key tile of unit t in stage t % kBStages, refilled with unit t + kBStages once the MMAs
+    // of unit t completed (the builders read its header before those MMAs).
     if (lane == 0) {
       int armed[kBStages] = {}, used[kBStages] = {};
-      int committed = -1, reused = -1;  // units committed; MMAs of units <= reused seen complete
+      int committed = -1, freed = -1;  // units committed; a_free seen for units <= freed
+      int Tc = T0;                     // key tile of the next unit to copy (copies go in unit order)
       auto copy_b = [&](int t) {
         const int sb = t % kBStages;
-        const int T = (int)((u0 + t) % TT);
+        const int T = Tc;
+        if (++Tc == TT) Tc = 0;
         tc::mbar_arrive_expect_tx(&sm.b_full[sb], (uint32_t)kTileBytes);
         tc::bulk_g2s(sm.B[sb], a.Bk + (size_t)T * kTileFloats, (uint32_t)kTileBytes, &sm.b_full[sb]);
         ++armed[sb];
       };
       for (int t = 0; t < L && t < kBStages; ++t) copy_b(t);
       for (int t = 0; t < L && !*err; ++t) {
-        const int st = t % kStages, sb = t % kBStages;
-        bool ok = tc::mbar_wait(&sm.a_full[st], (uint32_t)((t / kStages) & 1), kSpin);
-        ok = ok && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), kSpin);
+        const int st = t % kStages, sa = t % kAStages, sb = t % kBStages;
+        bool ok = tc::mbar_wait(&sm.a_full[sa], (uint32_t)((t / kAStages) & 1), a.spin);
+        ok = ok && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), a.spin);
         if (ok) ++used[sb];
-        if (ok && t >= kStages) {
-          // accumulator st was last read for unit t - kStages: its key stage can take unit t - kStages + kBStages
-          ok = tc::mbar_wait(&sm.acc_empty[st], (uint32_t)(((t - kStages) / kStages) & 1), kSpin);
-          if (ok) {
-            reused = t - kStages;
-            if (t - kStages + kBStages < L) copy_b(t - kStages + kBStages);
-          }
-        }
+        // accumulator st was last read for unit t - kStages
+        ok = ok && (t < kStages ||
+                    tc::mbar_wait(&sm.acc_empty[st], (uint32_t)(((t - kStages) / kStages) & 1), a.spin));
         if (!ok) { *err = 1; break; }
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(st * kKeys);
-        const uint64_t da = tc::smem_desc(tc::smem_addr(sm.A[st]), 128, kSbo);
+        const uint64_t da = tc::smem_desc(tc::smem_addr(sm.A[sa]), 128, kSbo);
         const uint64_t db = tc::smem_desc(tc::smem_addr(sm.B[sb]), 128, kSbo);
         tc::mma_tf32(d, da, db, kIdesc, false);
         tc::mma_tf32(d, da + (256 >> 4), db + (256 >> 4), kIdesc, true);  // K values 8..15
         tc::commit(&sm.m_done[st]);
+        tc::commit(&sm.a_free[sa]);
         committed = t;
+        // the key stage of unit t - kLag takes unit t - kLag + kBStages once the MMAs of that unit
+        // completed (kLag units back, so that this wait does not hold up the next MMAs: a commit's
+        // arrival trails the MMAs by hundreds of cycles)
+        if (t >= kLag && t - kLag + kBStages < L) {
+          if (!tc::mbar_wait(&sm.a_free[(t - kLag) % kAStages], (uint32_t)(((t - kLag) / kAStages) & 1), a.spin)) {
+            *err = 1;
+            break;
+          }
+          freed = t - kLag;
+          copy_b(t - kLag + kBStages);
+        }
       }
+      // every copy armed lands and every MMA commit arrives before the CTA ends (bounded)
       if (*err) {
-        // let every copy armed and every MMA committed land before the CTA ends (bounded)
         for (int sb = 0; sb < kBStages; ++sb)
           for (; used[sb] < armed[sb]; ++used[sb])
             (void)tc::mbar_wait(&sm.b_full[sb], (uint32_t)(used[sb] & 1), kSpin);
-        for (int t = reused + 1; t <= committed; ++t) {
-          if (t + kStages <= committed) continue;  // only the latest commit of each stage
-          (void)tc::mbar_wait(&sm.m_done[t % kStages], (uint32_t)((t / kStages) & 1), kSpin);
-        }
       }
+      for (int t = freed + 1; t <= committed; ++t) {
+        if (t + kAStages <= committed) continue;  // only the latest commit of each row stage
+        (void)tc::mbar_wait(&sm.a_free[t % kAStages], (uint32_t)((t / kAStages) & 1), kSpin);
+      }
+      for (int t = committed - kStages + 1; t <= committed; ++t)
+        if (t >= 0) (void)tc::mbar_wait(&sm.m_done[t % kStages], (uint32_t)((t / kStages) & 1), kSpin);
     }
     __syncwarp();
   } else if (warp >= kConsWarps && warp < kIssueWarp) {
     // ------------------------------------------------------------------ row builders
     const int p = tid - kBuildBase;
-    int rb = -1;
+    int rb = rb0, T = T0;
     bool live = false;
     float xq[3] = {0.f, 0.f, 0.f}, mref = 0.f;
     for (int t = 0; t < L; ++t) {
-      const long long u = u0 + t;
-      const int rbt = (int)(u / TT);
-      if (rbt != rb) {
-        rb = rbt;
+      if (t > 0 && ++T == TT) { T = 0; ++rb; }
+      if (t == 0 || T == 0) {
         const int i = rb * kRows + p;
         live = i < nq;
 #pragma unroll
         for (int d = 0; d < 3; ++d) xq[d] = (live && d < D) ? a.q[(size_t)i * D + d] : 0.f;
         mref = (live && use_ref) ? e.lse_buf[i] : 0.f;
       }
-      const int st = t % kStages, sb = t % kBStages;
-      // the tile's header arrives with its copy; the row stage is free once its accumulator was read
-      bool ok = !*err && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), kSpin);
-      if (ok && t >= kStages) ok = tc::mbar_wait(&sm.acc_empty[st], (uint32_t)(((t - kStages) / kStages) & 1), kSpin);
+      const int sa = t % kAStages, sb = t % kBStages;
+      // the tile's header arrives with its copy; the row stage is free once the MMAs that read it completed
+      bool ok = !*err && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), a.spin);
+      if (ok && t >= kAStages) ok = tc::mbar_wait(&sm.a_free[sa], (uint32_t)(((t - kAStages) / kAStages) & 1), a.spin);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) *err = 1;
@@ -368,103 +390,112 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
       const float l0 = tc::to_tf32(x0 - h0), l1 = tc::to_tf32(x1 - h1), l2 = tc::to_tf32(x2 - h2);
       float ch, cm, cl;
       split3(c, ch, cm, cl);
-      float* A = sm.A[st];
+      float* A = sm.A[sa];
       put4(A, p, 0, h0, l0, h0, h1);
       put4(A, p, 4, l1, h1, h2, l2);
       put4(A, p, 8, h2, ch, cm, cl);
       put4(A, p, 12, 1.f, 1.f, 1.f, 0.f);
       tc::fence_proxy_async();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&sm.a_full[st]);
+      if (lane == 0) tc::mbar_arrive(&sm.a_full[sa]);
     }
   } else if (warp < kConsWarps) {
     // ------------------------------------------------------------------ consumers
-    const int lq = warp & 3, hc = warp >> 2;  // TMEM lane quarter, column half
+    // Two groups of four warps take alternate units (group pg the units t with
+    // t % 2 == pg), so that one group reads its accumulator while the other is on
+    // the MUFU; warp w reads TMEM lanes 32 (w % 4) .. + 31, all 128 columns.
+    const int lq = warp & 3, pg = warp >> 2;
     const int row = 32 * lq + lane;
-    const uint32_t tl = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(64 * hc);
+    const uint32_t tl = tmem + ((uint32_t)(32 * lq) << 16);
     float M = kInitMax, S = 0.f, Cc = 0.f;  // running (max, sum, compensation) of the row
     bool dead = false;
     int qpost = 0;  // row blocks handed to the epilogue warps (thread 0 of the consumers)
-    auto post = [&](int rb) -> bool {
+    auto post = [&](int rbp) -> bool {
       const int k = qpost % kQueue;
       if (qpost >= kQueue &&
           !tc::mbar_wait(&sm.q_empty[k], (uint32_t)(((qpost / kQueue) - 1) & 1), kSpin))
         return false;
-      sm.queue[k] = rb;
+      sm.queue[k] = rbp;
       tc::mbar_arrive(&sm.q_full[k]);
       ++qpost;
       return true;
     };
+    // 64 exponents of v (log2 units) summed into (S, Cc), with the running max in running-max mode
+    auto consume = [&](const uint32_t (&r0)[32], const uint32_t (&r1)[32], float hbar) {
+      float v[64];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) { v[k] = __uint_as_float(r0[k]); v[32 + k] = __uint_as_float(r1[k]); }
+      u64 s0 = pk(0.f, 0.f), s1 = pk(0.f, 0.f);
+      if (use_ref) {
+        // v = t - m: the sum needs no max
+#pragma unroll
+        for (int k = 0; k < 64; k += 8) ex2_sum8(v + k, s0, s1);
+        float x0, x1;
+        upk(add2(s0, s1), x0, x1);
+        two_add(S, Cc, x0 + x1);
+      } else {
+        // v = t - Hbar_T: the max and sum of these 64, merged into the running pair
+        float cm = fmaxf(v[0], v[1]);
+#pragma unroll
+        for (int k = 2; k < 64; k += 2) cm = max3f(cm, v[k], v[k + 1]);
+        const u64 nm = pk(-cm, -cm);
+#pragma unroll
+        for (int k = 0; k < 64; k += 8) {
+          float w[8];
+#pragma unroll
+          for (int h = 0; h < 8; h += 2) upk(add2(pk(v[k + h], v[k + h + 1]), nm), w[h], w[h + 1]);
+          ex2_sum8(w, s0, s1);
+        }
+        float x0, x1;
+        upk(add2(s0, s1), x0, x1);
+        const float mT = cm + hbar;
+        const float Mn = fmaxf(M, mT);
+        const float f0 = ex2f(M - Mn);
+        S *= f0;
+        Cc *= f0;
+        two_add(S, Cc, (x0 + x1) * ex2f(mT - Mn));
+        M = Mn;
+      }
+    };
+    int rb = rb0, T = T0;
     for (int t = 0; t < L; ++t) {
-      const long long u = u0 + t;
-      const int rb = (int)(u / TT), T = (int)(u % TT);
-      const int st = t % kStages, sb = t % kBStages;
-      float hbar = 0.f;
-      if (!dead) {
-        bool ok = !*err && tc::mbar_wait(&sm.m_done[st], (uint32_t)((t / kStages) & 1), kSpin);
-        // (the tile's copy completed before its MMAs; this wait makes its header visible here)
-        ok = ok && tc::mbar_wait(&sm.b_full[sb], (uint32_t)((t / kBStages) & 1), kSpin);
+      if (t > 0 && ++T == TT) { T = 0; ++rb; }
+      const int st = t % kStages;
+      if ((t & 1) == pg && !dead) {
+        const float hbar = use_ref ? 0.f : __ldg(a.hbk + T);
+        bool ok = !*err && tc::mbar_wait(&sm.m_done[st], (uint32_t)((t / kStages) & 1), a.spin);
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-wide
         if (!ok) {
           if (lane == 0) *err = 1;
           dead = true;
-        }
-      }
-      if (!dead) {
-        hbar = sm.B[sb][kOpBytes / 4 + 3];
-        tc::fence_after_sync();
-        uint32_t r0[32], r1[32];
-        ld32_async(tl + (uint32_t)(st * kKeys), r0);
-        ld32_async(tl + (uint32_t)(st * kKeys + 32), r1);
-        wait_ld32(r0);
-        wait_ld32(r1);
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&sm.acc_empty[st]);
-        float v[64];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) { v[k] = __uint_as_float(r0[k]); v[32 + k] = __uint_as_float(r1[k]); }
-        u64 s0 = pk(0.f, 0.f), s1 = pk(0.f, 0.f);
-        if (use_ref) {
-          // v = t - m: the sum needs no max
-#pragma unroll
-          for (int k = 0; k < 64; k += 8) ex2_sum8(v + k, s0, s1);
-          float x0, x1;
-          upk(add2(s0, s1), x0, x1);
-          two_add(S, Cc, x0 + x1);
         } else {
-          // v = t - Hbar_T: this tile's max and sum, merged into the running pair
-          float cm = fmaxf(v[0], v[1]);
-#pragma unroll
-          for (int k = 2; k < 64; k += 2) cm = max3f(cm, v[k], v[k + 1]);
-          const u64 nm = pk(-cm, -cm);
-#pragma unroll
-          for (int k = 0; k < 64; k += 8) {
-            float w[8];
-#pragma unroll
-            for (int h = 0; h < 8; h += 2) upk(add2(pk(v[k + h], v[k + h + 1]), nm), w[h], w[h + 1]);
-            ex2_sum8(w, s0, s1);
-          }
-          float x0, x1;
-          upk(add2(s0, s1), x0, x1);
-          const float mT = cm + hbar;
-          const float Mn = fmaxf(M, mT);
-          const float f0 = ex2f(M - Mn);
-          S *= f0;
-          Cc *= f0;
-          two_add(S, Cc, (x0 + x1) * ex2f(mT - Mn));
-          M = Mn;
+          tc::fence_after_sync();
+          uint32_t r0[32], r1[32];
+          const uint32_t ta = tl + (uint32_t)(st * kKeys);
+          ld32_async(ta, r0);
+          ld32_async(ta + 32, r1);
+          wait_ld32(r0);
+          wait_ld32(r1);
+          consume(r0, r1, hbar);
+          ld32_async(ta + 64, r0);
+          ld32_async(ta + 96, r1);
+          wait_ld32(r0);
+          wait_ld32(r1);
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&sm.acc_empty[st]);
+          consume(r0, r1, hbar);
         }
       }
       if (T == TT - 1 || t == L - 1) {
-        // the end of this CTA's part of row block rb: the two column halves of a row make one partial
+        // the end of this CTA's part of row block rb: the two groups' sums of a row make one partial
         const int i = rb * kRows + row;
-        if (hc == 1) {
+        if (pg == 1) {
           sm.half[row] = make_float2(M, S);
           sm.halfc[row] = make_float2(Cc, 0.f);
         }
         asm volatile("bar.sync %0, %1;" ::"n"(kBarCons), "n"(32 * kConsWarps) : "memory");
-        if (hc == 0 && i < nq) {
+        if (pg == 0 && i < nq) {
           const float2 h1 = sm.half[row];
           const float c1 = sm.halfc[row].x;
           float Mo, So;
@@ -573,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tc3(Tc3Args a, EpiParams 
           }
           H = fmaf(-sf, r2, fmaf(sf, vo, lw));
         }
-        write_key_h(e.tc_b_out, rb, g.tid, live, H, g, sm.hmax);
+        write_key_h(e.tc_b_out, e.tc_hb_out, rb, g.tid, live, H, g, sm.hmax);
       }
       epi::block_finish(e, ea, rb, RB, g);
       g.sync();
@@ -629,23 +660,24 @@ SweepGeom tc3_geom(int nq, int nk) {
 }
 
 cudaError_t launch_tc3_keys(const float* pts, int n, int dim, const float4* cen, const float* l2w, const float* pot,
-                            double s, float* Bop, bool full, cudaStream_t st) {
+                            double s, float* Bop, float* hb, bool full, cudaStream_t st) {
   const int tiles = (n + kKeys - 1) / kKeys;
   switch (dim) {
-    case 1: k_tc3_keys<1><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, full ? 1 : 0); break;
-    case 2: k_tc3_keys<2><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, full ? 1 : 0); break;
-    default: k_tc3_keys<3><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, full ? 1 : 0);
+    case 1: k_tc3_keys<1><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, hb, full ? 1 : 0); break;
+    case 2: k_tc3_keys<2><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, hb, full ? 1 : 0); break;
+    default: k_tc3_keys<3><<<tiles, kKeys, 0, st>>>(pts, n, cen, l2w, pot, s, Bop, hb, full ? 1 : 0);
   }
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc3_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
-                             const float* pot_k, const float* Bk, double s, float* part,
+                             const float* pot_k, const float* Bk, const float* hbk, double s, float* part,
                              const SweepGeom& g, const EpiParams& epi, cudaStream_t st) {
   EpiParams e = epi;
   epi_finish_params(e);
-  Tc3Args a{q.pts, k.pts, centers_k, k.l2w, pot_k, Bk, part, q.n, k.n, (k.n + kKeys - 1) / kKeys, s};
+  Tc3Args a{q.pts, k.pts, centers_k, k.l2w, pot_k, Bk, hbk, part, q.n, k.n, (k.n + kKeys - 1) / kKeys, s,
+            wait_limit()};
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

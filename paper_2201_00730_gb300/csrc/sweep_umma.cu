@@ -45,7 +45,7 @@ constexpr int kAccCols = kKeys;               // TMEM columns per accumulator (N
 constexpr int kAcc = 2;                       // accumulators in TMEM (a ring)
 constexpr int kTmemCols = kAcc * kAccCols;
 constexpr int kMaxChunk = 4096;               // keys per CTA (H_j kept in shared memory)
-constexpr long long kSpin = 1LL << 24;        // mbarrier polls before giving up
+constexpr long long kSpin = kWaitPolls;       // drain waits: mbarrier polls before giving up
 constexpr uint32_t kIdesc = tc::idesc_f16(kRows, kKeys);  // N = 256, the largest for M = 128
 constexpr uint32_t kPiece = 65536;            // bytes per bulk copy
 constexpr size_t kOneCtaSmem = 120 * 1024;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kAllThreads, 1)
 k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int nq, const __half* __restrict__ opk,
              const float* __restrict__ nk2, int nk, const float* __restrict__ l2w, const float* __restrict__ pot,
              const double* __restrict__ shift, double s, const int* __restrict__ maxbits, int TT, int splits,
-             float* __restrict__ part) {
+             float* __restrict__ part, long long spin, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int dim16 = 16 * KS;
   constexpr int KA = 2 * dim16;  // FP16 values a row
@@ -237,7 +237,7 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
           if (++tile == TT) { tile = 0; ++rb; }
           if (tile == 0) {
             // next row block: its rows replace A once the MMAs of tile t - 1, the last to read A, completed
-            if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), kSpin)) {
+            if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), spin)) {
               *err = 1;
               break;
             }
@@ -248,13 +248,13 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
         }
         bool ok = true;
         if (a_used < a_armed) {
-          ok = tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), kSpin);
+          ok = tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), spin);
           if (ok) ++a_used;
         }
-        ok = ok && tc::mbar_wait(&br.b_full[st], (uint32_t)((t / kStages) & 1), kSpin);
+        ok = ok && tc::mbar_wait(&br.b_full[st], (uint32_t)((t / kStages) & 1), spin);
         if (ok) ++used[st];
         // accumulator b was last read for tile t - kAcc
-        ok = ok && (t < kAcc || tc::mbar_wait(&br.empty[b], (uint32_t)(((t - kAcc) / kAcc) & 1), kSpin));
+        ok = ok && (t < kAcc || tc::mbar_wait(&br.empty[b], (uint32_t)(((t - kAcc) / kAcc) & 1), spin));
         if (!ok) { *err = 1; break; }
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(b * kAccCols);
@@ -271,7 +271,7 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
         committed = t;
         // key stage of unit t - 1 -> unit t - 1 + kStages, once the MMAs of unit t - 1 completed
         if (t >= 1 && t - 1 + kStages < L) {
-          if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), kSpin)) { *err = 1; break; }
+          if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), spin)) { *err = 1; break; }
           reused = t - 1;
           const int rs = (t - 1) % kStages;
           copy_pieces(reinterpret_cast<char*>(B) + (size_t)rs * bytesB,
@@ -306,7 +306,7 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
       if (t > 0 && ++tile == TT) { tile = 0; ++rb; }
       if (!dead) {
         const int b = t % kAcc;
-        bool done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), kSpin);
+        bool done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), spin);
         done = __all_sync(0xffffffffu, done);  // tcgen05.ld is warp-wide
         if (!done) {
           if (lane == 0) *err = 1;
@@ -391,6 +391,7 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (tid == 0 && br.err && status) atomicOr(status, kStatusTimeout);
 }
 
 size_t umma_smem_bytes(int dim16) {
@@ -403,7 +404,7 @@ size_t umma_smem_bytes(int dim16) {
 template <int KS>
 cudaError_t run_umma(const __half* opq, const float* nq2, int nq, const __half* opk, const float* nk2, int nk,
                      const float* l2w, const float* pot, const double* shift, double s, const int* maxbits,
-                     float* part, const SweepGeom& g, cudaStream_t st) {
+                     float* part, const SweepGeom& g, int* status, cudaStream_t st) {
   const size_t smem = umma_smem_bytes(16 * KS);
   static std::mutex mu;
   static bool attr = false;
@@ -416,7 +417,7 @@ cudaError_t run_umma(const __half* opq, const float* nq2, int nq, const __half* 
     }
   }
   k_sweep_umma<KS><<<g.ctas, kAllThreads, smem, st>>>(opq, nq2, nq, opk, nk2, nk, l2w, pot, shift, s, maxbits,
-                                                      g.keys_per_split / kKeys, g.splits, part);
+                                                      g.keys_per_split / kKeys, g.splits, part, wait_limit(), status);
   note_launch();
   return cudaGetLastError();
 }
@@ -478,13 +479,13 @@ SweepGeom umma_geom(int nq, int nk) {
 
 cudaError_t launch_umma_sweep(const void* opq, const float* nq2, int nq, const void* opk, const float* nk2, int nk,
                               int dim, const float* l2w, const float* pot, const double* shift, double s,
-                              const int* maxbits, float* part, const SweepGeom& g, cudaStream_t st) {
+                              const int* maxbits, float* part, const SweepGeom& g, int* status, cudaStream_t st) {
   const __half* q = static_cast<const __half*>(opq);
   const __half* k = static_cast<const __half*>(opk);
   switch (umma_dim16(dim) / 16) {
-    case 2: return run_umma<2>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, st);
-    case 3: return run_umma<3>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, st);
-    default: return run_umma<4>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, st);
+    case 2: return run_umma<2>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, status, st);
+    case 3: return run_umma<3>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, status, st);
+    default: return run_umma<4>(q, nq2, nq, k, nk2, nk, l2w, pot, shift, s, maxbits, part, g, status, st);
   }
 }
 

@@ -121,7 +121,7 @@ struct WsLayout {
   size_t op_x, op_y, n2_x, n2_y, op_sc;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
-  size_t tc_bx, tc_by;  // key tiles of the tensor-core tiled sweeps
+  size_t tc_bx, tc_by, tc_hbx, tc_hby;  // key tiles of the tensor-core tiled sweeps and their Hbar
   size_t sort_tmp_bytes, total;
 };
 
@@ -174,6 +174,8 @@ WsLayout ws_layout(const uot_problem& p) {
     if (tc3_fits(p.n, p.m)) {
       L.tc_bx = take(sizeof(float) * tc3_operand_floats(p.n));
       L.tc_by = take(sizeof(float) * tc3_operand_floats(p.m));
+      L.tc_hbx = take(sizeof(float) * ((p.n + kTileKeys - 1) / kTileKeys));
+      L.tc_hby = take(sizeof(float) * ((p.m + kTileKeys - 1) / kTileKeys));
     }
   }
   L.total = off;
@@ -194,7 +196,7 @@ struct Ctx {
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
   bool tiled;
   bool tc3;  // the solver's tiled half-steps run on the tensor cores (ordering != 3)
-  float *tc_bx, *tc_by;  // their key tiles
+  float *tc_bx, *tc_by, *tc_hbx, *tc_hby;  // their key tiles and tile maxima Hbar
   const float *px, *py, *pa, *pb;
   int *perm_x, *perm_y;
   float4 *cen_x, *cen_y;
@@ -250,7 +252,7 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
   c->tc3 = c->tiled && prob->ordering != 3 && tc3_fits(prob->n, prob->m);
-  c->tc_bx = c->tc_by = nullptr;
+  c->tc_bx = c->tc_by = c->tc_hbx = c->tc_hby = nullptr;
   c->px = prob->x; c->py = prob->y; c->pa = prob->a; c->pb = prob->b;
   c->perm_x = c->perm_y = nullptr;
   c->cen_x = c->cen_y = nullptr;
@@ -278,6 +280,8 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
     if (c->tc3) {
       c->tc_bx = reinterpret_cast<float*>(b + L.tc_bx);
       c->tc_by = reinterpret_cast<float*>(b + L.tc_by);
+      c->tc_hbx = reinterpret_cast<float*>(b + L.tc_hbx);
+      c->tc_hby = reinterpret_cast<float*>(b + L.tc_hby);
     }
   }
   return UOT_OK;
@@ -361,7 +365,7 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       epi->key_shift = shift;
       *fused = true;
       UOT_CUDA(launch_tc3_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, axis == 0 ? c.tc_by : c.tc_bx,
-                                c.s, part, g, *epi, c.st));
+                                axis == 0 ? c.tc_hby : c.tc_hbx, c.s, part, g, *epi, c.st));
     } else if (c.tiled && !moments) {
       SweepGeom g = tile_geom(q.n, k.n, p.dim);
       *splits = g.splits;
@@ -379,7 +383,7 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       *splits = g.splits;
       UOT_CUDA(launch_umma_sweep(axis == 0 ? c.op_x : c.op_y, axis == 0 ? c.n2_x : c.n2_y, q.n,
                                  axis == 0 ? c.op_y : c.op_x, axis == 0 ? c.n2_y : c.n2_x, k.n, p.dim, k.l2w, pot,
-                                 shift, c.s, c.op_sc, part, g, c.st));
+                                 shift, c.s, c.op_sc, part, g, &c.state->status, c.st));
     } else if (mma_path(p)) {
       // gradient sweep with moments: dC/dx = 2 (x - y)
       SweepGeom g = flash_geom(q.n, k.n);
@@ -483,8 +487,8 @@ uot_status loop_prologue(Loop& L) {
   if (c.tc3 && !L.small) {
     // key operands of the tensor-core half-steps: coordinates for the whole solve, H of the
     // initial f (the g side's H comes from the first g half-step's epilogue)
-    UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, true, c.st));
-    UOT_CUDA(launch_tc3_keys(c.ys, p.m, p.dim, c.cen_y, c.l2_b, nullptr, c.s, c.tc_by, true, c.st));
+    UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, c.tc_hbx, true, c.st));
+    UOT_CUDA(launch_tc3_keys(c.ys, p.m, p.dim, c.cen_y, c.l2_b, nullptr, c.s, c.tc_by, c.tc_hby, true, c.st));
   }
   return UOT_OK;
 }
@@ -510,7 +514,7 @@ uot_status g_half(Loop& L, int t, const LoopCtl& lc) {
   e.resid_hist = L.opt.residual_history; e.hist_index = t;
   e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
   e.lse_buf = L.lse_g; e.lse_policy = L.opt.lse_reference;
-  if (c.tc3) { e.tc_b_out = c.tc_by; e.tc_cen_out = c.cen_y; e.tc_pts_out = c.ys; }
+  if (c.tc3) { e.tc_b_out = c.tc_by; e.tc_hb_out = c.tc_hby; e.tc_cen_out = c.cen_y; e.tc_pts_out = c.ys; }
   e.loop_ctl = lc.ctl;
   e.loop_max_iter = L.opt.max_iter; e.loop_check_every = L.opt.check_every; e.loop_tol = L.opt.tol;
   e.cond_while = lc.cond_while; e.cond_if = lc.cond_if;
@@ -536,7 +540,7 @@ uot_status f_half(Loop& L, int t, const LoopCtl& lc) {
   ef.resid_hist = nullptr; ef.hist_index = t;
   ef.slot_in = so; ef.slot_out = so; ef.state = c.state; ef.part = c.part_r; ef.blk = c.blk;
   ef.lse_buf = L.lse_f; ef.lse_policy = L.opt.lse_reference;
-  if (c.tc3) { ef.tc_b_out = c.tc_bx; ef.tc_cen_out = c.cen_x; ef.tc_pts_out = c.xs; }
+  if (c.tc3) { ef.tc_b_out = c.tc_bx; ef.tc_hb_out = c.tc_hbx; ef.tc_cen_out = c.cen_x; ef.tc_pts_out = c.xs; }
   ef.loop_ctl = lc.ctl;
   uot_status v = sweep(c, 0, L.gbuf[so], L.ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
   if (v != UOT_OK) return v;
@@ -615,7 +619,7 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
         if (variant == 1) UOT_CUDA(launch_ti_init(L.fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st, t & 1));
         // the extrapolated iterate replaces f: the x side's key constants follow it
         if (c.tc3)
-          UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, false, c.st));
+          UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, c.tc_hbx, false, c.st));
       }
     }
   }
@@ -1009,6 +1013,17 @@ uot_status emit_solve(Loop& L, cudaStream_t s, cudaStream_t b1, cudaStream_t b2,
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+std::atomic<long long> g_wait_limit{0};  // 0: kWaitPolls; < 0: no polls
+}  // namespace
+
+long long wait_limit() {
+  const long long v = g_wait_limit.load(std::memory_order_relaxed);
+  return v > 0 ? v : (v < 0 ? 0 : kWaitPolls);
+}
+
+void set_wait_limit(long long polls) { g_wait_limit.store(polls, std::memory_order_relaxed); }
+
 void set_last_error(const char* msg) { g_last_error = msg; }
 
 int device_sm_count() {
@@ -1094,8 +1109,8 @@ uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, 
   e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk;
   if (c.tc3) {
     // the tensor-core sweep reads the key side's operand: coordinates and H of pot
-    if (axis == 0) UOT_CUDA(launch_tc3_keys(c.ys, c.p.m, c.p.dim, c.cen_y, c.l2_b, pot_i, c.s, c.tc_by, true, c.st));
-    else UOT_CUDA(launch_tc3_keys(c.xs, c.p.n, c.p.dim, c.cen_x, c.l2_a, pot_i, c.s, c.tc_bx, true, c.st));
+    if (axis == 0) UOT_CUDA(launch_tc3_keys(c.ys, c.p.m, c.p.dim, c.cen_y, c.l2_b, pot_i, c.s, c.tc_by, c.tc_hby, true, c.st));
+    else UOT_CUDA(launch_tc3_keys(c.xs, c.p.n, c.p.dim, c.cen_x, c.l2_a, pot_i, c.s, c.tc_bx, c.tc_hbx, true, c.st));
   }
   v = sweep(c, axis, pot_i, nullptr, false, &splits, &e, &fused);
   if (v != UOT_OK) return v;
@@ -1317,6 +1332,8 @@ uot_status uot_plan_solve(uot_plan* plan, float* f, float* g, uot_result* res_de
   UOT_CUDA(cudaGraphLaunch(exec, st));
   return UOT_OK;
 }
+
+void uot_test_set_wait_limit(int64_t polls) { set_wait_limit((long long)polls); }
 
 const char* uot_last_error(void) { return g_last_error.c_str(); }
 

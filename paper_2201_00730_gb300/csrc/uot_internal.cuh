@@ -81,10 +81,16 @@ struct SweepGeom {
 };
 
 int device_sm_count();
+// Polls allowed to a main-loop mbarrier wait of the tensor-core sweeps before it
+// gives up (default kWaitPolls; lowered only by the test hook uot_test_set_wait_limit).
+constexpr long long kWaitPolls = 1LL << 24;
+long long wait_limit();
 // Counts one kernel launch (process-wide counter read by uot_kernel_launches).
 void note_launch();
 // Sets the calling thread's message returned by uot_last_error().
 void set_last_error(const char* msg);
+// Test hook behind uot_test_set_wait_limit (0 restores kWaitPolls).
+void set_wait_limit(long long polls);
 SweepGeom points_geom(int nq, int nk, int dim, bool moments);
 SweepGeom dense_row_geom(int nrows, int ncols);
 SweepGeom dense_col_geom(int nrows, int ncols);
@@ -156,15 +162,16 @@ cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4
 // tc3_operand_floats(n) floats in all (16-byte aligned; per 128-point tile the
 // operand rows and a header with the tile's centre and largest key constant):
 // launch_tc3_keys builds them (full: coordinate parts too) from a potential
-// (nullable: 0); afterwards the epilogue of every half-step that writes that
-// side's potential keeps their H parts current (epi.tc_* fields).
+// (nullable: 0), with the tiles' Hbar also in hb (one float per tile);
+// afterwards the epilogue of every half-step that writes that side's potential
+// keeps their H parts and Hbar current (epi.tc_* fields).
 bool tc3_fits(int nq, int nk);
 size_t tc3_operand_floats(int n);
 SweepGeom tc3_geom(int nq, int nk);
 cudaError_t launch_tc3_keys(const float* pts, int n, int dim, const float4* cen, const float* l2w, const float* pot,
-                            double s, float* Bop, bool full, cudaStream_t st);
+                            double s, float* Bop, float* hb, bool full, cudaStream_t st);
 cudaError_t launch_tc3_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
-                             const float* pot_k, const float* Bk, double s, float* part,
+                             const float* pot_k, const float* Bk, const float* hbk, double s, float* part,
                              const SweepGeom& g, const struct EpiParams& epi, cudaStream_t st);
 // Tensor-core sweep with moments (dim >= 32, p = 2): partials [splits][2 + dim][nq]
 // (max, sum of mult_j 2^(t - max), momscale * the moments of (x_i - y_j)).
@@ -187,9 +194,11 @@ cudaError_t launch_umma_scale(const float* x, int n, const float* y, int m, int 
 cudaError_t launch_umma_operand(const float* pts, int n, int dim, const float* center, const int* maxbits,
                                 void* op, float* norm2, cudaStream_t st);
 SweepGeom umma_geom(int nq, int nk);
+// A main-loop wait that gives up (bounded, wait_limit()) sets kStatusTimeout in
+// *status (nullable) and NaN partials; copies and MMAs in flight land first.
 cudaError_t launch_umma_sweep(const void* opq, const float* nq2, int nq, const void* opk, const float* nk2, int nk,
                               int dim, const float* l2w, const float* pot, const double* shift, double s,
-                              const int* maxbits, float* part, const SweepGeom& g, cudaStream_t st);
+                              const int* maxbits, float* part, const SweepGeom& g, int* status, cudaStream_t st);
 // Dense cost: axis 0 = rows of C are queries, axis 1 = columns of C are queries.
 cudaError_t launch_dense_sweep(int axis, const float* C, int n, int m, const float* l2w_k,
                                const float* pot_k, const double* shift_k, double s, float* part,
@@ -245,6 +254,7 @@ struct EpiParams {
   // H parts and Hbar the epilogue rewrites from the new potential, with the
   // side's tile centres and points (Morton order)
   float* tc_b_out;
+  float* tc_hb_out;
   const float4* tc_cen_out;
   const float* tc_pts_out;
   // device-driven iteration (a solve captured in a CUDA graph, the loop a

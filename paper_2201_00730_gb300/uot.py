@@ -65,6 +65,12 @@ class FW1DBatch(C.Structure):
                 ("x", C.c_void_p), ("a", C.c_void_p), ("y", C.c_void_p), ("b", C.c_void_p)]
 
 
+class MMOT1DBatch(C.Structure):
+    _fields_ = [("count", C.c_int32), ("n_iter", C.c_int32), ("K", C.c_int32), ("reserved", C.c_int32),
+                ("n", C.c_void_p), ("off", C.c_void_p), ("rho", C.c_void_p), ("omega", C.c_void_p),
+                ("x", C.c_void_p), ("alpha", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -113,6 +119,15 @@ def lib() -> C.CDLL:
         L.uot_plan_workspace_size.restype = S
         L.uot_plan_solve.argtypes = [V, V, V, V, V, S, V]
         L.uot_plan_solve.restype = C.c_int
+        L.uot_test_set_wait_limit.argtypes = [C.c_int64]
+        L.uot_test_set_wait_limit.restype = None
+        L.uot_mmot1d_workspace_size.argtypes = [C.POINTER(MMOT1DBatch)]
+        L.uot_mmot1d_workspace_size.restype = S
+        L.uot_mmot1d_barycenter_size.argtypes = [C.POINTER(MMOT1DBatch)]
+        L.uot_mmot1d_barycenter_size.restype = S
+        L.uot_mmot1d_batched.argtypes = [C.POINTER(MMOT1DBatch), V, V, V, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int32), V, S, V]
+        L.uot_mmot1d_batched.restype = C.c_int
         L.uot_kernel_launches.argtypes = []
         L.uot_kernel_launches.restype = C.c_uint64
         L.uot_profile_begin.argtypes = []
@@ -584,6 +599,60 @@ def fw1d_batched(problems, n_iter: int, p: float = 2.0, device="cuda:0", check: 
     fs = [F[xo[k]:xo[k] + n[k]] for k in range(cnt)]
     gs = [G[yo[k]:yo[k] + m[k]] for k in range(cnt)]
     return FW1DOut(fs, gs, list(stat), code)
+
+
+@dataclass
+class MMOT1DOut:
+    f: list            # per problem, per measure: translated potentials (device FP64 views)
+    bary_x: list       # per problem: barycenter points (device FP64 views)
+    bary_w: list       # per problem: barycenter weights
+    status: list
+    code: int
+
+
+def mmot1d_batched(problems, n_iter: int, device="cuda:0", check: bool = True) -> MMOT1DOut:
+    """1-D unbalanced multi-marginal OT and barycenters (Sec. 5) by Frank-Wolfe, many problems in one call.
+
+    `problems`: sequence of objects with lists xs (K ascending 1-D arrays), alphas (K weight arrays),
+    omega (K barycentric weights summing to one) and a float rho; every problem has the same K.
+    Inputs are packed into device arrays here (marshalling only).
+    """
+    import numpy as np
+    dev = torch.device(device)
+    cnt = len(problems)
+    K = len(problems[0].xs)
+    n = np.array([[np.asarray(xk).size for xk in q.xs] for q in problems], dtype=np.int32).reshape(-1)
+    off = np.concatenate([[0], np.cumsum(n.astype(np.int64))[:-1]]).astype(np.int64)
+    rho = np.array([q.rho for q in problems], dtype=np.float64)
+    om = np.array([list(q.omega) for q in problems], dtype=np.float64).reshape(-1)
+    cat = lambda vs: torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [np.asarray(v, dtype=np.float32).ravel() for v in vs]))).to(dev)
+    X = cat([xk for q in problems for xk in q.xs])
+    A = cat([ak for q in problems for ak in q.alphas])
+    host = [n, off, rho, om]
+    bt = MMOT1DBatch(cnt, int(n_iter), K, 0, *[h.ctypes.data for h in host], X.data_ptr(), A.data_ptr())
+    nbytes = lib().uot_mmot1d_workspace_size(C.byref(bt))
+    if nbytes == 0:
+        raise UOTError(1, lib().uot_last_error().decode())
+    nb = int(lib().uot_mmot1d_barycenter_size(C.byref(bt)))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    F = torch.empty(X.numel(), dtype=torch.float64, device=dev)
+    BX = torch.zeros(nb, dtype=torch.float64, device=dev)
+    BW = torch.zeros(nb, dtype=torch.float64, device=dev)
+    blen = (C.c_int32 * cnt)()
+    stat = (C.c_int32 * cnt)()
+    code = lib().uot_mmot1d_batched(C.byref(bt), _ptr(F), _ptr(BX), _ptr(BW), blen, stat, _ptr(ws), ws.numel(),
+                                    _stream())
+    if check:
+        _check(code)
+    fs, bxs, bws = [], [], []
+    bo = 0
+    for p in range(cnt):
+        fs.append([F[off[p * K + k]:off[p * K + k] + n[p * K + k]] for k in range(K)])
+        bxs.append(BX[bo:bo + blen[p]])
+        bws.append(BW[bo:bo + blen[p]])
+        bo += int(n[p * K:(p + 1) * K].sum())
+    return MMOT1DOut(fs, bxs, bws, list(stat), code)
 
 
 def version() -> str:

@@ -194,3 +194,23 @@ def dense_cost_f32_device(x: np.ndarray, y: np.ndarray, device, rows_per_block: 
             acc += d * d
         out[i0:i0 + rows_per_block] = acc.to(torch.float32)
     return out
+
+
+def config_mmot1d(count: int = 64, K: int = 8, n: int = 200, seed: int = 1007, rho: float = 1.0, ragged: bool = False):
+    """`count` independent 1-D multi-marginal problems of K measures, the shape of the paper's
+    barycenter experiment (Sec. 5: K = 8 one-dimensional Gaussian mixtures): measure k has n points
+    (with ragged, between n/2 and n) sorted from a two-component Gaussian mixture whose centres move
+    with k, Exp(1) weights rescaled to a mass in [0.5, 2], uniform barycentric weights 1/K, rho."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        xs, als = [], []
+        for k in range(K):
+            nk = int(rng.integers(max(1, n // 2), n + 1)) if ragged else n
+            c = rng.choice([-1.0 + 0.25 * k, 0.5 + 0.1 * k], size=nk)
+            xs.append(np.sort(c + 0.15 * rng.standard_normal(nk)).astype(np.float32))
+            w = rng.exponential(1.0, nk)
+            als.append((w / w.sum() * rng.uniform(0.5, 2.0)).astype(np.float32))
+        out.append(SimpleNamespace(xs=xs, alphas=als, omega=[1.0 / K] * K, rho=float(rho)))
+    return out

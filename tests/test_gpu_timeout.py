@@ -1,0 +1,60 @@
+"""Failure detection on the GPU without a fault: every mbarrier wait of the tensor-core
+sweeps is bounded, and a wait that gives up must come back as UOT_ERR_TIMEOUT with the
+CUDA context still usable.  The test hook uot_test_set_wait_limit(-1) lets the main-loop
+waits poll no time at all, so that the first of them gives up; the waits that drain
+copies and MMAs in flight keep their full limit."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import uot as O
+from paper_2201_00730_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def U():
+    from paper_2201_00730_gb300 import build, uot
+    build.build()
+    return uot
+
+
+def spec_of(U, p, ordering=0):
+    dev = torch.device("cuda:0")
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+    return U.Spec(t(p.a), t(p.b), p.eps, p.rho1, p.rho2, x=t(p.x), y=t(p.y), ordering=ordering)
+
+
+CASES = {
+    # 3-D clouds on the tensor-core tiled half-steps
+    "tiled_tc": lambda: W.random_problem(4000, 3500, 3, seed=31, eps=2e-2),
+    # D = 48 clouds on the tcgen05 cross-term sweep
+    "d48": lambda: W.random_problem(900, 700, 48, seed=32, eps=5e-2, rho1=0.5, rho2=0.5),
+}
+
+
+@pytest.mark.parametrize("kind", list(CASES))
+def test_wait_that_gives_up_reports_timeout_and_context_survives(U, kind):
+    p = CASES[kind]()
+    if kind == "d48":
+        sd = np.sqrt(1.0 / 96.0)
+        rng = np.random.default_rng(5)
+        p.x = (sd * rng.standard_normal(p.x.shape)).astype(np.float32)
+        p.y = (sd * rng.standard_normal(p.y.shape)).astype(np.float32)
+    spec = spec_of(U, p, ordering=1 if kind == "tiled_tc" else 0)
+    L = U.lib()
+    L.uot_test_set_wait_limit(-1)
+    try:
+        with pytest.raises(U.UOTError) as ei:
+            U.solve(spec, "ti", max_iter=4, tol=1e-12, check_every=1)
+        assert ei.value.status == 5, ei.value  # UOT_ERR_TIMEOUT
+    finally:
+        L.uot_test_set_wait_limit(0)
+    torch.cuda.synchronize()  # the context is intact: nothing faulted
+    # the same problem solves normally afterwards and matches the oracle
+    T = 6
+    r = U.solve(spec, "ti", max_iter=T, tol=0.0)
+    ref = O.ti_sinkhorn(O.cost_matrix(p.x, p.y), p.a, p.b, p.eps, p.rho1, p.rho2, T)
+    err = (r.f.double().cpu() - ref.f).abs()
+    assert bool((err <= 1e-4 * p.eps + 2 * 2.0 ** -23 * ref.f.abs()).all()), err.max().item()
