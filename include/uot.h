@@ -74,9 +74,7 @@ typedef struct {
   int32_t cost_kind;   /* uot_cost_kind                                               */
   float p;             /* exponent p >= 1 of the points cost; p == 2 is the fast path */
   int32_t ordering;    /* points cost with dim <= 3 and p == 2 only: 0 = automatic, 1 = always put  */
-                       /* both clouds in Morton order and use the tiled sweeps (the solver's half-  */
-                       /* steps form each cost entry's exponent on the tensor cores, tcgen05), 2 =  */
-                       /* never, 3 = Morton order with every sweep on the CUDA cores.               */
+                       /* both clouds in Morton order and use the tiled sweeps, 2 = never.          */
                        /* Results agree within rounding; ordering costs a few hundred us per call   */
                        /* and pays off from about 1.5e9 cost entries per call, the automatic        */
                        /* threshold.  With 0, a solve of a problem with N M <= 2^20 whose clouds    */

@@ -64,7 +64,7 @@ uot_status validate(const uot_problem* p) {
   if (!finite_pos(p->eps) || !finite_pos(p->rho1) || !finite_pos(p->rho2))
     return fail(UOT_ERR_INVALID_ARG, "eps, rho1, rho2 must be finite and > 0");
   if (!p->a || !p->b) return fail(UOT_ERR_INVALID_ARG, "weights a and b must be device pointers");
-  if (p->ordering < 0 || p->ordering > 3) return fail(UOT_ERR_INVALID_ARG, "ordering must be 0, 1, 2 or 3");
+  if (p->ordering < 0 || p->ordering > 2) return fail(UOT_ERR_INVALID_ARG, "ordering must be 0, 1 or 2");
   if (p->cost_kind == UOT_COST_POINTS) {
     if (p->dim < 1 || p->dim > 64) return fail(UOT_ERR_INVALID_ARG, "dim must be in 1..64 (got %d)", p->dim);
     if (!(p->p >= 1.0f) || !isfinite(p->p)) return fail(UOT_ERR_INVALID_ARG, "cost exponent p must be >= 1");
@@ -96,10 +96,6 @@ PartSizes part_sizes(const uot_problem& p) {
     if (tiled_path(p)) {
       upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
       upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
-      if (tc3_fits(p.n, p.m)) {
-        upd(ps.rows, (size_t)tc3_geom(p.n, p.m).splits * 2 * p.n);
-        upd(ps.cols, (size_t)tc3_geom(p.m, p.n).splits * 2 * p.m);
-      }
     }
     if (mma_path(p)) {
       upd(ps.rows, (size_t)umma_geom(p.n, p.m).splits * 2 * p.n);
@@ -121,7 +117,6 @@ struct WsLayout {
   size_t op_x, op_y, n2_x, n2_y, op_sc;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
-  size_t tc_bx, tc_by, tc_hbx, tc_hby;  // key tiles of the tensor-core tiled sweeps and their Hbar
   size_t sort_tmp_bytes, total;
 };
 
@@ -171,12 +166,6 @@ WsLayout ws_layout(const uot_problem& p) {
     L.idx_in = take(sizeof(int) * nmax);
     L.sort_tmp_bytes = sort_temp_bytes(nmax);
     L.sort_tmp = take(L.sort_tmp_bytes);
-    if (tc3_fits(p.n, p.m)) {
-      L.tc_bx = take(sizeof(float) * tc3_operand_floats(p.n));
-      L.tc_by = take(sizeof(float) * tc3_operand_floats(p.m));
-      L.tc_hbx = take(sizeof(float) * ((p.n + kTileKeys - 1) / kTileKeys));
-      L.tc_hby = take(sizeof(float) * ((p.m + kTileKeys - 1) / kTileKeys));
-    }
   }
   L.total = off;
   return L;
@@ -195,8 +184,6 @@ struct Ctx {
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
   bool tiled;
-  bool tc3;  // the solver's tiled half-steps run on the tensor cores (ordering != 3)
-  float *tc_bx, *tc_by, *tc_hbx, *tc_hby;  // their key tiles and tile maxima Hbar
   const float *px, *py, *pa, *pb;
   int *perm_x, *perm_y;
   float4 *cen_x, *cen_y;
@@ -210,7 +197,7 @@ struct Ctx {
 bool worth_ordering(const uot_problem& p, double sweeps) {
   if (!tiled_path(p) || p.ordering == 2) return false;
   if (p.ordering == 0 && small_path(p)) return false;  // the resident cluster solver needs no ordering
-  return p.ordering == 1 || p.ordering == 3 || (double)p.n * (double)p.m * sweeps > 1.5e9;
+  return p.ordering == 1 || (double)p.n * (double)p.m * sweeps > 1.5e9;
 }
 
 uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* stream, Ctx* c,
@@ -251,8 +238,6 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
   c->tiled = worth_ordering(*prob, sweeps);
-  c->tc3 = c->tiled && prob->ordering != 3 && tc3_fits(prob->n, prob->m);
-  c->tc_bx = c->tc_by = c->tc_hbx = c->tc_hby = nullptr;
   c->px = prob->x; c->py = prob->y; c->pa = prob->a; c->pb = prob->b;
   c->perm_x = c->perm_y = nullptr;
   c->cen_x = c->cen_y = nullptr;
@@ -277,12 +262,6 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
     c->osc.temp = b + L.sort_tmp;
     c->osc.temp_bytes = L.sort_tmp_bytes;
     c->px = c->xs; c->py = c->ys; c->pa = c->as; c->pb = c->bs;
-    if (c->tc3) {
-      c->tc_bx = reinterpret_cast<float*>(b + L.tc_bx);
-      c->tc_by = reinterpret_cast<float*>(b + L.tc_by);
-      c->tc_hbx = reinterpret_cast<float*>(b + L.tc_hbx);
-      c->tc_hby = reinterpret_cast<float*>(b + L.tc_hby);
-    }
   }
   return UOT_OK;
 }
@@ -358,15 +337,7 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
     SideDesc X{c.px, c.l2_a, c.ln_a, p.n}, Y{c.py, c.l2_b, c.ln_b, p.m};
     const SideDesc& q = axis == 0 ? X : Y;
     const SideDesc& k = axis == 0 ? Y : X;
-    if (c.tiled && !moments && epi && c.tc3) {
-      SweepGeom g = tc3_geom(q.n, k.n);
-      *splits = g.splits;
-      epi->nq = q.n; epi->splits = g.splits; epi->part = part; epi->rb_counter = c.rbc; epi->moments = 0;
-      epi->key_shift = shift;
-      *fused = true;
-      UOT_CUDA(launch_tc3_sweep(q, k, axis == 0 ? c.cen_y : c.cen_x, p.dim, pot, axis == 0 ? c.tc_by : c.tc_bx,
-                                axis == 0 ? c.tc_hby : c.tc_hbx, c.s, part, g, *epi, c.st));
-    } else if (c.tiled && !moments) {
+    if (c.tiled && !moments) {
       SweepGeom g = tile_geom(q.n, k.n, p.dim);
       *splits = g.splits;
       if (epi) {
@@ -484,12 +455,6 @@ uot_status loop_prologue(Loop& L) {
   else if (c.tiled) UOT_CUDA(launch_gather_vec(L.f, c.perm_x, p.n, L.fst, c.st));
   UOT_CUDA(cudaMemsetAsync(L.gbuf[0], 0, sizeof(float) * p.m, c.st));
   if (L.ti) UOT_CUDA(launch_ti_init(L.fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st));
-  if (c.tc3 && !L.small) {
-    // key operands of the tensor-core half-steps: coordinates for the whole solve, H of the
-    // initial f (the g side's H comes from the first g half-step's epilogue)
-    UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, c.tc_hbx, true, c.st));
-    UOT_CUDA(launch_tc3_keys(c.ys, p.m, p.dim, c.cen_y, c.l2_b, nullptr, c.s, c.tc_by, c.tc_hby, true, c.st));
-  }
   return UOT_OK;
 }
 
@@ -514,7 +479,6 @@ uot_status g_half(Loop& L, int t, const LoopCtl& lc) {
   e.resid_hist = L.opt.residual_history; e.hist_index = t;
   e.slot_in = si; e.slot_out = so; e.state = c.state; e.part = c.part_c; e.blk = c.blk;
   e.lse_buf = L.lse_g; e.lse_policy = L.opt.lse_reference;
-  if (c.tc3) { e.tc_b_out = c.tc_by; e.tc_hb_out = c.tc_hby; e.tc_cen_out = c.cen_y; e.tc_pts_out = c.ys; }
   e.loop_ctl = lc.ctl;
   e.loop_max_iter = L.opt.max_iter; e.loop_check_every = L.opt.check_every; e.loop_tol = L.opt.tol;
   e.cond_while = lc.cond_while; e.cond_if = lc.cond_if;
@@ -540,7 +504,6 @@ uot_status f_half(Loop& L, int t, const LoopCtl& lc) {
   ef.resid_hist = nullptr; ef.hist_index = t;
   ef.slot_in = so; ef.slot_out = so; ef.state = c.state; ef.part = c.part_r; ef.blk = c.blk;
   ef.lse_buf = L.lse_f; ef.lse_policy = L.opt.lse_reference;
-  if (c.tc3) { ef.tc_b_out = c.tc_bx; ef.tc_hb_out = c.tc_hbx; ef.tc_cen_out = c.cen_x; ef.tc_pts_out = c.xs; }
   ef.loop_ctl = lc.ctl;
   uot_status v = sweep(c, 0, L.gbuf[so], L.ti ? &c.state->slot[so].cg : nullptr, false, &splits, &ef, &fused);
   if (v != UOT_OK) return v;
@@ -617,9 +580,6 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
                                              variant == 2 ? sl : nullptr, &c.state->status, c.st));
         // H: the new fb is held in full (cf = 0); its Smin_a^rho1 for the next g half-step
         if (variant == 1) UOT_CUDA(launch_ti_init(L.fst, c.ln_a, p.n, p.rho1, c.state, c.blk, c.st, t & 1));
-        // the extrapolated iterate replaces f: the x side's key constants follow it
-        if (c.tc3)
-          UOT_CUDA(launch_tc3_keys(c.xs, p.n, p.dim, c.cen_x, c.l2_a, L.fst, c.s, c.tc_bx, c.tc_hbx, false, c.st));
       }
     }
   }
@@ -1107,11 +1067,6 @@ uot_status uot_softmin(const uot_problem* prob, int32_t axis, const float* pot, 
   e.out_is_f = axis == 0; e.lnw_o = axis == 0 ? c.ln_a : c.ln_b; e.out = out; e.state = c.state;
   e.l2w_o = axis == 0 ? c.l2_a : c.l2_b; e.l2lo_o = axis == 0 ? c.lo_a : c.lo_b;
   e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk;
-  if (c.tc3) {
-    // the tensor-core sweep reads the key side's operand: coordinates and H of pot
-    if (axis == 0) UOT_CUDA(launch_tc3_keys(c.ys, c.p.m, c.p.dim, c.cen_y, c.l2_b, pot_i, c.s, c.tc_by, c.tc_hby, true, c.st));
-    else UOT_CUDA(launch_tc3_keys(c.xs, c.p.n, c.p.dim, c.cen_x, c.l2_a, pot_i, c.s, c.tc_bx, c.tc_hbx, true, c.st));
-  }
   v = sweep(c, axis, pot_i, nullptr, false, &splits, &e, &fused);
   if (v != UOT_OK) return v;
   e.splits = splits;

@@ -157,22 +157,6 @@ SweepGeom tile_geom(int nq, int nk, int dim);
 cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
                               const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
                               const struct EpiParams* epi, cudaStream_t st);
-// Tensor-core tiled half-step sweep (sorted clouds, dim <= 3, p = 2) with the
-// fused epilogue (sweep_tc3.cu).  Each side has key tiles of
-// tc3_operand_floats(n) floats in all (16-byte aligned; per 128-point tile the
-// operand rows and a header with the tile's centre and largest key constant):
-// launch_tc3_keys builds them (full: coordinate parts too) from a potential
-// (nullable: 0), with the tiles' Hbar also in hb (one float per tile);
-// afterwards the epilogue of every half-step that writes that side's potential
-// keeps their H parts and Hbar current (epi.tc_* fields).
-bool tc3_fits(int nq, int nk);
-size_t tc3_operand_floats(int n);
-SweepGeom tc3_geom(int nq, int nk);
-cudaError_t launch_tc3_keys(const float* pts, int n, int dim, const float4* cen, const float* l2w, const float* pot,
-                            double s, float* Bop, float* hb, bool full, cudaStream_t st);
-cudaError_t launch_tc3_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
-                             const float* pot_k, const float* Bk, const float* hbk, double s, float* part,
-                             const SweepGeom& g, const struct EpiParams& epi, cudaStream_t st);
 // Tensor-core sweep with moments (dim >= 32, p = 2): partials [splits][2 + dim][nq]
 // (max, sum of mult_j 2^(t - max), momscale * the moments of (x_i - y_j)).
 // Forward gradient sweep: l2w, pot, shift of the keys, zrow = hk = mk = null,
@@ -250,13 +234,6 @@ struct EpiParams {
   int lse_policy;       // 0: reference after a small change, 2: whenever one is stored
   const float* l2w_o;   // TI: log2 weights of the output side as float pairs (hi, lo)
   const float* l2lo_o;
-  // tensor-core tiled sweeps (nullable): the output side's key tiles, whose
-  // H parts and Hbar the epilogue rewrites from the new potential, with the
-  // side's tile centres and points (Morton order)
-  float* tc_b_out;
-  float* tc_hb_out;
-  const float4* tc_cen_out;
-  const float* tc_pts_out;
   // device-driven iteration (a solve captured in a CUDA graph, the loop a
   // conditional while node): 1 = this f half-step advances state->loop_t; 2 =
   // this g half-step evaluates the stopping rule of the host driver at iterate

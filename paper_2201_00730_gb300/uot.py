@@ -180,7 +180,7 @@ class Spec:
     y: torch.Tensor | None = None
     C: torch.Tensor | None = None
     p: float = 2.0
-    ordering: int = 0   # 0 automatic, 1 Morton tiles (dim <= 3, p = 2; tensor-core half-steps), 2 never, 3 Morton tiles on CUDA cores
+    ordering: int = 0   # 0 automatic, 1 Morton tiles (dim <= 3, p = 2), 2 never
 
     def __post_init__(self):
         if self.C is None and (self.x is None or self.y is None):

@@ -39,8 +39,8 @@ def same(got, ref, eps):
 
 
 CASES = {
-    "tiled_tc": (lambda: W.random_problem(3000, 2600, 3, seed=5, eps=2e-2, rho1=0.7, rho2=2.0, mass_b=0.8), 1, False),
-    "tiled_cc": (lambda: W.random_problem(3000, 2600, 2, seed=6, eps=2e-2, rho1=0.7, rho2=2.0, mass_b=0.8), 3, False),
+    "tiled_3d": (lambda: W.random_problem(3000, 2600, 3, seed=5, eps=2e-2, rho1=0.7, rho2=2.0, mass_b=0.8), 1, False),
+    "tiled_2d": (lambda: W.random_problem(3000, 2600, 2, seed=6, eps=2e-2, rho1=0.7, rho2=2.0, mass_b=0.8), 1, False),
     "direct": (lambda: W.random_problem(1200, 900, 3, seed=7, eps=5e-2, rho1=0.5, rho2=1.5), 2, False),
     "small": (lambda: W.random_problem(300, 257, 1, seed=8, eps=1e-2, rho1=1.0, rho2=0.3), 0, False),
     "dense": (lambda: W.random_problem(700, 1029, 2, seed=9, eps=5e-2, rho1=2.0, rho2=0.4), 0, True),

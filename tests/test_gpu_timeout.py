@@ -1,5 +1,5 @@
 """Failure detection on the GPU without a fault: every mbarrier wait of the tensor-core
-sweeps is bounded, and a wait that gives up must come back as UOT_ERR_TIMEOUT with the
+sweep (dim >= 32) is bounded, and a wait that gives up must come back as UOT_ERR_TIMEOUT with the
 CUDA context still usable.  The test hook uot_test_set_wait_limit(-1) lets the main-loop
 waits poll no time at all, so that the first of them gives up; the waits that drain
 copies and MMAs in flight keep their full limit."""
@@ -27,22 +27,21 @@ def spec_of(U, p, ordering=0):
 
 
 CASES = {
-    # 3-D clouds on the tensor-core tiled half-steps
-    "tiled_tc": lambda: W.random_problem(4000, 3500, 3, seed=31, eps=2e-2),
-    # D = 48 clouds on the tcgen05 cross-term sweep
+    # clouds on the tcgen05 cross-term sweep: one K block short of full, and two full ones
     "d48": lambda: W.random_problem(900, 700, 48, seed=32, eps=5e-2, rho1=0.5, rho2=0.5),
+    "d64": lambda: W.random_problem(1000, 777, 64, seed=33, eps=5e-2, rho1=0.5, rho2=0.5),
 }
 
 
 @pytest.mark.parametrize("kind", list(CASES))
 def test_wait_that_gives_up_reports_timeout_and_context_survives(U, kind):
     p = CASES[kind]()
-    if kind == "d48":
-        sd = np.sqrt(1.0 / 96.0)
-        rng = np.random.default_rng(5)
-        p.x = (sd * rng.standard_normal(p.x.shape)).astype(np.float32)
-        p.y = (sd * rng.standard_normal(p.y.shape)).astype(np.float32)
-    spec = spec_of(U, p, ordering=1 if kind == "tiled_tc" else 0)
+    # unit expected squared distance, as the D = 64 workloads
+    sd = np.sqrt(1.0 / (2.0 * p.x.shape[1]))
+    rng = np.random.default_rng(5)
+    p.x = (sd * rng.standard_normal(p.x.shape)).astype(np.float32)
+    p.y = (sd * rng.standard_normal(p.y.shape)).astype(np.float32)
+    spec = spec_of(U, p)
     L = U.lib()
     L.uot_test_set_wait_limit(-1)
     try:
