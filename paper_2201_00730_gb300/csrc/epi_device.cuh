@@ -25,6 +25,7 @@
 #include <climits>
 
 #include "ffloat.cuh"
+#include "sweep_common.cuh"
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -38,14 +39,15 @@ __device__ __forceinline__ float ex2f(float x) {
 
 // Merge of the key-chunk partials of R query rows at once (all loads of a group
 // of 8 chunks issued before any use): per row the pair (M, log2 S) with
-// log-sum-exp = M + log2 S in log2 units.
+// log-sum-exp = M + log2 S in log2 units.  The chunk sums are added with
+// Neumaier's compensation (the compensation rescaled with the sum).
 template <int R>
 __device__ __forceinline__ void merge_rows(const float* part, int CH, int nq, int splits, const int (&idx)[R],
                                            float (&Mo)[R], float (&Lo)[R]) {
   const size_t stride = (size_t)CH * nq;
-  float M[R], S[R];
+  float M[R], S[R], C[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) { M[r] = kInitMax; S[r] = 0.f; }
+  for (int r = 0; r < R; ++r) { M[r] = kInitMax; S[r] = 0.f; C[r] = 0.f; }
   for (int k0 = 0; k0 < splits; k0 += 8) {
     float mv[R][8], sv[R][8];
 #pragma unroll
@@ -68,15 +70,17 @@ __device__ __forceinline__ void merge_rows(const float* part, int CH, int nq, in
       float cm = M[r];
 #pragma unroll
       for (int u = 0; u < 8; ++u) cm = fmaxf(cm, mv[r][u]);
-      float a = S[r] * ex2f(M[r] - cm);
+      const float so = ex2f(M[r] - cm);
+      float a = S[r] * so, c = C[r] * so;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a = fmaf(sv[r][u], ex2f(mv[r][u] - cm), a);
+      for (int u = 0; u < 8; ++u) simd::neu_add(a, c, sv[r][u] * ex2f(mv[r][u] - cm));
       S[r] = a;
+      C[r] = c;
       M[r] = cm;
     }
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r) { Mo[r] = M[r]; Lo[r] = log2f(S[r]); }
+  for (int r = 0; r < R; ++r) { Mo[r] = M[r]; Lo[r] = log2f(S[r] + C[r]); }
 }
 
 // The same when every chunk's partial was taken against the same reference
@@ -87,9 +91,9 @@ template <int R>
 __device__ __forceinline__ void merge_rows_ref(const float* part, int CH, int nq, int splits, const int (&idx)[R],
                                                const float (&ref)[R], float (&Mo)[R], float (&Lo)[R]) {
   const size_t stride = (size_t)CH * nq;
-  float S[R];
+  float S[R], C[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) S[r] = 0.f;
+  for (int r = 0; r < R; ++r) { S[r] = 0.f; C[r] = 0.f; }
   for (int k0 = 0; k0 < splits; k0 += 8) {
     float sv[R][8];
 #pragma unroll
@@ -102,14 +106,12 @@ __device__ __forceinline__ void merge_rows_ref(const float* part, int CH, int nq
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float a = S[r];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a += sv[r][u];
-      S[r] = a;
+      for (int u = 0; u < 8; ++u) simd::neu_add(S[r], C[r], sv[r][u]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r) { Mo[r] = ref[r]; Lo[r] = log2f(S[r]); }
+  for (int r = 0; r < R; ++r) { Mo[r] = ref[r]; Lo[r] = log2f(S[r] + C[r]); }
 }
 
 // Per-launch constants of the half-step as float pairs, made once per block

@@ -46,6 +46,13 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
   return d;
 }
 
+// Neumaier's compensated addition s + y (running sum s, compensation c).
+__device__ __forceinline__ void neu_add(float& s, float& c, float y) {
+  const float t = s + y;
+  c += (fabsf(s) >= fabsf(y)) ? ((s - t) + y) : ((y - t) + s);
+  s = t;
+}
+
 // Softmin partial of one query row over all keys in the direct form, one warp
 // with a running max per lane; the lanes' pairs are combined on every lane.
 template <int D>

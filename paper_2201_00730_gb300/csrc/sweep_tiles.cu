@@ -15,8 +15,11 @@
 //
 // The inner loop runs on packed f32x2 instructions over key pairs (FFMA2 /
 // FADD2 / FMUL2: one issue slot for two lanes), one MUFU ex2 per entry, and a
-// running max per group of 8 keys.  Output: per (query, key chunk) partials
-// (max, sum of 2^(t - max)), merged by the combine kernel.
+// running max per group of 8 keys.  Each tile's sum (64 terms per lane) is
+// added to the row's running sum with Neumaier's compensated addition, so the
+// rounding of a chunk's sum does not grow with the number of its tiles.
+// Output: per (query, key chunk) partials (max, sum of 2^(t - max)), merged by
+// the epilogue (compensated as well).
 //
 // Fixed-reference mode (fused epilogue with a stored reference, decided per
 // launch on the device): inside a Sinkhorn solve a row's log-sum-exp moves
@@ -72,8 +75,7 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
   if constexpr (EPI) use_ref = e.lse_buf != nullptr && e.state->lse_ok[e.out_is_f] != 0;
 
   float xq[R][3];
-  float M[R], acc[R];
-  u64 ar[R];  // fixed-reference sums, M[r] holding the reference
+  float M[R], acc[R], cmp[R];  // running (max, sum, compensation); in fixed-reference mode M holds the reference
   const int ibase = blockIdx.x * (kThreads * R) + threadIdx.x;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -85,7 +87,7 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
       if (use_ref) M[r] = (i < nq) ? e.lse_buf[i] : 0.f;
     }
     acc[r] = 0.f;
-    ar[r] = pk(0.f, 0.f);
+    cmp[r] = 0.f;
   }
 
   for (int jt = j0; jt < j1; jt += kStageKeys) {
@@ -170,9 +172,15 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
               v = fma2(X[r][0], a[k].x, v);
               float w0, w1;
               upk(v, w0, w1);
-              ar[r] = add2(ar[r], pk(ex2f(w0), ex2f(w1)));
+              ac[r] = add2(ac[r], pk(ex2f(w0), ex2f(w1)));
             }
           }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float a0, a1;
+          upk(ac[r], a0, a1);
+          neu_add(acc[r], cmp[r], a0 + a1);
         }
         continue;
       }
@@ -216,7 +224,10 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
         upk(ac[r], a0, a1);
         const float MT = mu[r] + Rr[r];
         const float Mn = fmaxf(M[r], MT);
-        acc[r] = acc[r] * ex2f(M[r] - Mn) + (a0 + a1) * ex2f(MT - Mn);
+        const float so = ex2f(M[r] - Mn);
+        acc[r] *= so;
+        cmp[r] *= so;
+        neu_add(acc[r], cmp[r], (a0 + a1) * ex2f(MT - Mn));
         M[r] = Mn;
       }
     }
@@ -227,13 +238,7 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
     if (i < nq) {
       float* base = part + (size_t)split * 2 * nq;
       base[i] = M[r];
-      if (use_ref) {
-        float a0, a1;
-        upk(ar[r], a0, a1);
-        base[(size_t)nq + i] = a0 + a1;
-      } else {
-        base[(size_t)nq + i] = acc[r];
-      }
+      base[(size_t)nq + i] = acc[r] + cmp[r];
     }
   }
   if constexpr (EPI) {
