@@ -154,19 +154,20 @@ UOT_API uot_status uot_softmin(const uot_problem* prob, int32_t axis, const floa
  * Some callers have no device allocator at hand (a plain C host program
  * without a memory pool, a plug-in whose host framework forbids allocation
  * after start-up, a real-time loop that must not call cudaMalloc).  This entry
- * point takes no workspace: its scratch is a 16 MiB array compiled into the
+ * point takes no workspace: its scratch is a 32 MiB array compiled into the
  * library, reserved on every GPU that loads the library's device code and held
  * until the process exits.  The call itself performs no cudaMalloc, cudaFree
  * or other allocation.
- *  - Limit: problems whose uot_workspace_size() exceeds 16 MiB (with N = M
- *    and 3-D points on a 152-SM GB300 that happens above 51200 points per side)
- *    are rejected with UOT_ERR_UNSUPPORTED and a message; use uot_softmin for
- *    those.
+ *  - Limit: problems whose uot_workspace_size() exceeds 32 MiB are rejected
+ *    with UOT_ERR_UNSUPPORTED and a message; use uot_softmin for those.  With
+ *    N = M and 3-D points on a 152-SM GB300, 70000 points per side fit and
+ *    80000 do not (the partial buffers follow the launch shapes, so the size
+ *    does not grow smoothly with N).
  *  - The first call on each device looks up the scratch's device address with
  *    that device current; make that first call before any stream capture.
  *    Under lazy module loading (CUDA_MODULE_LOADING=LAZY, CUDA's default) that
  *    first call is also where the driver loads this library's device code and
- *    reserves the 16 MiB, so it is the one call that can fail with
+ *    reserves the 32 MiB, so it is the one call that can fail with
  *    UOT_ERR_CUDA for lack of device memory: callers that must not fail later
  *    (real-time loops) should make one warm-up call during start-up.  After
  *    cudaDeviceReset the look-up is redone on the next call (the address is
@@ -460,6 +461,46 @@ UOT_API size_t uot_mmot1d_barycenter_size(const uot_mmot1d_batch* batch);
  * else the first failing problem's status. */
 UOT_API uot_status uot_mmot1d_batched(const uot_mmot1d_batch* batch, double* f, double* bary_x, double* bary_w,
                                       int32_t* bary_len, int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Launch-shape tuning ------------------------------------------------------
+ *
+ * The launch shapes of the sweeps (rows per thread, key chunks, CTAs per SM) are
+ * picked by built-in rules unless a process-wide tuning table holds a value for
+ * the knob.  An entry is keyed by knob, point dimension (-1: any) and size
+ * bucket floor(log2(N M)) of the sweep (-1: any); the most specific entry
+ * present wins ((dim, bucket), (dim, any), (any, bucket), (any, any)).  Knobs
+ * and their allowed values (every one a shape the kernels are built for):
+ *   "tile.rows"          2, 4            rows per thread, tiled sweep (dim <= 3)
+ *   "tile.cta_cost"      5 10 15 25 40   per-CTA fixed cost (tenths of a 128-key
+ *                                        tile) in the tiled sweep's chunking
+ *   "points.rows"        1, 2, 4         rows per thread, direct sweep (dim <= 3)
+ *   "points.resident"    2, 3, 4, 6      CTAs per SM the direct sweep's chunking aims at
+ *   "dense.row_chunk"    2048 4096 8192  columns per CTA, dense row sweep
+ *   "dense.col_ctas"     2, 4, 8         CTAs per SM, dense column sweep
+ *   "batch.ctas_per_sm"  1, 2, 3, 4      persistent grid of uot_sinkhorn_batched
+ *                                        (capped at the kernel's occupancy)
+ * The entries only change launch shapes: results agree within rounding.
+ * Workspaces are sized for every allowed shape, so a change of the table never
+ * invalidates one (uot_workspace_size does not depend on it).  The autotuner of the
+ * Python package measures the candidates on the current device and writes a
+ * JSON cache, {"entries": [{"knob": K, "dim": D, "bucket": B, "value": V}, ...]};
+ * uot_plan_create loads the file named by the environment variable
+ * UOT_TUNE_FILE once per process.  All calls are thread-safe and touch no GPU. */
+
+/* Sets (value != 0) or clears (value == 0) one entry.  UOT_ERR_INVALID_ARG for an
+ * unknown knob, a value not allowed for it, dim outside -1..64 or bucket
+ * outside -1..126. */
+UOT_API uot_status uot_tune_set(const char* knob, int32_t dim, int32_t bucket, int64_t value);
+/* The entry that applies to a sweep of `entries` cost entries (<= 0: bucket
+ * any) in dimension dim, or 0 when the built-in rule applies. */
+UOT_API uot_status uot_tune_get(const char* knob, int32_t dim, int64_t entries, int64_t* value);
+/* floor(log2(entries)) (0 for entries <= 1): the size bucket of a sweep. */
+UOT_API int32_t uot_tune_bucket(int64_t entries);
+/* Removes every entry. */
+UOT_API uot_status uot_tune_clear(void);
+/* Adds the entries of a JSON tuning cache (layout above); nothing changes if
+ * the file cannot be read or holds an invalid entry (UOT_ERR_INVALID_ARG). */
+UOT_API uot_status uot_tune_load(const char* path);
 
 /* Message describing the last error of the calling thread ("" if none). */
 UOT_API const char* uot_last_error(void);

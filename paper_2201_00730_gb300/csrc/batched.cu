@@ -293,7 +293,9 @@ int batch_grid() {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_half, kThreads, 0) != cudaSuccess || occ < 1)
     occ = 4;
-  return device_sm_count() * occ;
+  // the persistent grid: occupancy-many CTAs per SM, or fewer when tuned so
+  const long long t = tune_value("batch.ctas_per_sm", -1, 0, occ);
+  return device_sm_count() * (int)(t < occ ? t : occ);
 }
 
 cudaError_t launch_batch_init(const BProb* probs, BState* st, const float* a, int count, int ti,

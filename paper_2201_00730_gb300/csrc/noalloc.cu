@@ -16,7 +16,7 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = size_t(16) << 20;  // 16 MiB per GPU
+constexpr size_t kScratchBytes = size_t(32) << 20;  // 32 MiB per GPU
 
 // The scratch: state, log weights, sweep partials and block partials of one
 // uot_softmin call.  Host code must not take its address directly (in host

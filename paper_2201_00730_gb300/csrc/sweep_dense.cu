@@ -194,12 +194,14 @@ k_dense_cols(const float* __restrict__ C, int n, int m, const float* __restrict_
 
 }  // namespace
 
-SweepGeom dense_row_geom(int nrows, int ncols) {
+SweepGeom dense_row_geom(int nrows, int ncols, bool tuned) {
   SweepGeom g{};
   g.threads = kThreads;
   g.rows = 1;
   g.row_blocks = (nrows + kRowsPerCta - 1) / kRowsPerCta;
-  int splits = (ncols + kRowChunk - 1) / kRowChunk;
+  // columns per CTA (at most kRowChunk: the shared copy of h)
+  const int chunk = tuned ? (int)tune_value("dense.row_chunk", -1, (long long)nrows * ncols, kRowChunk) : kRowChunk;
+  int splits = (ncols + chunk - 1) / chunk;
   int kps = (ncols + splits - 1) / splits;
   kps = (kps + 3) & ~3;  // keeps every chunk start 16-byte aligned
   g.keys_per_split = kps;
@@ -207,14 +209,15 @@ SweepGeom dense_row_geom(int nrows, int ncols) {
   return g;
 }
 
-SweepGeom dense_col_geom(int nrows, int ncols) {
+SweepGeom dense_col_geom(int nrows, int ncols, bool tuned) {
   SweepGeom g{};
   g.threads = kThreads;
   g.rows = 1;
   const int W = (ncols % 4 == 0) ? 4 : 1;
   const int cols_per_cta = kThreads * W;
   g.row_blocks = (ncols + cols_per_cta - 1) / cols_per_cta;
-  const long long target = (long long)device_sm_count() * 4;
+  const long long target =
+      (long long)device_sm_count() * (tuned ? tune_value("dense.col_ctas", -1, (long long)nrows * ncols, 4) : 4);
   long long splits = (target + g.row_blocks - 1) / g.row_blocks;
   const long long cap = (nrows + 63) / 64;  // at least 64 rows per slab
   if (splits > cap) splits = cap;

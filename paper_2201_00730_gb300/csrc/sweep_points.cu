@@ -287,21 +287,23 @@ cudaError_t launch_points_sweep(const SideDesc& q, const SideDesc& k, int dim, f
                  : dispatch<false>(q, k, dim, p, pot_k, shift_k, s, part, g, st);
 }
 
-SweepGeom points_geom(int nq, int nk, int dim, bool moments) {
+SweepGeom points_geom(int nq, int nk, int dim, bool moments, bool tuned) {
   SweepGeom g{};
   g.threads = kThreads;
   const bool fast = dim <= 3;
+  const long long entries = (long long)nq * nk;
   int R = 1;
   if (fast) {
     if (nq >= 64 * kThreads * 4) R = 4;
     else if (nq >= 16 * kThreads * 2) R = 2;
+    if (tuned) R = (int)tune_value("points.rows", dim, entries, R);
   }
   if (moments && dim == 3 && R > 2) R = 2;
   g.rows = R;
   const int rows_per_cta = kThreads * R;
   g.row_blocks = (nq + rows_per_cta - 1) / rows_per_cta;
   const int sms = device_sm_count();
-  const int resident = fast ? 3 : 2;
+  const int resident = (fast && tuned) ? (int)tune_value("points.resident", dim, entries, 3) : (fast ? 3 : 2);
   const long long target = (long long)sms * resident;
   // At least one wave of CTAs, and no CTA larger than ~16M entries.
   long long splits = (target + g.row_blocks - 1) / g.row_blocks;

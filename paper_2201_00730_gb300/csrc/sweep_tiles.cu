@@ -371,21 +371,26 @@ cudaError_t run(const SideDesc& q, const SideDesc& k, const float4* centers, con
 
 }  // namespace
 
-SweepGeom tile_geom(int nq, int nk, int dim) {
+SweepGeom tile_geom(int nq, int nk, int dim, bool tuned) {
   SweepGeom g{};
   g.threads = kThreads;
   const int sms = device_sm_count();
+  const long long entries = (long long)nq * nk;
   // 4 rows per thread (half the shared-memory loads per entry, 2 CTAs of 128
   // registers per SM) once there are a few row blocks; 2 rows (4 CTAs of 64
   // registers per SM) for small query sets, where more CTAs balance better
-  const int R = (nq >= 4096) ? 4 : 2;
+  int R = (nq >= 4096) ? 4 : 2;
+  if (tuned) R = (int)tune_value("tile.rows", dim, entries, R);
+  // row blocks index per-block counters and partial slots (kMaxBlocks of each)
+  if ((nq + kThreads * R - 1) / (kThreads * R) > kMaxBlocks) R = 4;
   g.rows = R;
   const int rows_per_cta = kThreads * R;
   g.row_blocks = (nq + rows_per_cta - 1) / rows_per_cta;
+  const double cta_cost = tuned ? 0.1 * (double)tune_value("tile.cta_cost", dim, entries, 15) : 1.5;
   const long long target = (long long)sms * occupancy_for(dim, R);
   const int max_tiles = (nk + kTileKeys - 1) / kTileKeys;
   // Pick the number of key chunks minimising (waves of CTAs) x (tiles per CTA +
-  // a fixed per-CTA cost of about 1.5 tiles: staging, merges, partial write).
+  // a fixed per-CTA cost, by default 1.5 tiles: staging, merges, partial write).
   // A chunk is a whole number of tiles.
   double best = 1e300;
   int best_k = 1;
@@ -395,7 +400,7 @@ SweepGeom tile_geom(int nq, int nk, int dim) {
     if (kk != k) continue;
     const long long ctas = (long long)g.row_blocks * kk;
     const long long waves = (ctas + target - 1) / target;
-    const double est = (double)waves * (tiles_per + 1.5);
+    const double est = (double)waves * (tiles_per + cta_cost);
     if (est < best * 0.999) { best = est; best_k = kk; }
   }
   const int tiles_per = (max_tiles + best_k - 1) / best_k;

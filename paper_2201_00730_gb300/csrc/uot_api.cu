@@ -85,17 +85,36 @@ struct PartSizes { size_t rows, cols; };
 PartSizes part_sizes(const uot_problem& p) {
   PartSizes ps{0, 0};
   auto upd = [](size_t& acc, size_t v) { if (v > acc) acc = v; };
+  // the largest partials over every shape the tuning table allows (and the
+  // built-in one), so that a workspace stays valid whatever the table holds later
   if (p.cost_kind == UOT_COST_POINTS) {
+    for (long long R : tune_allowed("points.rows")) {
+      for (long long res : tune_allowed("points.resident")) {
+        const TuneFix fx[2] = {{"points.rows", R}, {"points.resident", res}};
+        TuneScope scope(fx, 2);
+        for (int mom = 0; mom < 2; ++mom) {
+          const int ch = 2 + (mom ? p.dim : 0);
+          upd(ps.rows, (size_t)points_geom(p.n, p.m, p.dim, mom).splits * ch * p.n);
+          upd(ps.cols, (size_t)points_geom(p.m, p.n, p.dim, mom).splits * ch * p.m);
+        }
+      }
+    }
     for (int mom = 0; mom < 2; ++mom) {
       const int ch = 2 + (mom ? p.dim : 0);
-      SweepGeom gr = points_geom(p.n, p.m, p.dim, mom);
-      SweepGeom gc = points_geom(p.m, p.n, p.dim, mom);
-      upd(ps.rows, (size_t)gr.splits * ch * p.n);
-      upd(ps.cols, (size_t)gc.splits * ch * p.m);
+      upd(ps.rows, (size_t)points_geom(p.n, p.m, p.dim, mom, false).splits * ch * p.n);
+      upd(ps.cols, (size_t)points_geom(p.m, p.n, p.dim, mom, false).splits * ch * p.m);
     }
     if (tiled_path(p)) {
-      upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
-      upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
+      for (long long R : tune_allowed("tile.rows")) {
+        for (long long cost : tune_allowed("tile.cta_cost")) {
+          const TuneFix fx[2] = {{"tile.rows", R}, {"tile.cta_cost", cost}};
+          TuneScope scope(fx, 2);
+          upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
+          upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
+        }
+      }
+      upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim, false).splits * 2 * p.n);
+      upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim, false).splits * 2 * p.m);
     }
     if (mma_path(p)) {
       upd(ps.rows, (size_t)umma_geom(p.n, p.m).splits * 2 * p.n);
@@ -104,10 +123,18 @@ PartSizes part_sizes(const uot_problem& p) {
       upd(ps.cols, (size_t)flash_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
     }
   } else {
-    SweepGeom gr = dense_row_geom(p.n, p.m);
-    SweepGeom gc = dense_col_geom(p.n, p.m);
-    ps.rows = (size_t)gr.splits * 2 * p.n;
-    ps.cols = (size_t)gc.splits * 2 * p.m;
+    for (long long ch : tune_allowed("dense.row_chunk")) {
+      const TuneFix fx[1] = {{"dense.row_chunk", ch}};
+      TuneScope scope(fx, 1);
+      upd(ps.rows, (size_t)dense_row_geom(p.n, p.m).splits * 2 * p.n);
+    }
+    for (long long k : tune_allowed("dense.col_ctas")) {
+      const TuneFix fx[1] = {{"dense.col_ctas", k}};
+      TuneScope scope(fx, 1);
+      upd(ps.cols, (size_t)dense_col_geom(p.n, p.m).splits * 2 * p.m);
+    }
+    upd(ps.rows, (size_t)dense_row_geom(p.n, p.m, false).splits * 2 * p.n);
+    upd(ps.cols, (size_t)dense_col_geom(p.n, p.m, false).splits * 2 * p.m);
   }
   return ps;
 }
@@ -176,6 +203,7 @@ struct Ctx {
   DevState* state;
   double *ln_a, *ln_b, *blk;
   float *l2_a, *l2_b, *lo_a, *lo_b, *g_alt, *f_tmp, *g_tmp, *part_r, *part_c;  // lo_*: log2 w - l2_*
+  size_t cap_r, cap_c;  // floats in part_r, part_c
   unsigned int* rbc;  // per-row-block counters of the fused sweeps
   float* center;      // common centre of the clouds (tensor-core path)
   float *op_x, *op_y, *n2_x, *n2_y;  // tcgen05 operands and squared norms (dim >= 32)
@@ -223,6 +251,11 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->g_tmp = reinterpret_cast<float*>(b + L.g_tmp);
   c->part_r = reinterpret_cast<float*>(b + L.part_r);
   c->part_c = reinterpret_cast<float*>(b + L.part_c);
+  {
+    const PartSizes ps = part_sizes(*prob);
+    c->cap_r = ps.rows;
+    c->cap_c = ps.cols;
+  }
   c->blk = reinterpret_cast<double*>(b + L.blk);
   c->rbc = reinterpret_cast<unsigned int*>(b + L.rbc);
   c->center = reinterpret_cast<float*>(b + L.center);
@@ -333,12 +366,14 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
                        EpiParams* epi, bool* fused) {
   const uot_problem& p = c.p;
   float* part = axis == 0 ? c.part_r : c.part_c;
+  const size_t cap = axis == 0 ? c.cap_r : c.cap_c;
   if (p.cost_kind == UOT_COST_POINTS) {
     SideDesc X{c.px, c.l2_a, c.ln_a, p.n}, Y{c.py, c.l2_b, c.ln_b, p.m};
     const SideDesc& q = axis == 0 ? X : Y;
     const SideDesc& k = axis == 0 ? Y : X;
     if (c.tiled && !moments) {
       SweepGeom g = tile_geom(q.n, k.n, p.dim);
+      if ((size_t)g.splits * 2 * q.n > cap) g = tile_geom(q.n, k.n, p.dim, false);
       *splits = g.splits;
       if (epi) {
         epi->nq = q.n; epi->splits = g.splits; epi->part = part; epi->rb_counter = c.rbc; epi->moments = 0;
@@ -363,11 +398,14 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
                                   nullptr, c.s, 2.0f, part, g, c.st));
     } else {
       SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
+      if ((size_t)g.splits * (2 + (moments ? p.dim : 0)) * q.n > cap) g = points_geom(q.n, k.n, p.dim, moments, false);
       *splits = g.splits;
       UOT_CUDA(launch_points_sweep(q, k, p.dim, p.p, pot, shift, c.s, moments, part, g, c.st));
     }
   } else {
     SweepGeom g = axis == 0 ? dense_row_geom(p.n, p.m) : dense_col_geom(p.n, p.m);
+    if ((size_t)g.splits * 2 * (axis == 0 ? p.n : p.m) > cap)
+      g = axis == 0 ? dense_row_geom(p.n, p.m, false) : dense_col_geom(p.n, p.m, false);
     *splits = g.splits;
     UOT_CUDA(launch_dense_sweep(axis, p.C, p.n, p.m, axis == 0 ? c.l2_b : c.l2_a, pot, shift, c.s, part, g,
                                 c.st));
@@ -1199,6 +1237,7 @@ uot_status uot_profile_end(double* sweep_ms, int64_t* timed_launches, int64_t* l
 uot_status uot_plan_create(const uot_problem* prob, const uot_options* opt, int32_t variant, uot_plan** out) {
   if (!out) return fail(UOT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  tune_autoload();
   uot_status v = validate(prob);
   if (v != UOT_OK) return v;
   if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");

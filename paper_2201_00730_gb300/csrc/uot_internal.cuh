@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/uot.h"
 
 namespace uot {
@@ -91,10 +93,35 @@ void note_launch();
 void set_last_error(const char* msg);
 // Test hook behind uot_test_set_wait_limit (0 restores kWaitPolls).
 void set_wait_limit(long long polls);
-SweepGeom points_geom(int nq, int nk, int dim, bool moments);
-SweepGeom dense_row_geom(int nrows, int ncols);
-SweepGeom dense_col_geom(int nrows, int ncols);
+// tuned = false: the built-in shape, whatever the tuning table holds.
+SweepGeom points_geom(int nq, int nk, int dim, bool moments, bool tuned = true);
+SweepGeom dense_row_geom(int nrows, int ncols, bool tuned = true);
+SweepGeom dense_col_geom(int nrows, int ncols, bool tuned = true);
 int max_splits_for(const uot_problem& p);
+// Launch-shape tuning (tune.cu): the value of a knob for a sweep of `entries`
+// cost entries in dimension dim (-1: none), dflt when the table has none;
+// floor(log2(entries)); the one-time load of UOT_TUNE_FILE.
+long long tune_value(const char* knob, int dim, long long entries, long long dflt);
+int tune_bucket(long long entries);
+void tune_autoload();
+// While a TuneScope lives, tune_value returns its values for its knobs on this
+// thread (workspace sizing takes the largest partials over every allowed shape,
+// so that a workspace stays valid whatever the table holds later).
+struct TuneFix {
+  const char* knob;
+  long long value;
+};
+class TuneScope {
+ public:
+  TuneScope(const TuneFix* f, int n);
+  ~TuneScope();
+  TuneScope(const TuneScope&) = delete;
+  TuneScope& operator=(const TuneScope&) = delete;
+
+ private:
+  int n_;
+};
+std::vector<long long> tune_allowed(const char* knob);
 
 constexpr int kMaxBlocks = 4096;
 constexpr int kTileKeys = 128;  // keys per local-frame tile of the tiled sweep
@@ -149,7 +176,7 @@ cudaError_t launch_points_sweep(const SideDesc& q, const SideDesc& k, int dim, f
                                 const float* pot_k, const double* shift_k, double s,
                                 bool moments, float* part, const SweepGeom& g, cudaStream_t st);
 // Tiled sweep (sorted clouds, dim <= 3, p = 2); centers_k = tile centres of the key side.
-SweepGeom tile_geom(int nq, int nk, int dim);
+SweepGeom tile_geom(int nq, int nk, int dim, bool tuned = true);
 // With epi != nullptr the last CTA of each row block also runs the half-step
 // epilogue for its rows (no separate combine launch); epi->part must be `part`.
 // The sweep itself ignores shift_k: it is handed to the epilogue (epi->key_shift),

@@ -134,12 +134,36 @@ def lib() -> C.CDLL:
         L.uot_profile_begin.restype = C.c_int
         L.uot_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.uot_profile_end.restype = C.c_int
+        L.uot_tune_set.argtypes = [C.c_char_p, C.c_int32, C.c_int32, C.c_int64]
+        L.uot_tune_set.restype = C.c_int
+        L.uot_tune_get.argtypes = [C.c_char_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64)]
+        L.uot_tune_get.restype = C.c_int
+        L.uot_tune_bucket.argtypes = [C.c_int64]
+        L.uot_tune_bucket.restype = C.c_int32
+        L.uot_tune_clear.argtypes = []
+        L.uot_tune_clear.restype = C.c_int
+        L.uot_tune_load.argtypes = [C.c_char_p]
+        L.uot_tune_load.restype = C.c_int
         L.uot_last_error.argtypes = []
         L.uot_last_error.restype = C.c_char_p
         L.uot_version.argtypes = []
         L.uot_version.restype = C.c_char_p
         _lib = L
+        _apply_packaged_tuning()
     return _lib
+
+
+def _apply_packaged_tuning():
+    """Loads the launch-shape cache shipped with the package when it was measured on
+    this device (see autotune.py); the built-in shapes stay in force otherwise."""
+    if os.environ.get("UOT_NO_TUNE_CACHE") or not torch.cuda.is_available():
+        return
+    from . import autotune
+    try:
+        autotune.load()
+    except (OSError, ValueError, UOTError) as e:
+        import warnings
+        warnings.warn(f"tuning cache not applied: {e}")
 
 
 def _check(status: int, allow=(UOT_OK,)) -> int:
@@ -238,7 +262,7 @@ def softmin(spec: Spec, pot: torch.Tensor, axis: int, ws: torch.Tensor | None = 
 
 
 def softmin_noalloc(spec: Spec, pot: torch.Tensor, axis: int) -> torch.Tensor:
-    """uot_softmin without a workspace: the library's built-in 16 MiB scratch is used.
+    """uot_softmin without a workspace: the library's built-in 32 MiB scratch is used.
 
     For callers that cannot allocate device memory; see include/uot.h.
     """
@@ -653,6 +677,31 @@ def mmot1d_batched(problems, n_iter: int, device="cuda:0", check: bool = True) -
         bws.append(BW[bo:bo + blen[p]])
         bo += int(n[p * K:(p + 1) * K].sum())
     return MMOT1DOut(fs, bxs, bws, list(stat), code)
+
+
+def tune_set(knob: str, value: int, dim: int = -1, bucket: int = -1) -> None:
+    """Sets (value != 0) or clears (value 0) one entry of the launch-shape table."""
+    _check(lib().uot_tune_set(knob.encode(), int(dim), int(bucket), int(value)))
+
+
+def tune_get(knob: str, dim: int = -1, entries: int = 0) -> int:
+    """The entry that applies to a sweep of `entries` cost entries, 0 for the built-in rule."""
+    v = C.c_int64(0)
+    _check(lib().uot_tune_get(knob.encode(), int(dim), int(entries), C.byref(v)))
+    return int(v.value)
+
+
+def tune_bucket(entries: int) -> int:
+    return int(lib().uot_tune_bucket(int(entries)))
+
+
+def tune_clear() -> None:
+    _check(lib().uot_tune_clear())
+
+
+def tune_load(path: str) -> None:
+    """Adds the entries of a JSON tuning cache (see autotune.py)."""
+    _check(lib().uot_tune_load(os.fspath(path).encode()))
 
 
 def version() -> str:

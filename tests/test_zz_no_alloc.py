@@ -2,7 +2,7 @@
 
 uot_softmin_noalloc serves callers that cannot allocate device memory (a host
 program without an allocator, a plug-in whose host forbids allocation, a
-real-time loop): it runs the softmin sweep on a 16 MiB scratch array built into
+real-time loop): it runs the softmin sweep on a 32 MiB scratch array built into
 the library.  This file is collected last so that a failure here leaves every
 other test already run.
 """
