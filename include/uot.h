@@ -89,6 +89,13 @@ typedef struct {
   const float* b;      /* device, M weights, b_j >= 0      */
 } uot_problem;
 
+/* Divergence of a marginal penalty for uot_sinkhorn_phi (Sec. 3): the convex
+ * conjugate phi^* of the penalty, with parameter rho (rho1 for a, rho2 for b). */
+typedef enum {
+  UOT_PHI_KL = 0,   /* rho KL:        phi^*(q) = rho (e^{q/rho} - 1)          */
+  UOT_PHI_BERG = 1  /* Berg entropy:  phi^*(q) = -rho log(1 - q/rho), q < rho */
+} uot_phi;
+
 /* Iteration control for uot_sinkhorn / uot_ti_sinkhorn / uot_g_sinkhorn. */
 typedef struct {
   int32_t max_iter;          /* >= 1 full iterations (g half-step, then f half-step)          */
@@ -461,6 +468,31 @@ UOT_API size_t uot_mmot1d_barycenter_size(const uot_mmot1d_batch* batch);
  * else the first failing problem's status. */
 UOT_API uot_status uot_mmot1d_batched(const uot_mmot1d_batch* batch, double* f, double* bary_x, double* bary_w,
                                       int32_t* bary_len, int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* F- and G-Sinkhorn for a general smooth phi^* (Sec. 3), phi1 for the
+ * penalty on a, phi2 for the one on b (uot_phi).  With
+ * aprox_{phi^*}(x) = argmin_y eps e^{(x - y)/eps} + phi^*(y), one iteration is
+ *   variant 0 (F):  g <- -aprox_2(-Smin_a(C - f)),            f <- -aprox_1(-Smin_b(C - g));
+ *   variant 2 (G):  gb <- -aprox_2(-Smin_a(C - fb - lambda)) + lambda,
+ *                   fb <- -aprox_1(-Smin_b(C - gb + lambda)) - lambda,  lambda <- lambda*(fb, gb),
+ * lambda* = argmax_l <a, -phi_1^*(-fb - l)> + <b, -phi_2^*(-gb + l)> (Prop. 1),
+ * from f_0 = 0 (or f on entry with warm_start; G starts from fb_0 = f, lambda_0 = 0).
+ * The softmins run on the sweeps of uot_softmin (FP32, the 1e-4 eps bound);
+ * the prox maps and lambda* in FP64 (Berg: aprox(x) = rho - eps omega(L),
+ * omega the Wright omega function, L = log(rho/eps) + (rho - x)/eps; lambda* by
+ * Newton steps kept inside a bracket of the root).  Returns f (= fb + lambda for G)
+ * and g (= gb - lambda), result->lambda = lambda (0 for F), result->residual =
+ * max_j |g_t - g_{t-1}| of the last iteration (gb for G), tested every
+ * check_every iterations against opt->tol.  Options anderson_k and
+ * residual_history are not used; lse_reference has no effect.  Workspace:
+ * uot_sinkhorn_phi_workspace_size(prob) bytes, 256-byte aligned.  Errors as for
+ * uot_sinkhorn, plus UOT_ERR_INVALID_ARG for another variant or divergence.
+ * With phi1 = phi2 = UOT_PHI_KL, variant 0 gives uot_sinkhorn's iterates and
+ * variant 2 uot_g_sinkhorn's, within rounding. */
+UOT_API size_t uot_sinkhorn_phi_workspace_size(const uot_problem* prob);
+UOT_API uot_status uot_sinkhorn_phi(const uot_problem* prob, const uot_options* opt, int32_t variant, int32_t phi1,
+                                    int32_t phi2, float* f, float* g, uot_result* result, void* ws, size_t ws_bytes,
+                                    void* stream);
 
 /* ---- Launch-shape tuning ------------------------------------------------------
  *

@@ -647,6 +647,25 @@ uot_status solve(int variant, const uot_problem* prob, const uot_options* opt, f
 
 // ---- unrolled backward -------------------------------------------------------
 // Extra workspace of uot_grad_unrolled after the regular layout of the problem.
+// uot_sinkhorn_phi: the solver workspace, then fb, gb, the softmin S (sweep
+// order), the lambda* state and its block partials.
+struct PhiLayout {
+  size_t fb, gb, S, lam, lblk, total;
+};
+
+PhiLayout phi_layout(const uot_problem& p) {
+  PhiLayout L{};
+  size_t off = align256(ws_layout(p).total);
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  L.fb = take(sizeof(float) * p.n);
+  L.gb = take(sizeof(float) * p.m);
+  L.S = take(sizeof(float) * (p.n > p.m ? p.n : p.m));
+  L.lam = take(sizeof(LamState));
+  L.lblk = take(sizeof(double) * 2 * kMaxBlocks);
+  L.total = off;
+  return L;
+}
+
 struct URLayout {
   size_t base, ck_f, ck_slot, fbar, gbarn, Sp, Gp, ghat, S, G, fhat, rec, fst, g0, fbb, gbb, Sb, Spb, ffin, gfin,
       fbT, gbT, ga, gb, gx, gy, val, mom, adj, sums, total;
@@ -1125,6 +1144,110 @@ uot_status uot_ti_sinkhorn(const uot_problem* prob, const uot_options* opt, floa
 uot_status uot_g_sinkhorn(const uot_problem* prob, const uot_options* opt, float* f, float* g,
                           uot_result* result, void* ws, size_t ws_bytes, void* stream) {
   return solve(2, prob, opt, f, g, result, ws, ws_bytes, stream);
+}
+
+size_t uot_sinkhorn_phi_workspace_size(const uot_problem* prob) {
+  if (validate(prob) != UOT_OK) return 0;
+  return phi_layout(*prob).total;
+}
+
+uot_status uot_sinkhorn_phi(const uot_problem* prob, const uot_options* opt, int32_t variant, int32_t phi1,
+                            int32_t phi2, float* f, float* g, uot_result* result, void* ws, size_t ws_bytes,
+                            void* stream) {
+  if (!opt) return fail(UOT_ERR_INVALID_ARG, "options is NULL");
+  if (variant != 0 && variant != 2) return fail(UOT_ERR_INVALID_ARG, "variant must be 0 (F) or 2 (G)");
+  if ((phi1 != UOT_PHI_KL && phi1 != UOT_PHI_BERG) || (phi2 != UOT_PHI_KL && phi2 != UOT_PHI_BERG))
+    return fail(UOT_ERR_INVALID_ARG, "phi1, phi2 must be UOT_PHI_KL or UOT_PHI_BERG");
+  if (opt->max_iter < 1 || opt->check_every < 1) return fail(UOT_ERR_INVALID_ARG, "need max_iter, check_every >= 1");
+  if (!(opt->tol >= 0.0) || !isfinite(opt->tol)) return fail(UOT_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (!f || !g) return fail(UOT_ERR_INVALID_ARG, "f and g must be device pointers");
+  uot_status v = validate(prob);
+  if (v != UOT_OK) return v;
+  const PhiLayout PL = phi_layout(*prob);
+  if (ws_bytes < PL.total)
+    return fail(UOT_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, PL.total);
+  Ctx c;
+  v = make_ctx(prob, ws, ws_bytes, stream, &c, 2.0 * opt->max_iter);
+  if (v != UOT_OK) return v;
+  v = prepare(c);
+  if (v != UOT_OK) return v;
+  const uot_problem& p = c.p;
+  char* b = static_cast<char*>(ws);
+  float* fb = reinterpret_cast<float*>(b + PL.fb);
+  float* gb = reinterpret_cast<float*>(b + PL.gb);
+  float* S = reinterpret_cast<float*>(b + PL.S);
+  LamState* ls = reinterpret_cast<LamState*>(b + PL.lam);
+  double* lblk = reinterpret_cast<double*>(b + PL.lblk);
+  const bool G = variant == 2;
+  if (opt->warm_start) {
+    if (c.tiled) UOT_CUDA(launch_gather_vec(f, c.perm_x, p.n, fb, c.st));
+    else UOT_CUDA(cudaMemcpyAsync(fb, f, sizeof(float) * p.n, cudaMemcpyDeviceToDevice, c.st));
+  } else {
+    UOT_CUDA(cudaMemsetAsync(fb, 0, sizeof(float) * p.n, c.st));
+  }
+  UOT_CUDA(cudaMemsetAsync(gb, 0, sizeof(float) * p.m, c.st));
+  UOT_CUDA(cudaMemsetAsync(ls, 0, sizeof(LamState), c.st));
+  Slot* sl = &c.state->slot[0];
+  // one softmin half-step into S (the key potential in the sweeps' order, its shift exact)
+  auto softmin_into_S = [&](int axis, const float* pot, const double* shift) -> uot_status {
+    EpiParams e{};
+    e.mode = EPI_SOFTMIN; e.nq = axis == 0 ? p.n : p.m; e.s = c.s;
+    e.eps = p.eps; e.rho_o = axis == 0 ? p.rho1 : p.rho2; e.rho_i = axis == 0 ? p.rho2 : p.rho1;
+    e.out_is_f = axis == 0; e.lnw_o = axis == 0 ? c.ln_a : c.ln_b; e.out = S; e.state = c.state;
+    e.l2w_o = axis == 0 ? c.l2_a : c.l2_b; e.l2lo_o = axis == 0 ? c.lo_a : c.lo_b;
+    e.part = axis == 0 ? c.part_r : c.part_c; e.blk = c.blk; e.slot_in = 0; e.slot_out = 0;
+    int splits = 0;
+    bool fused = false;
+    uot_status w = sweep(c, axis, pot, shift, false, &splits, &e, &fused);
+    if (w != UOT_OK) return w;
+    e.splits = splits;
+    if (!fused) UOT_CUDA(launch_combine(e, c.st));
+    return UOT_OK;
+  };
+  int t = 0, status = 0;
+  float r = NAN;
+  while (t < opt->max_iter) {
+    ++t;
+    UOT_CUDA(cudaMemsetAsync(&c.state->resid, 0, sizeof(float), c.st));
+    // g half-step: keys f (plus lambda for G)
+    v = softmin_into_S(1, fb, G ? &sl->cf : nullptr);
+    if (v != UOT_OK) return v;
+    UOT_CUDA(launch_phi_half(S, gb, p.m, phi2, p.rho2, p.eps, G ? &ls->lam : nullptr, 1.0, &c.state->resid,
+                             &c.state->status, c.st));
+    // f half-step: keys g (minus lambda for G)
+    v = softmin_into_S(0, gb, G ? &sl->cg : nullptr);
+    if (v != UOT_OK) return v;
+    UOT_CUDA(launch_phi_half(S, fb, p.n, phi1, p.rho1, p.eps, G ? &ls->lam : nullptr, -1.0, nullptr,
+                             &c.state->status, c.st));
+    if (G)
+      UOT_CUDA(launch_lambda_star(fb, gb, c.pa, c.pb, p.n, p.m, phi1, phi2, p.rho1, p.rho2, ls, lblk, c.state, 0,
+                                  48, c.st));
+    if (t == opt->max_iter || (opt->tol > 0.0 && t % opt->check_every == 0)) {
+      v = read_flags(c, &status, &r);
+      if (v != UOT_OK) return v;
+      if (status != 0 || isnan(r)) break;
+      if (opt->tol > 0.0 && r <= opt->tol) break;
+    }
+  }
+  UOT_CUDA(launch_phi_out(fb, gb, c.perm_x, c.perm_y, f, g, p.n, p.m, &ls->lam, G ? 1 : 0, c.st));
+  double lam = 0.0;
+  UOT_CUDA(cudaMemcpyAsync(&lam, &ls->lam, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  UOT_CUDA(cudaStreamSynchronize(c.st));
+  uot_status out = UOT_OK;
+  const bool converged = !isnan(r) && r <= opt->tol;
+  if (status & kStatusBadWeights) out = fail(UOT_ERR_NONFINITE, "negative, NaN or infinite weights");
+  else if (status & kStatusTimeout) out = fail(UOT_ERR_TIMEOUT, "a bounded device-side wait gave up (tensor-core sweep)");
+  else if (status != 0 || isnan(r)) out = fail(UOT_ERR_NONFINITE, "non-finite value met during the iteration");
+  else if (opt->tol > 0.0 && !converged) out = UOT_NOT_CONVERGED;
+  if (result) {
+    result->iters = t;
+    result->converged = converged ? 1 : 0;
+    result->status = out;
+    result->lse_misses = 0;
+    result->residual = r;
+    result->lambda = G ? lam : 0.0;
+  }
+  return out;
 }
 
 uot_status uot_dual_value(const uot_problem* prob, const float* f, const float* g, double* out,

@@ -98,6 +98,26 @@ SweepGeom points_geom(int nq, int nk, int dim, bool moments, bool tuned = true);
 SweepGeom dense_row_geom(int nrows, int ncols, bool tuned = true);
 SweepGeom dense_col_geom(int nrows, int ncols, bool tuned = true);
 int max_splits_for(const uot_problem& p);
+// General phi^* (general_phi.cu).  State of the lambda* search: the current
+// lambda, the bracket [lo, hi] of the root of F', the last-block counter.
+struct LamState {
+  double lam, lo, hi;
+  unsigned int counter;
+  int done;
+};
+// out = -aprox_{phi^*}(-S) + sign * *shift (shift nullable), elementwise over n;
+// resid (nullable) gets max |out_new - out_old| by an atomic max.
+cudaError_t launch_phi_half(const float* S, float* out, int n, int phi, double rho, double eps, const double* shift,
+                            double sign, float* resid, int* status, cudaStream_t st);
+// lambda*(fb, gb): one bracketing launch and `steps` Newton launches (each a no-op
+// once converged); the result goes to ls->lam and to the shifts of st->slot[slot].
+cudaError_t launch_lambda_star(const float* fb, const float* gb, const float* a, const float* b, int n, int m,
+                               int phi1, int phi2, double rho1, double rho2, LamState* ls, double* blk, DevState* st,
+                               int slot, int steps, cudaStream_t s);
+// f = fb + lambda, g = gb - lambda (g_mode; else plain copies) in the caller's order.
+cudaError_t launch_phi_out(const float* fb, const float* gb, const int* pf, const int* pg, float* f, float* g, int n,
+                           int m, const double* lam, int g_mode, cudaStream_t st);
+
 // Launch-shape tuning (tune.cu): the value of a knob for a sweep of `entries`
 // cost entries in dimension dim (-1: none), dflt when the table has none;
 // floor(log2(entries)); the one-time load of UOT_TUNE_FILE.

@@ -134,6 +134,11 @@ def lib() -> C.CDLL:
         L.uot_profile_begin.restype = C.c_int
         L.uot_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.uot_profile_end.restype = C.c_int
+        L.uot_sinkhorn_phi_workspace_size.argtypes = [P]
+        L.uot_sinkhorn_phi_workspace_size.restype = S
+        L.uot_sinkhorn_phi.argtypes = [P, C.POINTER(Options), C.c_int32, C.c_int32, C.c_int32, V, V,
+                                       C.POINTER(Result), V, S, V]
+        L.uot_sinkhorn_phi.restype = C.c_int
         L.uot_tune_set.argtypes = [C.c_char_p, C.c_int32, C.c_int32, C.c_int64]
         L.uot_tune_set.restype = C.c_int
         L.uot_tune_get.argtypes = [C.c_char_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64)]
@@ -332,6 +337,32 @@ def solve(spec: Spec, method: str = "ti", max_iter: int = 1000, tol: float = 0.0
 
 
 VARIANTS = {"plain": 0, "ti": 1, "g": 2}
+PHI = {"kl": 0, "berg": 1}
+
+
+def solve_phi(spec: Spec, method: str = "g", phi1: str = "berg", phi2: str = "berg", max_iter: int = 1000,
+              tol: float = 0.0, check_every: int = 10, f0: torch.Tensor | None = None) -> SolveOut:
+    """F-Sinkhorn ('f') or G-Sinkhorn ('g') with the divergences phi1 (on a) and phi2 (on b),
+    each 'kl' or 'berg' (uot_sinkhorn_phi).  Returns (f, g), lambda (G) and the residual
+    max |g_t - g_(t-1)| of the last iteration."""
+    if method not in ("f", "g") or phi1 not in PHI or phi2 not in PHI:
+        raise ValueError("method 'f' or 'g'; phi1, phi2 'kl' or 'berg'")
+    pr = spec.struct()
+    dev = spec.a.device
+    f = torch.empty(spec.n, dtype=torch.float32, device=dev)
+    g = torch.empty(spec.m, dtype=torch.float32, device=dev)
+    if f0 is not None:
+        f.copy_(f0)
+    nbytes = int(lib().uot_sinkhorn_phi_workspace_size(C.byref(pr)))
+    if nbytes == 0:
+        raise UOTError(1, lib().uot_last_error().decode())
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    opt = Options(int(max_iter), int(check_every), float(tol), 1 if f0 is not None else 0, 0, None, 0, 0.0, None)
+    res = Result()
+    st = lib().uot_sinkhorn_phi(C.byref(pr), C.byref(opt), 0 if method == "f" else 2, PHI[phi1], PHI[phi2],
+                                _ptr(f), _ptr(g), C.byref(res), _ptr(ws), ws.numel(), _stream())
+    _check(st, allow=(UOT_OK, UOT_NOT_CONVERGED))
+    return SolveOut(f, g, res.iters, bool(res.converged), st, res.residual, res.lambda_, None, 0)
 
 
 class Plan:

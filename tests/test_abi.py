@@ -161,3 +161,17 @@ def test_plan_rejects_anderson_and_bad_variant(L):
     opt = uot.Options(10, 5, 0.0, 0, 0, None, 0, 0.0, None)
     assert L.uot_plan_create(C.byref(pr), C.byref(opt), 5, C.byref(h)) == 1
     assert L.uot_plan_workspace_size(None) == 0
+
+
+def test_sinkhorn_phi_rejects_bad_variant_and_divergence(L):
+    """uot_sinkhorn_phi checks its variant and divergences before any CUDA call."""
+    from paper_2201_00730_gb300 import uot
+    pr = uot.Problem(10, 12, 2, 0, 2.0, 0, 0.1, 1.0, 1.0, 256, 256, None, 256, 256)
+    opt = uot.Options(10, 5, 0.0, 0, 0, None, 0, 0.0, None)
+    res = uot.Result()
+    p = C.c_void_p(256)
+    assert L.uot_sinkhorn_phi(C.byref(pr), C.byref(opt), 1, 0, 1, p, p, C.byref(res), p, 1 << 30, None) == 1
+    assert b"variant" in L.uot_last_error()
+    assert L.uot_sinkhorn_phi(C.byref(pr), C.byref(opt), 2, 0, 2, p, p, C.byref(res), p, 1 << 30, None) == 1
+    assert b"UOT_PHI" in L.uot_last_error()
+    assert L.uot_sinkhorn_phi(C.byref(pr), None, 0, 0, 0, p, p, C.byref(res), p, 1 << 30, None) == 1
