@@ -90,26 +90,24 @@ k_adjoint(const float* __restrict__ q, int nq, const float* __restrict__ kp, int
 }
 
 // value_q = 2^M sum; moments alike; FP64 assembly of the key chunks.
+// One thread per (row, channel c): c = 0 the value, c = 1 + d moment d (rows fastest:
+// coalesced partial loads).  Chunk weights 2^(M_k - M) in FP32 (relative error ~1e-7), the
+// sums and the common factor 2^M in FP64.
 __global__ void k_adjoint_merge(const float* part, int nq, int dim, int splits, double* val, double* mom) {
   const int CH = 2 + dim;
+  const int c = blockIdx.y;
+  const int ch = c == 0 ? 1 : 1 + c;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
     float M = kInitMax;
-    for (int k = 0; k < splits; ++k) M = fmaxf(M, part[(size_t)k * CH * nq + i]);
+    for (int k = 0; k < splits; ++k) M = fmaxf(M, __ldg(part + (size_t)k * CH * nq + i));
     double v = 0.0;
     for (int k = 0; k < splits; ++k) {
       const float* b = part + (size_t)k * CH * nq;
-      v += (double)b[(size_t)nq + i] * exp2((double)b[i] - (double)M);
+      v += (double)__ldg(b + (size_t)ch * nq + i) * (double)ex2f(__ldg(b + i) - M);
     }
-    const double scale = exp2((double)M);
-    val[i] = v * scale;
-    for (int d = 0; d < dim; ++d) {
-      double m = 0.0;
-      for (int k = 0; k < splits; ++k) {
-        const float* b = part + (size_t)k * CH * nq;
-        m += (double)b[(size_t)(2 + d) * nq + i] * exp2((double)b[i] - (double)M);
-      }
-      mom[(size_t)i * dim + d] = m * scale;
-    }
+    v *= exp2((double)M);
+    if (c == 0) val[i] = v;
+    else mom[(size_t)i * dim + (c - 1)] = v;
   }
 }
 
@@ -139,9 +137,7 @@ cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int 
     cudaError_t e = launch_flash_sweep(q, nq, kp, nk, dim, center, nullptr, nullptr, nullptr, pot_q, h_k, c_k, s, 1.0f,
                                        part, gf, st);
     if (e != cudaSuccess) return e;
-    int gb = (nq + 255) / 256;
-    if (gb > 1024) gb = 1024;
-    k_adjoint_merge<<<gb, 256, 0, st>>>(part, nq, dim, gf.splits, val, mom);
+    k_adjoint_merge<<<dim3((nq + 255) / 256, dim + 1), 256, 0, st>>>(part, nq, dim, gf.splits, val, mom);
     note_launch();
     return cudaGetLastError();
   }
@@ -157,9 +153,7 @@ cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int 
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int gb = (nq + 255) / 256;
-  if (gb > 1024) gb = 1024;
-  k_adjoint_merge<<<gb, 256, 0, st>>>(part, nq, dim, g.splits, val, mom);
+  k_adjoint_merge<<<dim3((nq + 255) / 256, dim + 1), 256, 0, st>>>(part, nq, dim, g.splits, val, mom);
   note_launch();
   return cudaGetLastError();
 }

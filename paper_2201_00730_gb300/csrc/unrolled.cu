@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "sweep_common.cuh"
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -67,25 +68,23 @@ __global__ void k_add_scalar(const float* u, const double* c, int n, float* v) {
     v[i] = (float)((double)u[i] + cc);
 }
 
-// Normalised gradient moments G_q = sum_k w_qk dC/dq / sum_k w_qk from sweep partials with moments.
+// Normalised gradient moments G_q = sum_k w_qk dC/dq / sum_k w_qk from sweep partials with moments:
+// one thread per (row, coordinate) (rows fastest: coalesced partial loads); the chunk weights
+// 2^(M_k - M) in FP32 (relative error ~1e-7), the sums in FP64.
 __global__ void k_moments(const float* part, int nq, int dim, int splits, double scale, float* G) {
   const int CH = 2 + dim;
+  const int d = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
     float M = kInitMax;
-    for (int k = 0; k < splits; ++k) M = fmaxf(M, part[(size_t)k * CH * nq + i]);
-    double sum = 0.0;
+    for (int k = 0; k < splits; ++k) M = fmaxf(M, __ldg(part + (size_t)k * CH * nq + i));
+    double sum = 0.0, mo = 0.0;
     for (int k = 0; k < splits; ++k) {
       const float* b = part + (size_t)k * CH * nq;
-      sum += (double)b[(size_t)nq + i] * exp2((double)b[i] - (double)M);
+      const double w = (double)simd::ex2f(__ldg(b + i) - M);
+      sum += (double)__ldg(b + (size_t)nq + i) * w;
+      mo += (double)__ldg(b + (size_t)(2 + d) * nq + i) * w;
     }
-    for (int d = 0; d < dim; ++d) {
-      double mo = 0.0;
-      for (int k = 0; k < splits; ++k) {
-        const float* b = part + (size_t)k * CH * nq;
-        mo += (double)b[(size_t)(2 + d) * nq + i] * exp2((double)b[i] - (double)M);
-      }
-      G[(size_t)i * dim + d] = (float)(scale * mo / sum);
-    }
+    G[(size_t)i * dim + d] = (float)(scale * mo / sum);
   }
 }
 
@@ -236,8 +235,9 @@ cudaError_t launch_add_scalar(const float* u, const double* c, int n, float* v, 
   return cudaSuccess;
 }
 cudaError_t launch_moments(const float* part, int nq, int dim, int splits, double scale, float* G, cudaStream_t st) {
-  UOT_LAUNCH(k_moments, nq, part, nq, dim, splits, scale, G);
-  return cudaSuccess;
+  k_moments<<<dim3((nq + kBlk - 1) / kBlk, dim), kBlk, 0, st>>>(part, nq, dim, splits, scale, G);
+  note_launch();
+  return cudaGetLastError();
 }
 cudaError_t launch_final_side(const float* part, int CH, int nq, int splits, double s, double eps, double rho,
                               const float* pot, const double* lnw, float* cot, double* blk, unsigned int* ctr,
