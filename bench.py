@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--rho", type=float, default=1.0)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-tol, dense and CPU legs")
     ap.add_argument("--plain-cap", type=int, default=200000, help="iteration cap of plain Sinkhorn in time-to-tol")
-    ap.add_argument("--kernel-case", choices=["points", "dense", "d64", "small"], default=None,
+    ap.add_argument("--kernel-case", choices=["points", "dense", "d64", "small", "fw1d", "d64unrolled", "mmot1d"],
+                    default=None,
                     help="only launch a few sweeps of the workload (for Nsight Compute captures) and exit")
     return ap.parse_args()
 
@@ -605,6 +606,21 @@ def run_kernel_case(args):
         ws = spec.workspace()
         for _ in range(3):
             U.softmin(spec, torch.zeros(q.m, device=dev), 0, ws)
+    elif args.kernel_case == "fw1d":
+        # 1024 Frank-Wolfe problems, N = M = 200: the batched 1-D kernel, 200 steps per call
+        probs = W.config_fw1d()
+        for _ in range(2):
+            U.fw1d_batched(probs, 200)
+    elif args.kernel_case == "mmot1d":
+        # 64 multi-marginal problems, K = 8 marginals of 200 points, 100 Frank-Wolfe steps
+        probs = W.config_mmot1d()
+        for _ in range(2):
+            U.mmot1d_batched(probs, 100)
+    elif args.kernel_case == "d64unrolled":
+        # D = 64, N = M = 8192: unrolled backward of 40 TI iterations (moment and adjoint sweeps)
+        q = W.config3()
+        spec = U.Spec(t(q.a), t(q.b), q.eps, q.rho1, q.rho2, x=t(q.x), y=t(q.y))
+        U.grad_unrolled(spec, T=40, ckpt_every=20)
     elif args.kernel_case == "points":
         # a short TI solve: its sweeps are the fused tiled kernel of the timed step
         # (the first few with a running max, the later ones with the stored reference)
