@@ -505,6 +505,7 @@ UOT_API uot_status uot_sinkhorn_phi(const uot_problem* prob, const uot_options* 
  *   "tile.rows"          2, 4            rows per thread, tiled sweep (dim <= 3)
  *   "tile.cta_cost"      5 10 15 25 40   per-CTA fixed cost (tenths of a 128-key
  *                                        tile) in the tiled sweep's chunking
+ *   "tile.waves"         1, 2, 3, 4      fewest waves of CTAs the chunking may take
  *   "points.rows"        1, 2, 4         rows per thread, direct sweep (dim <= 3)
  *   "points.resident"    2, 3, 4, 6      CTAs per SM the direct sweep's chunking aims at
  *   "dense.row_chunk"    2048 4096 8192  columns per CTA, dense row sweep

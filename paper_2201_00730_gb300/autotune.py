@@ -30,6 +30,7 @@ from . import workloads as W
 KNOBS = {
     "tile.rows": (2, 4),
     "tile.cta_cost": (5, 10, 15, 25, 40),
+    "tile.waves": (1, 2, 3, 4),
     "points.rows": (1, 2, 4),
     "points.resident": (2, 3, 4, 6),
     "dense.row_chunk": (2048, 4096, 8192),
@@ -39,7 +40,7 @@ KNOBS = {
 
 # knobs of each path, in the order they are tuned
 PATH_KNOBS = {
-    "tiled": ("tile.rows", "tile.cta_cost"),
+    "tiled": ("tile.rows", "tile.waves", "tile.cta_cost"),
     "direct": ("points.rows", "points.resident"),
     "dense": ("dense.row_chunk", "dense.col_ctas"),
 }

@@ -387,6 +387,9 @@ SweepGeom tile_geom(int nq, int nk, int dim, bool tuned) {
   const int rows_per_cta = kThreads * R;
   g.row_blocks = (nq + rows_per_cta - 1) / rows_per_cta;
   const double cta_cost = tuned ? 0.1 * (double)tune_value("tile.cta_cost", dim, entries, 15) : 1.5;
+  // at least this many waves of CTAs when the keys allow it: with several waves
+  // an SM whose resident CTA ends early takes the next one instead of idling
+  const int min_waves = tuned ? (int)tune_value("tile.waves", dim, entries, 1) : 1;
   const long long target = (long long)sms * occupancy_for(dim, R);
   const int max_tiles = (nk + kTileKeys - 1) / kTileKeys;
   // Pick the number of key chunks minimising (waves of CTAs) x (tiles per CTA +
@@ -400,6 +403,7 @@ SweepGeom tile_geom(int nq, int nk, int dim, bool tuned) {
     if (kk != k) continue;
     const long long ctas = (long long)g.row_blocks * kk;
     const long long waves = (ctas + target - 1) / target;
+    if (waves < min_waves && tiles_per > 1) continue;
     const double est = (double)waves * (tiles_per + cta_cost);
     if (est < best * 0.999) { best = est; best_k = kk; }
   }

@@ -39,13 +39,14 @@ struct Knob {
 };
 
 // rows per thread of the tiled sweep; its per-CTA fixed cost (tenths of a tile)
-// in the choice of key chunks; rows per thread of the direct sweep (dim <= 3);
+// in the choice of key chunks; the fewest waves of CTAs it may choose; rows per thread of the direct sweep (dim <= 3);
 // resident CTAs per SM the direct sweep's chunking aims at; columns per CTA of
 // the dense row sweep; CTAs per SM of the dense column sweep; CTAs per SM of
 // the batched solver's persistent grid
 const Knob kKnobs[] = {
     {"tile.rows", {2, 4, 0}},
     {"tile.cta_cost", {5, 10, 15, 25, 40, 0}},
+    {"tile.waves", {1, 2, 3, 4, 0}},
     {"points.rows", {1, 2, 4, 0}},
     {"points.resident", {2, 3, 4, 6, 0}},
     {"dense.row_chunk", {2048, 4096, 8192, 0}},

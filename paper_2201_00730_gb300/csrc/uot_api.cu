@@ -107,10 +107,12 @@ PartSizes part_sizes(const uot_problem& p) {
     if (tiled_path(p)) {
       for (long long R : tune_allowed("tile.rows")) {
         for (long long cost : tune_allowed("tile.cta_cost")) {
-          const TuneFix fx[2] = {{"tile.rows", R}, {"tile.cta_cost", cost}};
-          TuneScope scope(fx, 2);
-          upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
-          upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
+          for (long long w : tune_allowed("tile.waves")) {
+            const TuneFix fx[3] = {{"tile.rows", R}, {"tile.cta_cost", cost}, {"tile.waves", w}};
+            TuneScope scope(fx, 3);
+            upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim).splits * 2 * p.n);
+            upd(ps.cols, (size_t)tile_geom(p.m, p.n, p.dim).splits * 2 * p.m);
+          }
         }
       }
       upd(ps.rows, (size_t)tile_geom(p.n, p.m, p.dim, false).splits * 2 * p.n);

@@ -41,6 +41,7 @@ def close(got, ref, eps):
 CASES = [
     ("tiled", "tile.rows", (611, 437, 2), 1),
     ("tiled", "tile.cta_cost", (5000, 3000, 3), 1),
+    ("tiled", "tile.waves", (5000, 3000, 3), 1),
     ("direct", "points.rows", (2100, 1300, 3), 2),
     ("direct", "points.resident", (2100, 1300, 2), 2),
     ("dense", "dense.row_chunk", (700, 5000, 2), "dense"),
