@@ -1,15 +1,28 @@
 // Gradient and adjoint sweeps for high-dimensional point clouds (dim >= 32,
-// p = 2) with the contractions on mma.sync tensor-core fragments (the
+// p = 2) with both contractions on mma.sync tensor-core fragments (the
 // non-moment sweeps run on tcgen05, sweep_umma.cu):
 //
-//   t_ij = h_j - s |x_i - y_j|^2 = (h_j - s |y_j|^2) + (-s |x_i|^2) + 2 s x_i . y_j
+//   t_ij = h_j - s |x_i - y_j|^2 = (h_j - s |y'_j|^2) + (-s |x'_i|^2) + 2 s x'_i . y'_j,
 //
-// (coordinates taken relative to a common centre c, so the two squared norms
-// stay small).  The dot products x_i . y_j are evaluated with mma.sync
-// m16n8k8 TF32 in three passes (hi.hi + hi.lo + lo.hi with x = hi + lo,
-// hi = tf32(x)), which keeps the product at about FP32 accuracy (one TF32
-// pass would cost ~1e-3 relative), with the online log-sum-exp on the
-// accumulator fragments in registers as in fused attention kernels.
+// x' = x - c, y' = y - c with c the clouds' common centre.  As in the tcgen05
+// sweep, every coordinate is scaled by a power of two 2^e shared by both
+// clouds (the largest |x - c| 2^e in [2^14, 2^15)) and split into FP16 parts
+// hi + lo (11 significant bits each); x'.y' is hi.hi + lo.hi + hi.lo on
+// mma.sync m16n8k16 FP16 with FP32 accumulation (the dropped lo.lo is below
+// 2^-22 of |x'||y'|) and the squared norms use the same represented values.
+// The moments are a second contraction, as in fused attention:
+//     mom_d = momscale * sum_j mult_j 2^(t_ij - max) (x_i - y_j)_d
+//           = momscale (x'_i,d sum_j P_ij - O_i,d),  O = P . Z,  Z_j = mult_j y'_j,
+// with P the exponential weights of the running max (in [0, 1], split into
+// FP16 hi + lo) and Z scaled once more by a power of two 2^k per CTA (the
+// largest |mult_j| of the CTA's keys in [1/2, 1]) so that it fits FP16; O runs
+// on the same m16n8k16 instruction (Ph.Zh + Pl.Zh + Ph.Zl), its accumulator
+// fragments rescaled with the running max, and P comes from the S accumulator
+// fragments as they stand (the accumulator of two 8-key tiles is the A
+// fragment of one 16-key step).  The exponent is t_ij = H_j + Z_i - s |x_i - y_j|^2 with
+//   forward: H_j = log2 w_j + s (pot_j + shift), Z_i = 0, mult = 1 (live keys);
+//   adjoint: H_j = s h_j, Z_i = s pot_i, mult = the signed key cotangent.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,161 +35,237 @@ constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kRows = 16 * kWarps;  // 128 query rows per CTA
 constexpr int kKeys = 64;           // keys per tile
-constexpr int kDMax = 64;           // dim <= 64, padded to a multiple of 8
-constexpr int kLd = kDMax + 4;      // padded row stride (words): conflict-free fragment loads
+constexpr int kLdT = kKeys / 2 + 4; // words per dimension row of Z^T (conflict-free fragment loads)
 
 __device__ __forceinline__ float ex2f(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float p2f(int e) { return __int_as_float((127 + e) << 23); }
 
-__device__ __forceinline__ uint32_t tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// Scale exponent of the coordinates: the largest |x - c| (float bits) times 2^e in [2^14, 2^15).
+__device__ __forceinline__ int coord_exp(const int* maxbits) {
+  const int mb = maxbits ? *maxbits : 0;
+  if (mb <= 0) return 0;
+  const int e = 14 - (((mb >> 23) & 255) - 127);
+  return e < -40 ? -40 : (e > 40 ? 40 : e);
 }
 
-// split x = hi + lo with both parts representable in TF32
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_hi(x);
-  lo = tf32_hi(x - __uint_as_float(hi));
+__device__ __forceinline__ void split_h(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+__device__ __forceinline__ uint32_t pack_h(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+// a = hi + lo of two values, packed (first value in the low half)
+__device__ __forceinline__ void split_pack(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  __half h0, l0, h1, l1;
+  split_h(v0, h0, l0);
+  split_h(v1, h1, l1);
+  hi = pack_h(h0, h1);
+  lo = pack_h(l0, l1);
 }
 
-__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                      uint32_t b1) {
   asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// Softmin sweep with moments on the tensor cores (dim >= 32, p = 2): the
-// partials of the plain sweep plus, per row, the moment channels
-//     mom_d = momscale * sum_j mult_j 2^(t_ij - max) (x_i - y_j)_d
-// of the gradient sweeps (forward: mult = 1, momscale = 2, the dC/dx factor)
-// and of the unrolled backward's adjoint sweeps (mult = the signed key
-// cotangent, momscale = 1).  As in fused attention, the moment is a second
-// contraction: x_i sum_j P_ij - sum_j P_ij y_j with P the (scaled) exponential
-// weights, so O = P.Y runs on the tensor cores too (3xTF32 again), with the
-// keys of an 8-key block taken in the order (0, 2, 4, 6, 1, 3, 5, 7): the
-// accumulator fragment of S = X.Y^T then is the A fragment of P.Y as it stands.
-// The exponent is t_ij = H_j + Z_i - s |x_i - y_j|^2 with
-//   forward: H_j = log2 w_j + s (pot_j + shift), Z_i = 0;
-//   adjoint: H_j = s h_j, Z_i = s pot_i.
-__global__ void __launch_bounds__(kThreads, 1)
+// Shared memory of one CTA (KS = dim16 / 16 K-steps of 16 coordinates).
+template <int KS>
+struct FlashSmem {
+  static constexpr int kLdK = 8 * KS + 4;  // words per key row of Y (pairs of coordinates), padded
+  uint32_t xh[kRows * kLdK], xl[kRows * kLdK];  // X' 2^e of the CTA's rows, row-major, hi / lo
+  uint32_t yh[kKeys * kLdK], yl[kKeys * kLdK];  // Y' 2^e, key-major, hi / lo
+  uint32_t zh[16 * KS * kLdT], zl[16 * KS * kLdT];  // Z 2^(e+k), coordinate-major (pairs of keys), hi / lo
+  float kH[kKeys], kM[kKeys];
+  float red[kWarps];
+};
+
+// One CTA: 128 query rows (8 warps of 16) against the keys [split kps, + kps).
+template <int KS>
+__global__ void __launch_bounds__(kThreads, 2)
 k_sweep_flash(const float* __restrict__ q, int nq, const float* __restrict__ kp, int nk, int dim,
-              const float* __restrict__ center, const float* __restrict__ l2w, const float* __restrict__ pot,
-              const double* __restrict__ shift, const float* __restrict__ zrow, const float* __restrict__ hk,
-              const float* __restrict__ mk, double s, float momscale, int kps, float* __restrict__ part) {
-  extern __shared__ uint32_t smem[];
-  uint32_t* khi = smem;                      // [kKeys][kLd]
-  uint32_t* klo = khi + kKeys * kLd;         // [kKeys][kLd]
-  float* kH = reinterpret_cast<float*>(klo + kKeys * kLd);  // [kKeys]
-  float* kM = kH + kKeys;                                   // [kKeys] key multipliers
+              const float* __restrict__ center, const int* __restrict__ maxbits, const float* __restrict__ l2w,
+              const float* __restrict__ pot, const double* __restrict__ shift, const float* __restrict__ zrow,
+              const float* __restrict__ hk, const float* __restrict__ mk, double s, float momscale, int kps,
+              float* __restrict__ part) {
+  constexpr int D16 = 16 * KS;
+  constexpr int LDK = FlashSmem<KS>::kLdK;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  FlashSmem<KS>& sm = *reinterpret_cast<FlashSmem<KS>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tg = lane & 3;
+  const int g = lane >> 2, t = lane & 3;
   const int split = blockIdx.y;
   const int j0 = split * kps, j1 = min(nk, j0 + kps);
-  const int dim8 = (dim + 7) & ~7;
+  const int ce = coord_exp(maxbits);
+  const float csc = p2f(ce), icsc = p2f(-ce);
   const double sh = shift ? *shift : 0.0;
-  const float sf = (float)s, s2 = (float)(2.0 * s);
+  const float sf = (float)s;
+  const float s2 = (float)(2.0 * s) * icsc * icsc;  // the products carry 2^2e
 
+  // the CTA's multiplier scale 2^k: the largest |mult_j| of its keys times 2^k in [1/2, 1)
+  float mmax = 0.f;
+  if (mk) {
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += kThreads) mmax = fmaxf(mmax, fabsf(mk[j]));
+  } else {
+    mmax = 1.f;
+  }
+  for (int o = 16; o > 0; o >>= 1) mmax = fmaxf(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+  if (lane == 0) sm.red[warp] = mmax;
+  __syncthreads();
+  mmax = sm.red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) mmax = fmaxf(mmax, sm.red[w]);
+  int kz = 0;
+  if (mmax > 0.f && mmax < INFINITY) {
+    kz = -(((__float_as_int(mmax) >> 23) & 255) - 127) - 1;
+    kz = kz < -120 ? -120 : (kz > 120 ? 120 : kz);
+  }
+  const float zsc = p2f(kz), izsc = p2f(-kz);
+
+  // the CTA's rows: X' 2^e split, row-major, pairs of coordinates per word (the A fragments of
+  // S = X.Y^T are read from here: rows g and g + 8 of a warp's 16, coordinates (2t, 2t+1) and
+  // (2t+8, 2t+9) of a 16-coordinate step)
+  for (int u2 = threadIdx.x; u2 < kRows * (D16 / 2); u2 += kThreads) {
+    const int u = u2 / (D16 / 2), w = u2 - u * (D16 / 2), d = 2 * w;
+    const int r = blockIdx.x * kRows + u;
+    float v0 = 0.f, v1 = 0.f;
+    if (r < nq) {
+      const float* xr = q + (size_t)r * dim;
+      if (d < dim) v0 = (xr[d] - center[d]) * csc;
+      if (d + 1 < dim) v1 = (xr[d + 1] - center[d + 1]) * csc;
+    }
+    uint32_t hi, lo;
+    split_pack(v0, v1, hi, lo);
+    sm.xh[u * LDK + w] = hi;
+    sm.xl[u * LDK + w] = lo;
+  }
+  __syncthreads();
   const int rbase = blockIdx.x * kRows + warp * 16;
   const int rA = rbase + g, rB = rbase + g + 8;
-  uint32_t ahi[kDMax / 8][4], alo[kDMax / 8][4];
+  const uint32_t* xhA = sm.xh + (warp * 16 + g) * LDK;
+  const uint32_t* xhB = xhA + 8 * LDK;
+  const uint32_t* xlA = sm.xl + (warp * 16 + g) * LDK;
+  const uint32_t* xlB = xlA + 8 * LDK;
+  // |x'|^2 of the represented coordinates, per row (each of the quad's threads a quarter of the words)
   float qn[2] = {0.f, 0.f};
+  for (int w = t; w < D16 / 2; w += 4) {
+    const uint32_t hw[2] = {xhA[w], xhB[w]}, lw[2] = {xlA[w], xlB[w]};
 #pragma unroll
-  for (int ks = 0; ks < kDMax / 8; ++ks) {
-    if (ks * 8 < dim8) {
-      const int c0 = ks * 8 + tg, c1 = ks * 8 + tg + 4;
-      float v[4];
-      v[0] = (rA < nq && c0 < dim) ? q[(size_t)rA * dim + c0] - center[c0] : 0.f;
-      v[1] = (rB < nq && c0 < dim) ? q[(size_t)rB * dim + c0] - center[c0] : 0.f;
-      v[2] = (rA < nq && c1 < dim) ? q[(size_t)rA * dim + c1] - center[c1] : 0.f;
-      v[3] = (rB < nq && c1 < dim) ? q[(size_t)rB * dim + c1] - center[c1] : 0.f;
-      qn[0] = fmaf(v[0], v[0], fmaf(v[2], v[2], qn[0]));
-      qn[1] = fmaf(v[1], v[1], fmaf(v[3], v[3], qn[1]));
-#pragma unroll
-      for (int e = 0; e < 4; ++e) split_tf32(v[e], ahi[ks][e], alo[ks][e]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { ahi[ks][e] = 0u; alo[ks][e] = 0u; }
+    for (int k = 0; k < 2; ++k) {
+      const float2 fh = __half22float2(*reinterpret_cast<const __half2*>(&hw[k]));
+      const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&lw[k]));
+      const float y0 = fh.x + fl.x, y1 = fh.y + fl.y;
+      qn[k] = fmaf(y0, y0, fmaf(y1, y1, qn[k]));
     }
   }
-  qn[0] += __shfl_xor_sync(0xffffffffu, qn[0], 1);
-  qn[0] += __shfl_xor_sync(0xffffffffu, qn[0], 2);
-  qn[1] += __shfl_xor_sync(0xffffffffu, qn[1], 1);
-  qn[1] += __shfl_xor_sync(0xffffffffu, qn[1], 2);
-  const float ZA = (zrow && rA < nq) ? sf * zrow[rA] : 0.f, ZB = (zrow && rB < nq) ? sf * zrow[rB] : 0.f;
-  const float Rr[2] = {fmaf(-sf, qn[0], ZA), fmaf(-sf, qn[1], ZB)};  // row constants, added at the end
-  float mu[2] = {kInitMax, kInitMax}, acc[2] = {0.f, 0.f};
-  float o[kDMax / 8][4];  // P.Y: rows (g, g + 8) x dims (8 db + 2 tg, + 1)
 #pragma unroll
-  for (int db = 0; db < kDMax / 8; ++db) o[db][0] = o[db][1] = o[db][2] = o[db][3] = 0.f;
+  for (int k = 0; k < 2; ++k) {
+    qn[k] += __shfl_xor_sync(0xffffffffu, qn[k], 1);
+    qn[k] += __shfl_xor_sync(0xffffffffu, qn[k], 2);
+  }
+  const float ZA = (zrow && rA < nq) ? sf * zrow[rA] : 0.f, ZB = (zrow && rB < nq) ? sf * zrow[rB] : 0.f;
+  const float Rr[2] = {fmaf(-sf, qn[0] * icsc * icsc, ZA), fmaf(-sf, qn[1] * icsc * icsc, ZB)};
+  float mu[2] = {kInitMax, kInitMax}, acc[2] = {0.f, 0.f};
+  float o[2 * KS][4];  // O = P.Z: rows (g, g + 8) x coordinates (8 db + 2 t, + 1)
+#pragma unroll
+  for (int db = 0; db < 2 * KS; ++db) o[db][0] = o[db][1] = o[db][2] = o[db][3] = 0.f;
 
   for (int jt = j0; jt < j1; jt += kKeys) {
     const int cnt = min(kKeys, j1 - jt);
     __syncthreads();
-    for (int e = threadIdx.x; e < kKeys * dim8; e += kThreads) {
-      const int u = e / dim8, d = e - u * dim8;
-      float v = 0.f;
-      if (u < cnt && d < dim) v = kp[(size_t)(jt + u) * dim + d] - center[d];
+    // Y' 2^e split, key-major, pairs of coordinates per word
+    for (int u2 = threadIdx.x; u2 < kKeys * (D16 / 2); u2 += kThreads) {
+      const int u = u2 / (D16 / 2), w = u2 - u * (D16 / 2), d = 2 * w;
+      float v0 = 0.f, v1 = 0.f;
+      if (u < cnt) {
+        const float* kr = kp + (size_t)(jt + u) * dim;
+        if (d < dim) v0 = (kr[d] - center[d]) * csc;
+        if (d + 1 < dim) v1 = (kr[d + 1] - center[d + 1]) * csc;
+      }
       uint32_t hi, lo;
-      split_tf32(v, hi, lo);
-      khi[u * kLd + d] = hi;
-      klo[u * kLd + d] = lo;
+      split_pack(v0, v1, hi, lo);
+      sm.yh[u * LDK + w] = hi;
+      sm.yl[u * LDK + w] = lo;
     }
     __syncthreads();
+    // key constants, and Z = mult Y' 2^(e + k) split, coordinate-major, pairs of keys per word
     if (threadIdx.x < kKeys) {
       const int u = threadIdx.x;
       float H = kZeroW, mult = 0.f;
       if (u < cnt) {
         const int j = jt + u;
         float y2 = 0.f;
-#pragma unroll 8
-        for (int d = 0; d < dim8; ++d) {
-          const float v = __uint_as_float(khi[u * kLd + d]) + __uint_as_float(klo[u * kLd + d]);
-          y2 = fmaf(v, v, y2);
+        for (int w = 0; w < D16 / 2; ++w) {
+          const uint32_t hh = sm.yh[u * LDK + w], ll = sm.yl[u * LDK + w];
+          const float2 fh = __half22float2(*reinterpret_cast<const __half2*>(&hh));
+          const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&ll));
+          const float y0 = fh.x + fl.x, y1 = fh.y + fl.y;
+          y2 = fmaf(y0, y0, fmaf(y1, y1, y2));
         }
+        const double y2u = (double)y2 * (double)icsc * (double)icsc;
         if (hk) {
-          H = (float)(s * (double)hk[j] - s * (double)y2);
+          H = (float)(s * (double)hk[j] - s * y2u);
           mult = mk ? mk[j] : 1.f;
         } else {
           const float lw = l2w[j];
           if (lw > 0.5f * kZeroW) {
             const double pj = pot ? (double)pot[j] : 0.0;
-            H = (float)((double)lw + s * (pj + sh) - s * (double)y2);
+            H = (float)((double)lw + s * (pj + sh) - s * y2u);
             mult = mk ? mk[j] : 1.f;
           }
         }
       }
-      kH[u] = H;
-      kM[u] = mult;
+      sm.kH[u] = H;
+      sm.kM[u] = mult;
+    }
+    for (int idx = threadIdx.x; idx < D16 * (kKeys / 2); idx += kThreads) {
+      const int d = idx / (kKeys / 2), w = idx - d * (kKeys / 2);
+      float z[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int u = 2 * w + k;
+        const float mult = (u < cnt) ? (mk ? mk[jt + u] : 1.f) * zsc : 0.f;
+        const __half* ph = reinterpret_cast<const __half*>(sm.yh + u * LDK);
+        const __half* pl = reinterpret_cast<const __half*>(sm.yl + u * LDK);
+        z[k] = mult * (__half2float(ph[d]) + __half2float(pl[d]));
+      }
+      uint32_t hi, lo;
+      split_pack(z[0], z[1], hi, lo);
+      sm.zh[d * kLdT + w] = hi;
+      sm.zl[d * kLdT + w] = lo;
     }
     __syncthreads();
-    // S = X.Y^T on 16 rows x 64 keys per warp
+    // S = X.Y^T on 16 rows x 64 keys per warp (K-steps outside: one step's A fragments live)
     float c[kKeys / 8][4];
 #pragma unroll
-    for (int nb = 0; nb < kKeys / 8; ++nb) {
-      c[nb][0] = c[nb][1] = c[nb][2] = c[nb][3] = 0.f;
+    for (int nb = 0; nb < kKeys / 8; ++nb) c[nb][0] = c[nb][1] = c[nb][2] = c[nb][3] = 0.f;
 #pragma unroll
-      for (int ks = 0; ks < kDMax / 8; ++ks) {
-        if (ks * 8 < dim8) {
-          const int key = nb * 8 + g;
-          const uint32_t bh0 = khi[key * kLd + ks * 8 + tg], bh1 = khi[key * kLd + ks * 8 + tg + 4];
-          const uint32_t bl0 = klo[key * kLd + ks * 8 + tg], bl1 = klo[key * kLd + ks * 8 + tg + 4];
-          mma_tf32(c[nb], alo[ks][0], alo[ks][1], alo[ks][2], alo[ks][3], bh0, bh1);
-          mma_tf32(c[nb], ahi[ks][0], ahi[ks][1], ahi[ks][2], ahi[ks][3], bl0, bl1);
-          mma_tf32(c[nb], ahi[ks][0], ahi[ks][1], ahi[ks][2], ahi[ks][3], bh0, bh1);
-        }
+    for (int ks = 0; ks < KS; ++ks) {
+      const uint32_t ah0 = xhA[8 * ks + t], ah1 = xhB[8 * ks + t], ah2 = xhA[8 * ks + 4 + t], ah3 = xhB[8 * ks + 4 + t];
+      const uint32_t al0 = xlA[8 * ks + t], al1 = xlB[8 * ks + t], al2 = xlA[8 * ks + 4 + t], al3 = xlB[8 * ks + 4 + t];
+#pragma unroll
+      for (int nb = 0; nb < kKeys / 8; ++nb) {
+        const uint32_t* yh = sm.yh + (8 * nb + g) * LDK;
+        const uint32_t* yl = sm.yl + (8 * nb + g) * LDK;
+        const uint32_t bh0 = yh[8 * ks + t], bh1 = yh[8 * ks + 4 + t];
+        const uint32_t bl0 = yl[8 * ks + t], bl1 = yl[8 * ks + 4 + t];
+        mma16(c[nb], ah0, ah1, ah2, ah3, bh0, bh1);
+        mma16(c[nb], al0, al1, al2, al3, bh0, bh1);
+        mma16(c[nb], ah0, ah1, ah2, ah3, bl0, bl1);
       }
     }
     float tmA = kInitMax, tmB = kInitMax;
 #pragma unroll
     for (int nb = 0; nb < kKeys / 8; ++nb) {
-      const float H0 = kH[nb * 8 + 2 * tg], H1 = kH[nb * 8 + 2 * tg + 1];
+      const float H0 = sm.kH[8 * nb + 2 * t], H1 = sm.kH[8 * nb + 2 * t + 1];
       c[nb][0] = fmaf(s2, c[nb][0], H0);
       c[nb][1] = fmaf(s2, c[nb][1], H1);
       c[nb][2] = fmaf(s2, c[nb][2], H0);
@@ -192,61 +281,67 @@ k_sweep_flash(const float* __restrict__ q, int nq, const float* __restrict__ kp,
     const float scA = ex2f(mu[0] - mA), scB = ex2f(mu[1] - mB);
     float sA = acc[0] * scA, sB = acc[1] * scB;
 #pragma unroll
-    for (int db = 0; db < kDMax / 8; ++db) {
+    for (int db = 0; db < 2 * KS; ++db) {
       o[db][0] *= scA; o[db][1] *= scA;
       o[db][2] *= scB; o[db][3] *= scB;
     }
-    // P (weighted exponentials) in place of S, then O += P.Y with the key order (2 tg, 2 tg + 1)
+    // P in place of S (weights in [0, 1]); the sums carry the multipliers, O carries them in Z
 #pragma unroll
     for (int nb = 0; nb < kKeys / 8; ++nb) {
-      const float M0 = kM[nb * 8 + 2 * tg], M1 = kM[nb * 8 + 2 * tg + 1];
-      c[nb][0] = M0 * ex2f(c[nb][0] - mA);
-      c[nb][1] = M1 * ex2f(c[nb][1] - mA);
-      c[nb][2] = M0 * ex2f(c[nb][2] - mB);
-      c[nb][3] = M1 * ex2f(c[nb][3] - mB);
-      sA += c[nb][0] + c[nb][1];
-      sB += c[nb][2] + c[nb][3];
-      uint32_t ph[4], pl[4];
-      split_tf32(c[nb][0], ph[0], pl[0]);  // (row g,     key 2 tg)     -> a0
-      split_tf32(c[nb][2], ph[1], pl[1]);  // (row g + 8, key 2 tg)     -> a1
-      split_tf32(c[nb][1], ph[2], pl[2]);  // (row g,     key 2 tg + 1) -> a2
-      split_tf32(c[nb][3], ph[3], pl[3]);  // (row g + 8, key 2 tg + 1) -> a3
-      const int k0 = nb * 8 + 2 * tg, k1 = k0 + 1;
+      const float M0 = sm.kM[8 * nb + 2 * t], M1 = sm.kM[8 * nb + 2 * t + 1];
+      c[nb][0] = ex2f(c[nb][0] - mA);
+      c[nb][1] = ex2f(c[nb][1] - mA);
+      c[nb][2] = ex2f(c[nb][2] - mB);
+      c[nb][3] = ex2f(c[nb][3] - mB);
+      sA = fmaf(M0, c[nb][0], fmaf(M1, c[nb][1], sA));
+      sB = fmaf(M0, c[nb][2], fmaf(M1, c[nb][3], sB));
+    }
+    // O += P.Z, 16 keys a step: the S accumulators of two 8-key tiles are the A fragment
 #pragma unroll
-      for (int db = 0; db < kDMax / 8; ++db) {
-        if (db * 8 < dim8) {
-          const int d = db * 8 + g;
-          const uint32_t vh0 = khi[k0 * kLd + d], vh1 = khi[k1 * kLd + d];
-          const uint32_t vl0 = klo[k0 * kLd + d], vl1 = klo[k1 * kLd + d];
-          mma_tf32(o[db], pl[0], pl[1], pl[2], pl[3], vh0, vh1);
-          mma_tf32(o[db], ph[0], ph[1], ph[2], ph[3], vl0, vl1);
-          mma_tf32(o[db], ph[0], ph[1], ph[2], ph[3], vh0, vh1);
-        }
+    for (int kk = 0; kk < kKeys / 16; ++kk) {
+      uint32_t ph[4], pl[4];
+      split_pack(c[2 * kk][0], c[2 * kk][1], ph[0], pl[0]);
+      split_pack(c[2 * kk][2], c[2 * kk][3], ph[1], pl[1]);
+      split_pack(c[2 * kk + 1][0], c[2 * kk + 1][1], ph[2], pl[2]);
+      split_pack(c[2 * kk + 1][2], c[2 * kk + 1][3], ph[3], pl[3]);
+#pragma unroll
+      for (int db = 0; db < 2 * KS; ++db) {
+        const uint32_t* zh = sm.zh + (8 * db + g) * kLdT;
+        const uint32_t* zl = sm.zl + (8 * db + g) * kLdT;
+        const uint32_t bh0 = zh[8 * kk + t], bh1 = zh[8 * kk + 4 + t];
+        const uint32_t bl0 = zl[8 * kk + t], bl1 = zl[8 * kk + 4 + t];
+        mma16(o[db], ph[0], ph[1], ph[2], ph[3], bh0, bh1);
+        mma16(o[db], pl[0], pl[1], pl[2], pl[3], bh0, bh1);
+        mma16(o[db], ph[0], ph[1], ph[2], ph[3], bl0, bl1);
       }
     }
     mu[0] = mA; mu[1] = mB;
     acc[0] = sA; acc[1] = sB;
   }
-  acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-  acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
-  acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], 1);
-  acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], 2);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
+    acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 2);
+  }
   const int CH = 2 + dim;
   float* base = part + (size_t)split * CH * nq;
-  if (tg == 0) {
+  if (t == 0) {
     if (rA < nq) { base[rA] = mu[0] + Rr[0]; base[(size_t)nq + rA] = acc[0]; }
     if (rB < nq) { base[rB] = mu[1] + Rr[1]; base[(size_t)nq + rB] = acc[1]; }
   }
-  // moments: momscale (x_i acc - O_i), each (row, dim) held by one thread of the quad
+  // moments: momscale (x'_d sum_j P_ij mult_j - O_d 2^-(e + k)), each (row, coordinate) on one thread of the quad
+  const float osc = icsc * izsc;
 #pragma unroll
-  for (int db = 0; db < kDMax / 8; ++db) {
+  for (int db = 0; db < 2 * KS; ++db) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int d = db * 8 + 2 * tg + h;
+      const int d = db * 8 + 2 * t + h;
       if (d < dim) {
         const float cd = center[d];
-        if (rA < nq) base[(size_t)(2 + d) * nq + rA] = momscale * fmaf(q[(size_t)rA * dim + d] - cd, acc[0], -o[db][h]);
-        if (rB < nq) base[(size_t)(2 + d) * nq + rB] = momscale * fmaf(q[(size_t)rB * dim + d] - cd, acc[1], -o[db][2 + h]);
+        if (rA < nq)
+          base[(size_t)(2 + d) * nq + rA] = momscale * fmaf(q[(size_t)rA * dim + d] - cd, acc[0], -o[db][h] * osc);
+        if (rB < nq)
+          base[(size_t)(2 + d) * nq + rB] = momscale * fmaf(q[(size_t)rB * dim + d] - cd, acc[1], -o[db][2 + h] * osc);
       }
     }
   }
@@ -268,8 +363,6 @@ __global__ void k_center(const float* x, int n, const float* y, int m, int dim, 
   if (threadIdx.x == 0) center[d] = (float)(sh[0] / (double)(n + m));
 }
 
-size_t flash_smem_bytes() { return sizeof(uint32_t) * 2 * kKeys * kLd + sizeof(float) * 2 * kKeys; }
-
 }  // namespace
 
 cudaError_t launch_center(const float* x, int n, const float* y, int m, int dim, float* center, cudaStream_t st) {
@@ -278,14 +371,14 @@ cudaError_t launch_center(const float* x, int n, const float* y, int m, int dim,
   return cudaGetLastError();
 }
 
-// One CTA of 8 warps per SM at most (the kernel holds ~200 registers a thread):
-// key chunks so that row blocks x chunks fill the SMs.
+// Two CTAs of 8 warps per SM (about 128 registers a thread): key chunks so
+// that row blocks x chunks fill them.
 SweepGeom flash_geom(int nq, int nk) {
   SweepGeom g{};
   g.threads = kThreads;
   g.rows = 1;
   g.row_blocks = (nq + kRows - 1) / kRows;
-  const long long target = device_sm_count();
+  const long long target = 2LL * device_sm_count();
   const int max_tiles = (nk + kKeys - 1) / kKeys;
   double best = 1e300;
   int best_k = 1;
@@ -304,22 +397,36 @@ SweepGeom flash_geom(int nq, int nk) {
   return g;
 }
 
-cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
-                               const float* l2w, const float* pot, const double* shift, const float* zrow,
-                               const float* hk, const float* mk, double s, float momscale, float* part,
-                               const SweepGeom& g, cudaStream_t st) {
-  static bool attr_set = false;
-  const size_t smem = flash_smem_bytes();
+namespace {
+template <int KS>
+cudaError_t run_flash(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
+                      const int* maxbits, const float* l2w, const float* pot, const double* shift, const float* zrow,
+                      const float* hk, const float* mk, double s, float momscale, float* part, const SweepGeom& g,
+                      cudaStream_t st) {
+  const size_t smem = sizeof(FlashSmem<KS>);
+  static bool attr_set = false;  // per instantiation
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_flash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(k_sweep_flash<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid(g.row_blocks, g.splits);
-  k_sweep_flash<<<grid, kThreads, smem, st>>>(q, nq, kp, nk, dim, center, l2w, pot, shift, zrow, hk, mk, s, momscale,
-                                              g.keys_per_split, part);
+  k_sweep_flash<KS><<<grid, kThreads, smem, st>>>(q, nq, kp, nk, dim, center, maxbits, l2w, pot, shift, zrow, hk,
+                                                  mk, s, momscale, g.keys_per_split, part);
   note_launch();
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
+                               const int* maxbits, const float* l2w, const float* pot, const double* shift,
+                               const float* zrow, const float* hk, const float* mk, double s, float momscale,
+                               float* part, const SweepGeom& g, cudaStream_t st) {
+  if (dim < 17 || dim > 64) return cudaErrorInvalidValue;
+  const int KS = (dim + 15) / 16;
+  if (KS == 2) return run_flash<2>(q, nq, kp, nk, dim, center, maxbits, l2w, pot, shift, zrow, hk, mk, s, momscale, part, g, st);
+  if (KS == 3) return run_flash<3>(q, nq, kp, nk, dim, center, maxbits, l2w, pot, shift, zrow, hk, mk, s, momscale, part, g, st);
+  return run_flash<4>(q, nq, kp, nk, dim, center, maxbits, l2w, pot, shift, zrow, hk, mk, s, momscale, part, g, st);
 }
 
 }  // namespace uot

@@ -396,8 +396,8 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
       // gradient sweep with moments: dC/dx = 2 (x - y)
       SweepGeom g = flash_geom(q.n, k.n);
       *splits = g.splits;
-      UOT_CUDA(launch_flash_sweep(q.pts, q.n, k.pts, k.n, p.dim, c.center, k.l2w, pot, shift, nullptr, nullptr,
-                                  nullptr, c.s, 2.0f, part, g, c.st));
+      UOT_CUDA(launch_flash_sweep(q.pts, q.n, k.pts, k.n, p.dim, c.center, c.op_sc, k.l2w, pot, shift, nullptr,
+                                  nullptr, nullptr, c.s, 2.0f, part, g, c.st));
     } else {
       SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
       if ((size_t)g.splits * (2 + (moments ? p.dim : 0)) * q.n > cap) g = points_geom(q.n, k.n, p.dim, moments, false);
@@ -903,13 +903,13 @@ uot_status grad_unrolled(const uot_problem* prob, int T, int K, double* value, f
       UOT_CUDA(launch_bw_f1(p.n, p.dim, fbb, fhat, c.ln_a, rec + 3, sums + 2, kf, r1, a1, G, ga, gx, Sb, c.blk, ctr,
                             sums + 3, c.st));
       UOT_CUDA(launch_bw_smin_init(p.m, gbarn, c.ln_b, rec + 2, r2, -b1, sums + 3, gbb, gb, c.st));
-      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, ctr_c, c.st));
+      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, ctr_c, c.op_sc, c.st));
       UOT_CUDA(launch_bw_adj(p.m, p.dim, val, mom, c.ln_b, eps, gbb, gb, gy, c.blk, ctr, sums + 4, c.st));
       // g half-step of iteration t+1
       UOT_CUDA(launch_bw_g1(p.m, p.dim, gbb, ghat, c.ln_b, rec + 1, sums + 4, kg, r2, a2, Gp, gb, gy, Spb, c.blk, ctr,
                             sums + 5, c.st));
       UOT_CUDA(launch_bw_fset(p.n, fbar, c.ln_a, rec + 0, r1, -b2, sums + 5, fbb, ga, c.st));
-      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, ctr_c, c.st));
+      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, ctr_c, c.op_sc, c.st));
       UOT_CUDA(launch_bw_adj(p.n, p.dim, val, mom, c.ln_a, eps, fbb, ga, gx, c.blk, ctr, sums + 2, c.st));
     }
   }

@@ -210,10 +210,12 @@ cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4
 // momscale = 2.  Adjoint sweep: zrow = the query potential, hk = the keys' h,
 // mk = the keys' signed cotangents, momscale = 1.
 SweepGeom flash_geom(int nq, int nk);
+// maxbits: the largest |x - c| over both clouds as float bits (the tcgen05 path's
+// scale, computed once per call), for the power-of-two scale of the FP16 split.
 cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
-                               const float* l2w, const float* pot, const double* shift, const float* zrow,
-                               const float* hk, const float* mk, double s, float momscale, float* part,
-                               const SweepGeom& g, cudaStream_t st);
+                               const int* maxbits, const float* l2w, const float* pot, const double* shift,
+                               const float* zrow, const float* hk, const float* mk, double s, float momscale,
+                               float* part, const SweepGeom& g, cudaStream_t st);
 // tcgen05 sweep (dim >= 32, p = 2): the operand matrices of both clouds (split
 // FP16 coordinates relative to the common centre, scaled by a power of two
 // from the largest |x - c| in *maxbits, canonical K-major layout, rows padded
@@ -368,7 +370,7 @@ SweepGeom adjoint_geom(int nq, int nk);
 // center != null (dim >= 32): the sweep runs on the tensor cores (flash sweep).
 cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int dim, const float* pot_q,
                            const float* h_k, const float* c_k, double s, float* part, double* val, double* mom,
-                           const float* center, cudaStream_t st);
+                           const float* center, const int* maxbits, cudaStream_t st);
 cudaError_t launch_add_scalar(const float* u, const double* c, int n, float* v, cudaStream_t st);
 cudaError_t launch_moments(const float* part, int nq, int dim, int splits, double scale, float* G, cudaStream_t st);
 cudaError_t launch_final_side(const float* part, int CH, int nq, int splits, double s, double eps, double rho,
