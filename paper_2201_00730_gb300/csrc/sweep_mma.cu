@@ -86,7 +86,21 @@ struct FlashSmem {
   uint32_t zh[16 * KS * kLdT], zl[16 * KS * kLdT];  // Z 2^(e+k), coordinate-major (pairs of keys), hi / lo
   float kH[kKeys], kM[kKeys];
   float red[kWarps];
+  float cen[16 * KS];
+  // the next key tile, copied ahead (cp.async) while the current one computes:
+  // coordinates (row-major, dim a key) and the per-key scalars l2w, pot, hk, mk
+  float raw[kKeys * 16 * KS];
+  float rs[4][kKeys];
 };
+
+__device__ __forceinline__ void cp4(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g)
+               : "memory");
+}
 
 // One CTA: 128 query rows (8 warps of 16) against the keys [split kps, + kps).
 template <int KS>
@@ -130,6 +144,28 @@ k_sweep_flash(const float* __restrict__ q, int nq, const float* __restrict__ kp,
   }
   const float zsc = p2f(kz), izsc = p2f(-kz);
 
+  for (int d = threadIdx.x; d < D16; d += kThreads) sm.cen[d] = d < dim ? center[d] : 0.f;
+  // copies of key tile [jn, jn + 64) into raw / rs (the caller commits and waits)
+  const bool al16 = ((reinterpret_cast<uintptr_t>(kp) & 15u) == 0) && ((dim & 3) == 0);
+  auto issue = [&](int jn) {
+    const int cn = min(kKeys, j1 - jn);
+    const float* src = kp + (size_t)jn * dim;
+    const int nf = cn * dim;
+    if (al16) {
+      for (int k = threadIdx.x; k < (nf >> 2); k += kThreads) cp16(sm.raw + 4 * k, src + 4 * k);
+    } else {
+      for (int k = threadIdx.x; k < nf; k += kThreads) cp4(sm.raw + k, src + k);
+    }
+    if ((int)threadIdx.x < cn) {
+      const int j = jn + threadIdx.x;
+      if (l2w) cp4(&sm.rs[0][threadIdx.x], l2w + j);
+      if (pot) cp4(&sm.rs[1][threadIdx.x], pot + j);
+      if (hk) cp4(&sm.rs[2][threadIdx.x], hk + j);
+      if (mk) cp4(&sm.rs[3][threadIdx.x], mk + j);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (j0 < j1) issue(j0);
   // the CTA's rows: X' 2^e split, row-major, pairs of coordinates per word (the A fragments of
   // S = X.Y^T are read from here: rows g and g + 8 of a warp's 16, coordinates (2t, 2t+1) and
   // (2t+8, 2t+9) of a 16-coordinate step)
@@ -180,15 +216,16 @@ k_sweep_flash(const float* __restrict__ q, int nq, const float* __restrict__ kp,
 
   for (int jt = j0; jt < j1; jt += kKeys) {
     const int cnt = min(kKeys, j1 - jt);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     // Y' 2^e split, key-major, pairs of coordinates per word
     for (int u2 = threadIdx.x; u2 < kKeys * (D16 / 2); u2 += kThreads) {
       const int u = u2 / (D16 / 2), w = u2 - u * (D16 / 2), d = 2 * w;
       float v0 = 0.f, v1 = 0.f;
       if (u < cnt) {
-        const float* kr = kp + (size_t)(jt + u) * dim;
-        if (d < dim) v0 = (kr[d] - center[d]) * csc;
-        if (d + 1 < dim) v1 = (kr[d + 1] - center[d + 1]) * csc;
+        const float* kr = sm.raw + u * dim;
+        if (d < dim) v0 = (kr[d] - sm.cen[d]) * csc;
+        if (d + 1 < dim) v1 = (kr[d + 1] - sm.cen[d + 1]) * csc;
       }
       uint32_t hi, lo;
       split_pack(v0, v1, hi, lo);
@@ -210,29 +247,31 @@ k_sweep_flash(const float* __restrict__ q, int nq, const float* __restrict__ kp,
           const float y0 = fh.x + fl.x, y1 = fh.y + fl.y;
           y2 = fmaf(y0, y0, fmaf(y1, y1, y2));
         }
+        (void)j;
         const double y2u = (double)y2 * (double)icsc * (double)icsc;
         if (hk) {
-          H = (float)(s * (double)hk[j] - s * y2u);
-          mult = mk ? mk[j] : 1.f;
+          H = (float)(s * (double)sm.rs[2][u] - s * y2u);
+          mult = mk ? sm.rs[3][u] : 1.f;
         } else {
-          const float lw = l2w[j];
+          const float lw = sm.rs[0][u];
           if (lw > 0.5f * kZeroW) {
-            const double pj = pot ? (double)pot[j] : 0.0;
+            const double pj = pot ? (double)sm.rs[1][u] : 0.0;
             H = (float)((double)lw + s * (pj + sh) - s * y2u);
-            mult = mk ? mk[j] : 1.f;
+            mult = mk ? sm.rs[3][u] : 1.f;
           }
         }
       }
       sm.kH[u] = H;
       sm.kM[u] = mult;
     }
+    // coordinates fastest: the reads of Y' are consecutive halves
     for (int idx = threadIdx.x; idx < D16 * (kKeys / 2); idx += kThreads) {
-      const int d = idx / (kKeys / 2), w = idx - d * (kKeys / 2);
+      const int w = idx / D16, d = idx - w * D16;
       float z[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int u = 2 * w + k;
-        const float mult = (u < cnt) ? (mk ? mk[jt + u] : 1.f) * zsc : 0.f;
+        const float mult = (u < cnt) ? (mk ? sm.rs[3][u] : 1.f) * zsc : 0.f;
         const __half* ph = reinterpret_cast<const __half*>(sm.yh + u * LDK);
         const __half* pl = reinterpret_cast<const __half*>(sm.yl + u * LDK);
         z[k] = mult * (__half2float(ph[d]) + __half2float(pl[d]));
@@ -243,6 +282,8 @@ k_sweep_flash(const float* __restrict__ q, int nq, const float* __restrict__ kp,
       sm.zl[d * kLdT + w] = lo;
     }
     __syncthreads();
+    // raw and rs are free (read before the barrier): copy the next tile while this one computes
+    if (jt + kKeys < j1) issue(jt + kKeys);
     // S = X.Y^T on 16 rows x 64 keys per warp (K-steps outside: one step's A fragments live)
     float c[kKeys / 8][4];
 #pragma unroll
