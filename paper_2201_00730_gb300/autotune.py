@@ -154,6 +154,8 @@ def default_workloads(quick: bool = False):
         items.append(("tiled", W.config2(1.0, n=n)))
     items.append(("direct", W.random_problem(8192, 8192, 3, seed=41, eps=1e-2)))
     items.append(("dense", W.random_problem(4096, 6144, 2, seed=42, eps=5e-2)))
+    if not quick:
+        items.append(("dense", W.config2(1.0)))  # the 1.6 GB cost of the headline problem
     return items
 
 
