@@ -87,19 +87,20 @@ __device__ __forceinline__ void merge_rows(const float* part, int CH, int nq, in
 // ref[r] (fixed-reference sweeps): the maxima are ref and the merge is a plain
 // sum of the chunks' sums, in the same order and with the same result as
 // merge_rows, without the maxima's loads and the rescaling exponentials.
-template <int R>
+// G chunks' loads are issued together (one round trip per G chunks).
+template <int R, int G = 8>
 __device__ __forceinline__ void merge_rows_ref(const float* part, int CH, int nq, int splits, const int (&idx)[R],
                                                const float (&ref)[R], float (&Mo)[R], float (&Lo)[R]) {
   const size_t stride = (size_t)CH * nq;
   float S[R], C[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) { S[r] = 0.f; C[r] = 0.f; }
-  for (int k0 = 0; k0 < splits; k0 += 8) {
-    float sv[R][8];
+  for (int k0 = 0; k0 < splits; k0 += G) {
+    float sv[R][G];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < G; ++u) {
         const int k = k0 + u;
         sv[r][u] = (k < splits && idx[r] >= 0) ? __ldcg(part + (size_t)k * stride + (size_t)nq + idx[r]) : 0.f;
       }
@@ -107,7 +108,7 @@ __device__ __forceinline__ void merge_rows_ref(const float* part, int CH, int nq
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) simd::neu_add(S[r], C[r], sv[r][u]);
+      for (int u = 0; u < G; ++u) simd::neu_add(S[r], C[r], sv[r][u]);
     }
   }
 #pragma unroll

@@ -256,7 +256,7 @@ k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp,
       pre[r] = epi::prefetch(e, idx[r]);
     }
     float Mg[R], Lg[R];
-    if (use_ref) epi::merge_rows_ref<R>(part, 2, nq, gridDim.y, idx, M, Mg, Lg);
+    if (use_ref) epi::merge_rows_ref<R, 16>(part, 2, nq, gridDim.y, idx, M, Mg, Lg);
     else epi::merge_rows<R>(part, 2, nq, gridDim.y, idx, Mg, Lg);
     if (use_ref) {
       // rows whose log-sum-exp left the window around the reference are listed,
