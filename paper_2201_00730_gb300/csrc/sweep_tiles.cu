@@ -48,10 +48,10 @@ constexpr int kTilesPerStage = kStageKeys / kTileKeys;
 constexpr int kPairsPerStage = kStageKeys / 2;
 constexpr int kPairsPerTile = kTileKeys / 2;
 
-// R = 2 is limited to 64 registers so that 4 CTAs (32 warps) share an SM; on
-// GB300 that hides the ex2 / FMA latency chains better than more registers.
+// R = 2 is limited to 80 registers so that 3 CTAs (24 warps) share an SM (at 64
+// registers and 4 CTAs it spilled); R = 4 takes up to 128 registers, 2 CTAs.
 template <int D, int R, bool EPI>
-__global__ void __launch_bounds__(kThreads, (R == 2 ? 4 : 2))
+__global__ void __launch_bounds__(kThreads, (R == 2 ? 3 : 2))
 k_sweep_tiles(const float* __restrict__ q, int nq, const float* __restrict__ kp, int nk,
               const float4* __restrict__ centers, const float* __restrict__ l2w, const float* __restrict__ pot,
               const double* __restrict__ shift, double s, int kps, float* __restrict__ part, EpiParams e) {
@@ -377,7 +377,7 @@ SweepGeom tile_geom(int nq, int nk, int dim, bool tuned) {
   const int sms = device_sm_count();
   const long long entries = (long long)nq * nk;
   // 4 rows per thread (half the shared-memory loads per entry, 2 CTAs of 128
-  // registers per SM) once there are a few row blocks; 2 rows (4 CTAs of 64
+  // registers per SM) once there are a few row blocks; 2 rows (3 CTAs of 80
   // registers per SM) for small query sets, where more CTAs balance better
   int R = (nq >= 4096) ? 4 : 2;
   if (tuned) R = (int)tune_value("tile.rows", dim, entries, R);
