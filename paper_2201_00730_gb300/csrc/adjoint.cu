@@ -131,11 +131,12 @@ SweepGeom adjoint_geom(int nq, int nk) {
 
 cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int dim, const float* pot_q,
                            const float* h_k, const float* c_k, double s, float* part, double* val, double* mom,
-                           const float* center, const int* maxbits, cudaStream_t st) {
+                           const float* center, const int* maxbits, const MomOperands& mo, cudaStream_t st) {
   if (center && dim >= 32) {
-    const SweepGeom gf = flash_geom(nq, nk);
-    cudaError_t e = launch_flash_sweep(q, nq, kp, nk, dim, center, maxbits, nullptr, nullptr, nullptr, pot_q, h_k, c_k,
-                                       s, 1.0f, part, gf, st);
+    const SweepGeom gf = mom_geom(nq, nk);
+    cudaError_t e = launch_mom_sweep(mo.opq, mo.nq2, nq, mo.opk, mo.nk2, nk, q, kp, dim, center, maxbits, nullptr,
+                                     nullptr, nullptr, pot_q, h_k, c_k, s, 1.0f, mo.zt, mo.multbits, part, gf,
+                                     mo.status, st);
     if (e != cudaSuccess) return e;
     k_adjoint_merge<<<dim3((nq + 255) / 256, dim + 1), 256, 0, st>>>(part, nq, dim, gf.splits, val, mom);
     note_launch();

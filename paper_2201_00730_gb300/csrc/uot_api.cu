@@ -123,6 +123,8 @@ PartSizes part_sizes(const uot_problem& p) {
       upd(ps.cols, (size_t)umma_geom(p.m, p.n).splits * 2 * p.m);
       upd(ps.rows, (size_t)flash_geom(p.n, p.m).splits * (2 + p.dim) * p.n);
       upd(ps.cols, (size_t)flash_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
+      upd(ps.rows, (size_t)mom_geom(p.n, p.m).splits * (2 + p.dim) * p.n);
+      upd(ps.cols, (size_t)mom_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
     }
   } else {
     for (long long ch : tune_allowed("dense.row_chunk")) {
@@ -144,6 +146,7 @@ PartSizes part_sizes(const uot_problem& p) {
 struct WsLayout {
   size_t state, ln_a, ln_b, l2_a, l2_b, lo_a, lo_b, g_alt, f_tmp, g_tmp, part_r, part_c, blk, rbc, center;
   size_t op_x, op_y, n2_x, n2_y, op_sc;  // tcgen05 operands of the dim >= 32 path (empty otherwise)
+  size_t zt, zsc;                        // Z^T operand scratch of its moment sweeps
   // ordering of the tiled path (empty otherwise)
   size_t perm_x, perm_y, xs, ys, as, bs, fs, gs, cen_x, cen_y, blk_f, box, code_in, code_out, idx_in, sort_tmp;
   size_t sort_tmp_bytes, total;
@@ -175,6 +178,8 @@ WsLayout ws_layout(const uot_problem& p) {
     L.n2_x = take(sizeof(float) * p.n);
     L.n2_y = take(sizeof(float) * p.m);
     L.op_sc = take(sizeof(int));
+    L.zt = take(mom_zt_bytes(p.n > p.m ? p.n : p.m, p.dim));
+    L.zsc = take(sizeof(int));
   }
   if (tiled_path(p)) {
     const int nmax = p.n > p.m ? p.n : p.m;
@@ -210,6 +215,8 @@ struct Ctx {
   float* center;      // common centre of the clouds (tensor-core path)
   float *op_x, *op_y, *n2_x, *n2_y;  // tcgen05 operands and squared norms (dim >= 32)
   int* op_sc;                        // their power-of-two scale (largest |x - c|, as float bits)
+  void* zt;                          // Z^T operand of the moment sweeps
+  int* zsc;                          // its multiplier scale (largest |mult|, as float bits)
   cudaStream_t st;
   double s;  // log2(e) / eps
   // tiled path: clouds in Morton order (px..pb point at the sorted copies)
@@ -263,12 +270,16 @@ uot_status make_ctx(const uot_problem* prob, void* ws, size_t ws_bytes, void* st
   c->center = reinterpret_cast<float*>(b + L.center);
   c->op_x = c->op_y = c->n2_x = c->n2_y = nullptr;
   c->op_sc = nullptr;
+  c->zt = nullptr;
+  c->zsc = nullptr;
   if (mma_path(*prob)) {
     c->op_x = reinterpret_cast<float*>(b + L.op_x);
     c->op_y = reinterpret_cast<float*>(b + L.op_y);
     c->n2_x = reinterpret_cast<float*>(b + L.n2_x);
     c->n2_y = reinterpret_cast<float*>(b + L.n2_y);
     c->op_sc = reinterpret_cast<int*>(b + L.op_sc);
+    c->zt = b + L.zt;
+    c->zsc = reinterpret_cast<int*>(b + L.zsc);
   }
   c->st = static_cast<cudaStream_t>(stream);
   c->s = kLog2e / prob->eps;
@@ -394,10 +405,12 @@ uot_status sweep_inner(Ctx& c, int axis, const float* pot, const double* shift, 
                                  shift, c.s, c.op_sc, part, g, &c.state->status, c.st));
     } else if (mma_path(p)) {
       // gradient sweep with moments: dC/dx = 2 (x - y)
-      SweepGeom g = flash_geom(q.n, k.n);
+      SweepGeom g = mom_geom(q.n, k.n);
       *splits = g.splits;
-      UOT_CUDA(launch_flash_sweep(q.pts, q.n, k.pts, k.n, p.dim, c.center, c.op_sc, k.l2w, pot, shift, nullptr,
-                                  nullptr, nullptr, c.s, 2.0f, part, g, c.st));
+      UOT_CUDA(launch_mom_sweep(axis == 0 ? c.op_x : c.op_y, axis == 0 ? c.n2_x : c.n2_y, q.n,
+                                axis == 0 ? c.op_y : c.op_x, axis == 0 ? c.n2_y : c.n2_x, k.n, q.pts, k.pts, p.dim,
+                                c.center, c.op_sc, k.l2w, pot, shift, nullptr, nullptr, nullptr, c.s, 2.0f, c.zt, c.zsc,
+                                part, g, &c.state->status, c.st));
     } else {
       SweepGeom g = points_geom(q.n, k.n, p.dim, moments);
       if ((size_t)g.splits * (2 + (moments ? p.dim : 0)) * q.n > cap) g = points_geom(q.n, k.n, p.dim, moments, false);
@@ -903,13 +916,15 @@ uot_status grad_unrolled(const uot_problem* prob, int T, int K, double* value, f
       UOT_CUDA(launch_bw_f1(p.n, p.dim, fbb, fhat, c.ln_a, rec + 3, sums + 2, kf, r1, a1, G, ga, gx, Sb, c.blk, ctr,
                             sums + 3, c.st));
       UOT_CUDA(launch_bw_smin_init(p.m, gbarn, c.ln_b, rec + 2, r2, -b1, sums + 3, gbb, gb, c.st));
-      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, ctr_c, c.op_sc, c.st));
+      UOT_CUDA(launch_adjoint(p.y, p.m, p.x, p.n, p.dim, gbarn, S, Sb, c.s, adj, val, mom, ctr_c, c.op_sc,
+                              MomOperands{c.op_y, c.n2_y, c.op_x, c.n2_x, c.zt, c.zsc, &c.state->status}, c.st));
       UOT_CUDA(launch_bw_adj(p.m, p.dim, val, mom, c.ln_b, eps, gbb, gb, gy, c.blk, ctr, sums + 4, c.st));
       // g half-step of iteration t+1
       UOT_CUDA(launch_bw_g1(p.m, p.dim, gbb, ghat, c.ln_b, rec + 1, sums + 4, kg, r2, a2, Gp, gb, gy, Spb, c.blk, ctr,
                             sums + 5, c.st));
       UOT_CUDA(launch_bw_fset(p.n, fbar, c.ln_a, rec + 0, r1, -b2, sums + 5, fbb, ga, c.st));
-      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, ctr_c, c.op_sc, c.st));
+      UOT_CUDA(launch_adjoint(p.x, p.n, p.y, p.m, p.dim, fbar, Sp, Spb, c.s, adj, val, mom, ctr_c, c.op_sc,
+                              MomOperands{c.op_x, c.n2_x, c.op_y, c.n2_y, c.zt, c.zsc, &c.state->status}, c.st));
       UOT_CUDA(launch_bw_adj(p.n, p.dim, val, mom, c.ln_a, eps, fbb, ga, gx, c.blk, ctr, sums + 2, c.st));
     }
   }

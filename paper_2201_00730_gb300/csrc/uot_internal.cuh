@@ -210,6 +210,27 @@ cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4
 // momscale = 2.  Adjoint sweep: zrow = the query potential, hk = the keys' h,
 // mk = the keys' signed cotangents, momscale = 1.
 SweepGeom flash_geom(int nq, int nk);
+// Moment / adjoint sweep on tcgen05 (dim >= 32, p = 2; sweep_umma_mom.cu): the
+// plain tcgen05 sweep's operands and squared norms of the query (opq, nq2) and
+// key (opk, nk2) clouds, the points themselves, the moment channels of
+// launch_flash_sweep's partial layout; zt (mom_zt_bytes of the key cloud) and
+// multbits (one int) are scratch for the Z^T operand.
+struct MomOperands {
+  const void* opq;
+  const float* nq2;
+  const void* opk;
+  const float* nk2;
+  void* zt;
+  int* multbits;
+  int* status;
+};
+size_t mom_zt_bytes(int n, int dim);
+SweepGeom mom_geom(int nq, int nk);
+cudaError_t launch_mom_sweep(const void* opq, const float* nq2, int nq, const void* opk, const float* nk2, int nk,
+                             const float* q, const float* kp, int dim, const float* center, const int* maxbits,
+                             const float* l2w, const float* pot, const double* shift, const float* zrow,
+                             const float* hk, const float* mk, double s, float momscale, void* zt, int* multbits,
+                             float* part, const SweepGeom& g, int* status, cudaStream_t st);
 // maxbits: the largest |x - c| over both clouds as float bits (the tcgen05 path's
 // scale, computed once per call), for the power-of-two scale of the FP16 split.
 cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
@@ -370,7 +391,7 @@ SweepGeom adjoint_geom(int nq, int nk);
 // center != null (dim >= 32): the sweep runs on the tensor cores (flash sweep).
 cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int dim, const float* pot_q,
                            const float* h_k, const float* c_k, double s, float* part, double* val, double* mom,
-                           const float* center, const int* maxbits, cudaStream_t st);
+                           const float* center, const int* maxbits, const struct MomOperands& mo, cudaStream_t st);
 cudaError_t launch_add_scalar(const float* u, const double* c, int n, float* v, cudaStream_t st);
 cudaError_t launch_moments(const float* part, int nq, int dim, int splits, double scale, float* G, cudaStream_t st);
 cudaError_t launch_final_side(const float* part, int CH, int nq, int splits, double s, double eps, double rho,
