@@ -121,8 +121,6 @@ PartSizes part_sizes(const uot_problem& p) {
     if (mma_path(p)) {
       upd(ps.rows, (size_t)umma_geom(p.n, p.m).splits * 2 * p.n);
       upd(ps.cols, (size_t)umma_geom(p.m, p.n).splits * 2 * p.m);
-      upd(ps.rows, (size_t)flash_geom(p.n, p.m).splits * (2 + p.dim) * p.n);
-      upd(ps.cols, (size_t)flash_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
       upd(ps.rows, (size_t)mom_geom(p.n, p.m).splits * (2 + p.dim) * p.n);
       upd(ps.cols, (size_t)mom_geom(p.m, p.n).splits * (2 + p.dim) * p.m);
     }
@@ -727,7 +725,7 @@ URLayout ur_layout(const uot_problem& p, int T, int K) {
   size_t ap = (size_t)a1.splits * (2 + D) * M;
   if ((size_t)a2.splits * (2 + D) * N > ap) ap = (size_t)a2.splits * (2 + D) * N;
   if (mma_path(p)) {
-    const SweepGeom b1 = flash_geom(p.m, p.n), b2 = flash_geom(p.n, p.m);
+    const SweepGeom b1 = mom_geom(p.m, p.n), b2 = mom_geom(p.n, p.m);
     if ((size_t)b1.splits * (2 + D) * M > ap) ap = (size_t)b1.splits * (2 + D) * M;
     if ((size_t)b2.splits * (2 + D) * N > ap) ap = (size_t)b2.splits * (2 + D) * N;
   }

@@ -204,17 +204,14 @@ SweepGeom tile_geom(int nq, int nk, int dim, bool tuned = true);
 cudaError_t launch_tile_sweep(const SideDesc& q, const SideDesc& k, const float4* centers_k, int dim,
                               const float* pot_k, const double* shift_k, double s, float* part, const SweepGeom& g,
                               const struct EpiParams* epi, cudaStream_t st);
-// Tensor-core sweep with moments (dim >= 32, p = 2): partials [splits][2 + dim][nq]
-// (max, sum of mult_j 2^(t - max), momscale * the moments of (x_i - y_j)).
-// Forward gradient sweep: l2w, pot, shift of the keys, zrow = hk = mk = null,
-// momscale = 2.  Adjoint sweep: zrow = the query potential, hk = the keys' h,
-// mk = the keys' signed cotangents, momscale = 1.
-SweepGeom flash_geom(int nq, int nk);
-// Moment / adjoint sweep on tcgen05 (dim >= 32, p = 2; sweep_umma_mom.cu): the
-// plain tcgen05 sweep's operands and squared norms of the query (opq, nq2) and
-// key (opk, nk2) clouds, the points themselves, the moment channels of
-// launch_flash_sweep's partial layout; zt (mom_zt_bytes of the key cloud) and
-// multbits (one int) are scratch for the Z^T operand.
+// Moment / adjoint sweep on tcgen05 (dim >= 32, p = 2; sweep_umma_mom.cu):
+// partials [splits][2 + dim][nq] (max, sum of mult_j 2^(t - max), momscale *
+// the moments of (x_i - y_j)).  Forward gradient sweep: l2w, pot, shift of the
+// keys, zrow = hk = mk = null, momscale = 2.  Adjoint sweep: zrow = the query
+// potential, hk = the keys' h, mk = the keys' signed cotangents, momscale = 1.
+// opq / nq2 and opk / nk2: the plain tcgen05 sweep's operands and squared norms
+// of the query and key clouds; zt (mom_zt_bytes of the key cloud) and multbits
+// (one int) are scratch for the Z^T operand.
 struct MomOperands {
   const void* opq;
   const float* nq2;
@@ -231,12 +228,6 @@ cudaError_t launch_mom_sweep(const void* opq, const float* nq2, int nq, const vo
                              const float* l2w, const float* pot, const double* shift, const float* zrow,
                              const float* hk, const float* mk, double s, float momscale, void* zt, int* multbits,
                              float* part, const SweepGeom& g, int* status, cudaStream_t st);
-// maxbits: the largest |x - c| over both clouds as float bits (the tcgen05 path's
-// scale, computed once per call), for the power-of-two scale of the FP16 split.
-cudaError_t launch_flash_sweep(const float* q, int nq, const float* kp, int nk, int dim, const float* center,
-                               const int* maxbits, const float* l2w, const float* pot, const double* shift,
-                               const float* zrow, const float* hk, const float* mk, double s, float momscale,
-                               float* part, const SweepGeom& g, cudaStream_t st);
 // tcgen05 sweep (dim >= 32, p = 2): the operand matrices of both clouds (split
 // FP16 coordinates relative to the common centre, scaled by a power of two
 // from the largest |x - c| in *maxbits, canonical K-major layout, rows padded
@@ -388,7 +379,7 @@ cudaError_t launch_grad_epilogue(const GradParams& gp, cudaStream_t st);
 
 // ---- unrolled backward (adjoint.cu, unrolled.cu) -----------------------------
 SweepGeom adjoint_geom(int nq, int nk);
-// center != null (dim >= 32): the sweep runs on the tensor cores (flash sweep).
+// center != null (dim >= 32): the sweep runs on the tensor cores (tcgen05 moment sweep).
 cudaError_t launch_adjoint(const float* q, int nq, const float* kp, int nk, int dim, const float* pot_q,
                            const float* h_k, const float* c_k, double s, float* part, double* val, double* mom,
                            const float* center, const int* maxbits, const struct MomOperands& mo, cudaStream_t st);
