@@ -287,7 +287,8 @@ UOT_API uot_status uot_dual_value(const uot_problem* prob, const float* f, const
  *   grad_b_j = rho2 (1 - e^{-g_j/rho2}) - eps (e^{(g_j - S'_j)/eps} - m(a)), S' = Smin_a^eps(C - f)
  *   grad_x_i = sum_j pi_ij dC_ij/dx_i,   grad_y_j = sum_i pi_ij dC_ij/dy_j,
  * with pi formed on the fly and never stored.  Each output pointer may be NULL
- * (not computed); grad_x / grad_y need the points cost.  Asynchronous. */
+ * (not computed); grad_x / grad_y need the points cost.  Asynchronous (nothing is read back: for dim >=
+ * 32 a bounded tensor-core wait that gives up leaves NaN in the gradients). */
 UOT_API uot_status uot_grad(const uot_problem* prob, const float* f, const float* g, float* grad_a,
                     float* grad_b, float* grad_x, float* grad_y, void* ws, size_t ws_bytes,
                     void* stream);
