@@ -28,6 +28,7 @@
 
 #include <mutex>
 
+#include "ffloat.cuh"
 #include "sweep_common.cuh"
 #include "tc_ptx.cuh"
 #include "uot_internal.cuh"
@@ -200,18 +201,24 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
       copy_pieces(reinterpret_cast<char*>(B) + (size_t)t * bytesB,
                   reinterpret_cast<const char*>(opk) + (size_t)((t0 + t) % TT) * bytesB, bytesB, &br.b_full[t]);
   }
-  // key constants H_j = h_j - s |y'_j|^2 of the CTA's key tiles (zero-weight and padding keys: kZeroW)
-  for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
-    const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
-    float H = kZeroW;
-    if (j < nk) {
-      const float lw = l2w[j];
-      if (lw > 0.5f * kZeroW) {
-        const double pj = pot ? (double)pot[j] : 0.0;
-        H = (float)((double)lw + s * (pj + sh) - s * (double)nk2[j]);
+  // key constants H_j = h_j - s |y'_j|^2 of the CTA's key tiles (zero-weight and padding keys: kZeroW),
+  // in float pairs (about 44 bits, then rounded once to FP32): FP64 here, at the FP64 rate of this
+  // GPU, took a third of the sweep
+  {
+    const ffl::ff s_ff = ffl::from_double(s), sh_ff = ffl::from_double(sh);
+    for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
+      const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
+      float H = kZeroW;
+      if (j < nk) {
+        const float lw = l2w[j];
+        if (lw > 0.5f * kZeroW) {
+          const ffl::ff sp = ffl::mul(ffl::add(sh_ff, pot ? pot[j] : 0.f), s_ff);
+          const ffl::ff h = ffl::add(ffl::add(sp, ffl::neg(ffl::mul(s_ff, nk2[j]))), lw);
+          H = h.hi + h.lo;
+        }
       }
+      Hs[u] = H;
     }
-    Hs[u] = H;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -226,6 +233,26 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
       for (int t = 0; t < L && t < kStages; ++t) armed[t] = 1;
       int a_armed = 1, a_used = 0;
       int committed = -1, reused = -1;  // tiles committed; MMAs of tiles <= reused known complete
+      // pend: the last committed tile whose key stage is not yet refilled.  The refill (tile pend +
+      // kStages into stage pend % kStages) waits only for the MMAs of tile pend; it is polled while
+      // the next tile's MMAs are issued, so that the copy starts as soon as those MMAs complete.
+      int pend = -1;
+      auto refill = [&](int tp) {
+        reused = tp > reused ? tp : reused;
+        if (tp + kStages < L) {
+          const int rs = tp % kStages;
+          copy_pieces(reinterpret_cast<char*>(B) + (size_t)rs * bytesB,
+                      reinterpret_cast<const char*>(opk) + (size_t)((t0 + tp + kStages) % TT) * bytesB, bytesB,
+                      &br.b_full[rs]);
+          ++armed[rs];
+        }
+      };
+      auto poll = [&]() {
+        if (pend >= 0 && tc::mbar_test(&br.m_done[pend % kAcc], (uint32_t)((pend / kAcc) & 1))) {
+          refill(pend);
+          pend = -1;
+        }
+      };
       // descriptors: one K-step (16 values: two 16-byte core-matrix columns, 256 bytes) adds 16 to the
       // start field, the lo parts start dim16 / 8 core-matrix columns (16 KS in the field) further
       const uint64_t dAh = tc::smem_desc(tc::smem_addr(A), 128, sbo);
@@ -241,11 +268,13 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
               *err = 1;
               break;
             }
+            if (pend == t - 1) { refill(pend); pend = -1; }
             reused = t - 1;
             copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb * bytesA, bytesA, &br.a_full);
             ++a_armed;
           }
         }
+        poll();
         bool ok = true;
         if (a_used < a_armed) {
           ok = tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), spin);
@@ -263,22 +292,20 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
         // hi.hi, then lo.hi (lo parts of x), then hi.lo (lo parts of y)
 #pragma unroll
         for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBh + 16 * k, kIdesc, k > 0);
+        poll();
 #pragma unroll
         for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAl + 16 * k, dBh + 16 * k, kIdesc, true);
+        poll();
 #pragma unroll
         for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBl + 16 * k, kIdesc, true);
         tc::commit(&br.m_done[b]);
         committed = t;
-        // key stage of unit t - 1 -> unit t - 1 + kStages, once the MMAs of unit t - 1 completed
-        if (t >= 1 && t - 1 + kStages < L) {
-          if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), spin)) { *err = 1; break; }
-          reused = t - 1;
-          const int rs = (t - 1) % kStages;
-          copy_pieces(reinterpret_cast<char*>(B) + (size_t)rs * bytesB,
-                      reinterpret_cast<const char*>(opk) + (size_t)((t0 + t - 1 + kStages) % TT) * bytesB, bytesB,
-                      &br.b_full[rs]);
-          ++armed[rs];
+        // the refill still pending must be issued before the next tile waits for its stage
+        if (pend >= 0) {
+          if (!tc::mbar_wait(&br.m_done[pend % kAcc], (uint32_t)((pend / kAcc) & 1), spin)) { *err = 1; break; }
+          refill(pend);
         }
+        pend = t;
       }
       if (*err) {
         // drain: copies armed but never consumed, MMAs committed but never seen complete (bounded)
@@ -306,8 +333,11 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
       if (t > 0 && ++tile == TT) { tile = 0; ++rb; }
       if (!dead) {
         const int b = t % kAcc;
-        bool done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), spin);
-        done = __all_sync(0xffffffffu, done);  // tcgen05.ld is warp-wide
+        // one lane polls the barrier (sixteen warps of pollers slow every shared-memory access of the
+        // issuer); the warp-synchronous broadcast orders the others' tcgen05.ld after it
+        bool done = false;
+        if (lane == 0) done = !*err && tc::mbar_wait(&br.m_done[b], (uint32_t)((t / kAcc) & 1), spin);
+        done = __shfl_sync(0xffffffffu, done ? 1 : 0, 0) != 0;  // tcgen05.ld is warp-wide
         if (!done) {
           if (lane == 0) *err = 1;
           dead = true;

@@ -25,6 +25,7 @@
 
 #include <mutex>
 
+#include "ffloat.cuh"
 #include "sweep_common.cuh"
 #include "tc_ptx.cuh"
 #include "uot_internal.cuh"
@@ -208,25 +209,32 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
     tc::fence_mbar_init();
     br.err = 0;
   }
-  // key constants and multipliers of the CTA's key tiles (zero weight and padding: kZeroW, 0)
-  for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
-    const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
-    float H = kZeroW, m = 0.f;
-    if (j < nk) {
-      if (hk) {
-        H = (float)(s * (double)hk[j] - s * (double)nk2[j]);
-        m = mk ? mk[j] : 1.f;
-      } else {
-        const float lw = l2w[j];
-        if (lw > 0.5f * kZeroW) {
-          const double pj = pot ? (double)pot[j] : 0.0;
-          H = (float)((double)lw + s * (pj + sh) - s * (double)nk2[j]);
+  // key constants and multipliers of the CTA's key tiles (zero weight and padding: kZeroW, 0), in
+  // float pairs (about 44 bits, rounded once to FP32; FP64 here is slow on this GPU)
+  {
+    const ffl::ff s_ff = ffl::from_double(s), sh_ff = ffl::from_double(sh);
+    for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
+      const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
+      float H = kZeroW, m = 0.f;
+      if (j < nk) {
+        const ffl::ff sn = ffl::neg(ffl::mul(s_ff, nk2[j]));
+        if (hk) {
+          const ffl::ff h = ffl::add(ffl::mul(s_ff, hk[j]), sn);
+          H = h.hi + h.lo;
           m = mk ? mk[j] : 1.f;
+        } else {
+          const float lw = l2w[j];
+          if (lw > 0.5f * kZeroW) {
+            const ffl::ff sp = ffl::mul(ffl::add(sh_ff, pot ? pot[j] : 0.f), s_ff);
+            const ffl::ff h = ffl::add(ffl::add(sp, sn), lw);
+            H = h.hi + h.lo;
+            m = mk ? mk[j] : 1.f;
+          }
         }
       }
+      Hs[u] = H;
+      Ms[u] = m;
     }
-    Hs[u] = H;
-    Ms[u] = m;
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -57,3 +57,32 @@ def test_wait_that_gives_up_reports_timeout_and_context_survives(U, kind):
     ref = O.ti_sinkhorn(O.cost_matrix(p.x, p.y), p.a, p.b, p.eps, p.rho1, p.rho2, T)
     err = (r.f.double().cpu() - ref.f).abs()
     assert bool((err <= 1e-4 * p.eps + 2 * 2.0 ** -23 * ref.f.abs()).all()), err.max().item()
+
+
+def test_gradient_wait_that_gives_up_leaves_nan_and_context_survives(U):
+    """uot_grad is asynchronous: when a bounded wait of the tensor-core moment sweep
+    (dim >= 32) gives up, the spatial gradients come back NaN rather than wrong but finite,
+    and the next call on the same context gives the envelope gradients of the oracle."""
+    p = CASES["d64"]()
+    sd = np.sqrt(1.0 / (2.0 * p.x.shape[1]))
+    rng = np.random.default_rng(7)
+    p.x = (sd * rng.standard_normal(p.x.shape)).astype(np.float32)
+    p.y = (sd * rng.standard_normal(p.y.shape)).astype(np.float32)
+    spec = spec_of(U, p)
+    r = U.solve(spec, "ti", max_iter=30, tol=0.0)
+    L = U.lib()
+    L.uot_test_set_wait_limit(-1)
+    try:
+        bad = U.grad(spec, r.f, r.g, wrt=("x", "y"))
+        torch.cuda.synchronize()
+    finally:
+        L.uot_test_set_wait_limit(0)
+    assert bool(torch.isnan(bad["x"]).any()) and bool(torch.isnan(bad["y"]).any())
+    torch.cuda.synchronize()  # nothing faulted
+    gr = U.grad(spec, r.f, r.g)
+    ea, eb, ex, ey = O.envelope_grads(p.x, p.y, p.a, p.b, r.f.double().cpu(), r.g.double().cpu(),
+                                      p.eps, p.rho1, p.rho2)
+    for k, e in (("a", ea), ("b", eb), ("x", ex), ("y", ey)):
+        assert bool(torch.isfinite(gr[k]).all()), k
+        rel = ((gr[k].double().cpu() - e).norm() / e.norm()).item()
+        assert rel < 1e-4, (k, rel)
