@@ -120,11 +120,14 @@ __global__ void k_umma_operand(const float* __restrict__ pts, int n, int npad, i
 
 struct Bars {
   uint64_t a_full;
+  uint64_t a_free;            // the MMAs of a row block's last tile completed (A may be replaced)
   uint64_t b_full[kStages];   // key stage landed (bulk copies)
+  uint64_t b_free[kStages];   // the MMAs that read a key stage completed
   uint64_t m_done[kAcc];      // the MMAs of an accumulator completed
-  uint64_t empty[kAcc];       // the 8 consumer warps read an accumulator
+  uint64_t empty[kAcc];       // the consumer warps read an accumulator
   uint32_t tmem;
   int err;
+  float s_hi, s_lo, sh_hi, sh_lo, s2;  // s and the potential shift as float pairs; s 2^-2e
   float hm[2][3][kRows];      // column quarters 1..3: (max, sum) per row, by segment parity
   float hs[2][3][kRows];
 };
@@ -144,15 +147,18 @@ __host__ __device__ __forceinline__ long long cta_of_unit(long long x, long long
 
 // Roles: warps 0..15 read the accumulators (warp w: TMEM lane quarter w % 4,
 // i.e. rows 32 (w % 4) .. + 31, and column quarter w / 4 of every tile, one
-// 64-column TMEM load a tile); lane 0 of warp 16 issues the copies and the
-// MMAs.  Handoffs: a_full (query rows
-// landed), b_full (key tiles landed), m_done (MMAs -> consumers and the
-// issuer, which then reuses the key stage, or the query rows at a row-block
-// change), empty (consumers -> issuer, accumulator free again).  Every wait
-// is bounded; a wait that gives up sets err, which stops every role, and the
-// issuer then lets every copy and MMA in flight land before the CTA ends.
+// 64-column TMEM load a tile); lane 0 of warp 16 issues the MMAs; lane 0 of
+// warp 17 issues the copies.  Handoffs: a_full / b_full (query rows / key
+// tile landed: producer -> MMA), a_free / b_free (the MMAs that read them
+// completed: MMA -> producer, which refills them), m_done (MMAs ->
+// consumers), empty (consumers -> MMA, accumulator free again).  The two
+// single-thread roles are kept apart so that neither waits behind the other's
+// waits.  Every wait is bounded; a wait that gives up sets err, which stops
+// every role, and each issuing role then lets its own copies or MMAs in flight
+// land before the CTA ends.
 constexpr int kConsWarps = 16;
-constexpr int kAllThreads = 32 * (kConsWarps + 1);
+constexpr int kMmaWarp = kConsWarps, kCopyWarp = kConsWarps + 1;
+constexpr int kAllThreads = 32 * (kConsWarps + 2);
 
 // Work units are the pairs (row block of 128 queries, key tile of 256 keys),
 // numbered row-block-major, U = row blocks x TT of them; CTA c of the G in
@@ -183,105 +189,124 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
   const int rb0 = (int)(u0 / TT), t0 = (int)(u0 % TT);
   // H slots: slot v holds key tile (t0 + v) % TT, and unit u0 + t reads slot t % TT
   const int nslot = L < TT ? L : TT;
-  const float s2 = (float)(2.0 * s * pow2d(-2 * scale_exp(*maxbits)));  // products carry 2^2e
-  const double sh = shift ? *shift : 0.0;
-
   if (warp == 0) tc::tmem_alloc(&br.tmem, kTmemCols);
-  if (tid == 32 * kConsWarps) {
+  if (tid == 32 * kMmaWarp) {
     tc::mbar_init(&br.a_full, 1);
-    for (int b = 0; b < kStages; ++b) tc::mbar_init(&br.b_full[b], 1);
+    tc::mbar_init(&br.a_free, 1);
+    for (int b = 0; b < kStages; ++b) {
+      tc::mbar_init(&br.b_full[b], 1);
+      tc::mbar_init(&br.b_free[b], 1);
+    }
     for (int b = 0; b < kAcc; ++b) {
       tc::mbar_init(&br.m_done[b], 1);
       tc::mbar_init(&br.empty[b], kConsWarps);
     }
     tc::fence_mbar_init();
     br.err = 0;
+    // the CTA's FP64 work (slow on this GPU), done once: s and the shift as float pairs
+    const double sh = shift ? *shift : 0.0;
+    br.s_hi = (float)s;
+    br.s_lo = (float)(s - (double)br.s_hi);
+    br.sh_hi = (float)sh;
+    br.sh_lo = (float)(sh - (double)br.sh_hi);
+    br.s2 = (float)(2.0 * s * pow2d(-2 * scale_exp(*maxbits)));  // products carry 2^2e
+  }
+  // key constants H_j = h_j - s |y'_j|^2 of the CTA's key tiles (zero-weight and padding keys: kZeroW),
+  // in float pairs (about 44 bits, then rounded once to FP32); all of a thread's loads are issued
+  // before the barrier, so that they take one L2 round trip
+  constexpr int kPer = (kMaxChunk + kAllThreads - 1) / kAllThreads;
+  const int nu = nslot * kKeys;
+  float lw[kPer], pj[kPer], n2[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int u = tid + k * kAllThreads;
+    const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
+    const bool in = u < nu && j < nk;
+    lw[k] = in ? l2w[j] : kZeroW;
+    pj[k] = (in && pot) ? pot[j] : 0.f;
+    n2[k] = in ? nk2[j] : 0.f;
+  }
+  __syncthreads();  // barriers initialised, constants written
+  if (tid == 32 * kCopyWarp) {
+    // the first copies start before the key constants are computed
     copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb0 * bytesA, bytesA, &br.a_full);
     for (int t = 0; t < L && t < kStages; ++t)
       copy_pieces(reinterpret_cast<char*>(B) + (size_t)t * bytesB,
                   reinterpret_cast<const char*>(opk) + (size_t)((t0 + t) % TT) * bytesB, bytesB, &br.b_full[t]);
   }
-  // key constants H_j = h_j - s |y'_j|^2 of the CTA's key tiles (zero-weight and padding keys: kZeroW),
-  // in float pairs (about 44 bits, then rounded once to FP32): FP64 here, at the FP64 rate of this
-  // GPU, took a third of the sweep
   {
-    const ffl::ff s_ff = ffl::from_double(s), sh_ff = ffl::from_double(sh);
-    for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
-      const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
-      float H = kZeroW;
-      if (j < nk) {
-        const float lw = l2w[j];
-        if (lw > 0.5f * kZeroW) {
-          const ffl::ff sp = ffl::mul(ffl::add(sh_ff, pot ? pot[j] : 0.f), s_ff);
-          const ffl::ff h = ffl::add(ffl::add(sp, ffl::neg(ffl::mul(s_ff, nk2[j]))), lw);
+    const ffl::ff s_ff{br.s_hi, br.s_lo}, sh_ff{br.sh_hi, br.sh_lo};
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int u = tid + k * kAllThreads;
+      if (u < nu) {
+        float H = kZeroW;
+        if (lw[k] > 0.5f * kZeroW) {
+          const ffl::ff sp = ffl::mul(ffl::add(sh_ff, pj[k]), s_ff);
+          const ffl::ff h = ffl::add(ffl::add(sp, ffl::neg(ffl::mul(s_ff, n2[k]))), lw[k]);
           H = h.hi + h.lo;
         }
+        Hs[u] = H;
       }
-      Hs[u] = H;
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = br.tmem;
+  const float s2 = br.s2, s_f = br.s_hi;
   volatile int* err = &br.err;
 
-  if (warp == kConsWarps) {
-    // ------------------------------------------------------------------ issuer
+  if (warp == kCopyWarp) {
+    // --------------------------------------------------------------- producer
     if (lane == 0) {
-      int armed[kStages] = {}, used[kStages] = {};
+      int armed[kStages] = {}, a_armed = 1, nfree = 0;
       for (int t = 0; t < L && t < kStages; ++t) armed[t] = 1;
-      int a_armed = 1, a_used = 0;
-      int committed = -1, reused = -1;  // tiles committed; MMAs of tiles <= reused known complete
-      // pend: the last committed tile whose key stage is not yet refilled.  The refill (tile pend +
-      // kStages into stage pend % kStages) waits only for the MMAs of tile pend; it is polled while
-      // the next tile's MMAs are issued, so that the copy starts as soon as those MMAs complete.
-      int pend = -1;
-      auto refill = [&](int tp) {
-        reused = tp > reused ? tp : reused;
-        if (tp + kStages < L) {
-          const int rs = tp % kStages;
-          copy_pieces(reinterpret_cast<char*>(B) + (size_t)rs * bytesB,
-                      reinterpret_cast<const char*>(opk) + (size_t)((t0 + tp + kStages) % TT) * bytesB, bytesB,
-                      &br.b_full[rs]);
-          ++armed[rs];
+      int rb = rb0, tile = t0;
+      for (int t = 1; t < L && !*err; ++t) {
+        if (++tile == TT) { tile = 0; ++rb; }
+        if (tile == 0) {
+          // next row block: its rows replace A once the MMAs of the previous row block completed
+          if (!tc::mbar_wait(&br.a_free, (uint32_t)(nfree & 1), spin)) { *err = 1; break; }
+          ++nfree;
+          copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb * bytesA, bytesA, &br.a_full);
+          ++a_armed;
         }
-      };
-      auto poll = [&]() {
-        if (pend >= 0 && tc::mbar_test(&br.m_done[pend % kAcc], (uint32_t)((pend / kAcc) & 1))) {
-          refill(pend);
-          pend = -1;
+        if (t >= kStages) {
+          // key tile t goes to stage t % kStages once the MMAs of tile t - kStages completed
+          const int st = t % kStages;
+          if (!tc::mbar_wait(&br.b_free[st], (uint32_t)(((t - kStages) / kStages) & 1), spin)) { *err = 1; break; }
+          copy_pieces(reinterpret_cast<char*>(B) + (size_t)st * bytesB,
+                      reinterpret_cast<const char*>(opk) + (size_t)((t0 + t) % TT) * bytesB, bytesB,
+                      &br.b_full[st]);
+          ++armed[st];
         }
-      };
+      }
+      // this role's copies land before the CTA ends, whoever stopped (each barrier's latest phase;
+      // immediate when the MMAs consumed them; bounded)
+      (void)tc::mbar_wait(&br.a_full, (uint32_t)((a_armed - 1) & 1), kSpin);
+      for (int st = 0; st < kStages; ++st)
+        if (armed[st] > 0) (void)tc::mbar_wait(&br.b_full[st], (uint32_t)((armed[st] - 1) & 1), kSpin);
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    // -------------------------------------------------------------------- MMA
+    if (lane == 0) {
+      int committed = -1;
       // descriptors: one K-step (16 values: two 16-byte core-matrix columns, 256 bytes) adds 16 to the
       // start field, the lo parts start dim16 / 8 core-matrix columns (16 KS in the field) further
       const uint64_t dAh = tc::smem_desc(tc::smem_addr(A), 128, sbo);
       const uint64_t dAl = dAh + (uint64_t)(KS * 16);
-      int rb = rb0, tile = t0;
+      int tile = t0, a_used = 0;
       for (int t = 0; t < L && !*err; ++t) {
         const int st = t % kStages, b = t % kAcc;
-        if (t > 0) {
-          if (++tile == TT) { tile = 0; ++rb; }
-          if (tile == 0) {
-            // next row block: its rows replace A once the MMAs of tile t - 1, the last to read A, completed
-            if (!tc::mbar_wait(&br.m_done[(t - 1) % kAcc], (uint32_t)(((t - 1) / kAcc) & 1), spin)) {
-              *err = 1;
-              break;
-            }
-            if (pend == t - 1) { refill(pend); pend = -1; }
-            reused = t - 1;
-            copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)rb * bytesA, bytesA, &br.a_full);
-            ++a_armed;
-          }
-        }
-        poll();
+        if (t > 0 && ++tile == TT) tile = 0;
         bool ok = true;
-        if (a_used < a_armed) {
+        if (t == 0 || tile == 0) {
           ok = tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), spin);
-          if (ok) ++a_used;
+          ++a_used;
         }
         ok = ok && tc::mbar_wait(&br.b_full[st], (uint32_t)((t / kStages) & 1), spin);
-        if (ok) ++used[st];
         // accumulator b was last read for tile t - kAcc
         ok = ok && (t < kAcc || tc::mbar_wait(&br.empty[b], (uint32_t)(((t - kAcc) / kAcc) & 1), spin));
         if (!ok) { *err = 1; break; }
@@ -292,33 +317,19 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
         // hi.hi, then lo.hi (lo parts of x), then hi.lo (lo parts of y)
 #pragma unroll
         for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBh + 16 * k, kIdesc, k > 0);
-        poll();
 #pragma unroll
         for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAl + 16 * k, dBh + 16 * k, kIdesc, true);
-        poll();
 #pragma unroll
         for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBl + 16 * k, kIdesc, true);
         tc::commit(&br.m_done[b]);
+        tc::commit(&br.b_free[st]);
+        if (tile == TT - 1 || t == L - 1) tc::commit(&br.a_free);
         committed = t;
-        // the refill still pending must be issued before the next tile waits for its stage
-        if (pend >= 0) {
-          if (!tc::mbar_wait(&br.m_done[pend % kAcc], (uint32_t)((pend / kAcc) & 1), spin)) { *err = 1; break; }
-          refill(pend);
-        }
-        pend = t;
       }
-      if (*err) {
-        // drain: copies armed but never consumed, MMAs committed but never seen complete (bounded)
-        for (; a_used < a_armed; ++a_used) (void)tc::mbar_wait(&br.a_full, (uint32_t)(a_used & 1), kSpin);
-        for (int st = 0; st < kStages; ++st)
-          for (; used[st] < armed[st]; ++used[st])
-            (void)tc::mbar_wait(&br.b_full[st], (uint32_t)(used[st] & 1), kSpin);
-        for (int t = reused + 1; t <= committed; ++t) {
-          // only the most recent commit of each accumulator: wait for that phase
-          if (t + kAcc <= committed) continue;
-          (void)tc::mbar_wait(&br.m_done[t % kAcc], (uint32_t)((t / kAcc) & 1), kSpin);
-        }
-      }
+      // the MMAs committed complete before the CTA ends, whoever stopped (the latest phase of each
+      // accumulator; immediate when the consumers saw them; bounded)
+      for (int t = committed - kAcc + 1; t <= committed; ++t)
+        if (t >= 0) (void)tc::mbar_wait(&br.m_done[t % kAcc], (uint32_t)((t / kAcc) & 1), kSpin);
     }
     __syncwarp();
   } else {
@@ -403,7 +414,7 @@ k_sweep_umma(const __half* __restrict__ opq, const float* __restrict__ nq2, int 
             const int slot = (int)((long long)blockIdx.x - cta_of_unit((long long)rb * TT, U, G));
             float* base = part + (size_t)slot * 2 * nq;
             const bool bad = *err != 0;
-            base[i] = bad ? __int_as_float(0x7fc00000) : mn - (float)s * nq2[i];
+            base[i] = bad ? __int_as_float(0x7fc00000) : mn - s_f * nq2[i];
             base[(size_t)nq + i] = bad ? __int_as_float(0x7fc00000) : St;
             if (tile == TT - 1)
               for (int k = slot + 1; k < splits; ++k) {

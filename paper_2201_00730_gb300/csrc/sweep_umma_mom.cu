@@ -211,29 +211,44 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
   }
   // key constants and multipliers of the CTA's key tiles (zero weight and padding: kZeroW, 0), in
   // float pairs (about 44 bits, rounded once to FP32; FP64 here is slow on this GPU)
+  // (all of a thread's loads are issued before any is used: one L2 round trip, not one a key)
   {
     const ffl::ff s_ff = ffl::from_double(s), sh_ff = ffl::from_double(sh);
-    for (int u = tid; u < nslot * kKeys; u += kAllThreads) {
+    constexpr int kPer = (kMaxChunk + kAllThreads - 1) / kAllThreads;
+    const int nu = nslot * kKeys;
+    float hw[kPer], pj[kPer], n2[kPer], mm[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int u = tid + k * kAllThreads;
       const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
-      float H = kZeroW, m = 0.f;
-      if (j < nk) {
-        const ffl::ff sn = ffl::neg(ffl::mul(s_ff, nk2[j]));
-        if (hk) {
-          const ffl::ff h = ffl::add(ffl::mul(s_ff, hk[j]), sn);
-          H = h.hi + h.lo;
-          m = mk ? mk[j] : 1.f;
-        } else {
-          const float lw = l2w[j];
-          if (lw > 0.5f * kZeroW) {
-            const ffl::ff sp = ffl::mul(ffl::add(sh_ff, pot ? pot[j] : 0.f), s_ff);
-            const ffl::ff h = ffl::add(ffl::add(sp, sn), lw);
+      const bool in = u < nu && j < nk;
+      hw[k] = in ? (hk ? hk[j] : l2w[j]) : kZeroW;  // hk_j, or log2 w_j
+      pj[k] = (in && !hk && pot) ? pot[j] : 0.f;
+      n2[k] = in ? nk2[j] : 0.f;
+      mm[k] = (in && mk) ? mk[j] : 1.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int u = tid + k * kAllThreads;
+      if (u < nu) {
+        const int j = ((t0 + u / kKeys) % TT) * kKeys + u % kKeys;
+        float H = kZeroW, m = 0.f;
+        if (j < nk) {
+          const ffl::ff sn = ffl::neg(ffl::mul(s_ff, n2[k]));
+          if (hk) {
+            const ffl::ff h = ffl::add(ffl::mul(s_ff, hw[k]), sn);
             H = h.hi + h.lo;
-            m = mk ? mk[j] : 1.f;
+            m = mm[k];
+          } else if (hw[k] > 0.5f * kZeroW) {
+            const ffl::ff sp = ffl::mul(ffl::add(sh_ff, pj[k]), s_ff);
+            const ffl::ff h = ffl::add(ffl::add(sp, sn), hw[k]);
+            H = h.hi + h.lo;
+            m = mm[k];
           }
         }
+        Hs[u] = H;
+        Ms[u] = m;
       }
-      Hs[u] = H;
-      Ms[u] = m;
     }
   }
   tc::fence_before_sync();
