@@ -1,16 +1,17 @@
 // 1-D unregularised UOT by Frank-Wolfe on H_0 (Sec. 4, Alg. 2), batched: one
-// warp per problem; FP64 except the walk's potentials (float pairs).  Per step
-// the warp computes
+// warp per problem, in float pairs (about 44 bits: FP64 runs at a small
+// fraction of the FP32 rate on this GPU).  Per step the warp computes
 //   lambda* = rho1 rho2 / (rho1 + rho2) (log<a, e^{-fb/rho1}> - log<b, e^{-gb/rho2}>)   (Prop. 2)
 //   a~ = a e^{-(fb + lambda*)/rho1},  b~ = b e^{-(gb - lambda*)/rho2}              (Eq. fw-updated-histo)
-// with all lanes, then lane 0 walks the two sorted point lists once to get the
+// with all lanes (a~ and b~ divided by their common mass, which the walk does
+// not see), then lane 0 walks the two sorted point lists once to get the
 // duals (r, s) of the balanced 1-D OT between a~ and b~ (SolveOT1D, Alg. 1:
 // the point whose remaining mass is smaller is exhausted first, and each newly
 // reached point's potential is the current pair's cost minus the other side's
 // current potential), and all lanes take the step
 //   (fb, gb) <- (1 - gamma_t)(fb, gb) + gamma_t (r, s),  gamma_t = 2 / (2 + t).
-// The walk is sequential by nature (O(N + M) dependent steps, one FP64 add
-// each); the batch supplies the parallelism.  Working vectors live in the
+// The walk is sequential by nature (O(N + M) dependent steps, one float-pair
+// add each); the batch supplies the parallelism.  Working vectors live in the
 // workspace, indexed by the problems' offsets (a~ and b~ in shared memory when
 // the problem is small enough).
 #include <cuda_runtime.h>
@@ -39,22 +40,56 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_max_d(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+
+// float-pair warp reductions (the pair is rounded after each combination)
+__device__ __forceinline__ ffl::ff warp_sum_ff(ffl::ff v) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ffl::add(v, ffl::ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+__device__ __forceinline__ ffl::ff ff_max(ffl::ff a, ffl::ff b) {
+  return (a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo)) ? a : b;
+}
+__device__ __forceinline__ ffl::ff warp_max_ff(ffl::ff v) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_max(v, ffl::ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
   return v;
 }
 
-// log <w, e^{-v / rho}> over the entries with w > 0 (largest exponent taken out first)
-__device__ double log_dot_exp_neg(const float* __restrict__ w, const double* v, int n, double rho, int lane) {
-  double mx = -INFINITY;
+// log2(e) as a float pair
+constexpr double kLog2e = 1.44269504088896340736;
+constexpr ffl::ff kLog2eff{(float)kLog2e, (float)(kLog2e - (double)(float)kLog2e)};
+
+// e^y for a float pair y <= 0 (or of moderate size): 2^(y log2 e)
+__device__ __forceinline__ ffl::ff exp_ff(ffl::ff y) { return ffl::exp2(ffl::mul(y, kLog2eff)); }
+
+// w e^y for w >= 0 and a float pair y with w e^y <= 1 (y itself may be large when w is tiny): the
+// power of two is split off first so that the table exp2 stays within its range
+__device__ __forceinline__ ffl::ff w_exp_ff(float w, ffl::ff y) {
+  ffl::ff z = ffl::mul(y, kLog2eff);
+  float sc = 1.f;
+  if (z.hi > 60.f) {
+    const float k = ceilf(z.hi) - 60.f;  // w 2^k <= 1 since w 2^z <= 1
+    z = ffl::add(z, -k);
+    sc = ffl::pow2f((int)k);
+  }
+  return ffl::mul(ffl::exp2(z), w * sc);
+}
+
+// log <w, e^{-v rinv}> over the entries with w > 0 (largest exponent taken out first), float pairs
+__device__ ffl::ff log_dot_exp_neg(const float* __restrict__ w, const float2* v, int n, ffl::ff rinv, int lane) {
+  ffl::ff mx{-INFINITY, 0.f};
   for (int i = lane; i < n; i += 32)
-    if (w[i] > 0.f) mx = fmax(mx, -v[i] / rho);
-  mx = warp_max_d(mx);
-  double sm = 0.0;
+    if (w[i] > 0.f) mx = ff_max(mx, ffl::neg(ffl::mul(ffl::ff{v[i].x, v[i].y}, rinv)));
+  mx = warp_max_ff(mx);
+  ffl::ff sm{0.f, 0.f};
   for (int i = lane; i < n; i += 32)
-    if (w[i] > 0.f) sm += (double)w[i] * exp(-v[i] / rho - mx);
-  sm = warp_sum_d(sm);
-  return mx + log(sm);
+    if (w[i] > 0.f) {
+      const ffl::ff e = ffl::add(ffl::neg(ffl::mul(ffl::ff{v[i].x, v[i].y}, rinv)), ffl::neg(mx));
+      sm = ffl::add(sm, ffl::mul(exp_ff(e), w[i]));
+    }
+  sm = warp_sum_ff(sm);
+  return ffl::add(mx, ffl::log_ff(sm));
 }
 
 // |x - y|^p as a float pair: x - y exactly (two_sum), then its square (p = 2),
@@ -110,25 +145,51 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
     return;
   }
 
-  for (int i = lane; i < n; i += 32) FB[i] = 0.0;
-  for (int j = lane; j < m; j += 32) GB[j] = 0.0;
+  // working vectors as float pairs (about 44 bits) in the double-sized slots of the workspace: FP64
+  // runs at a small fraction of the FP32 rate on this GPU, and the exponentials of every step were
+  // the kernel's FP64 bound
+  float2 *FB2 = reinterpret_cast<float2*>(FB), *GB2 = reinterpret_cast<float2*>(GB);
+  float2 *AT2 = reinterpret_cast<float2*>(AT), *BT2 = reinterpret_cast<float2*>(BT);
+  for (int i = lane; i < n; i += 32) FB2[i] = make_float2(0.f, 0.f);
+  for (int j = lane; j < m; j += 32) GB2[j] = make_float2(0.f, 0.f);
   __syncwarp();
-  const double r1 = P.rho1, r2 = P.rho2, kappa = r1 * r2 / (r1 + r2);
-  double lam = 0.0;
+  const double r1 = P.rho1, r2 = P.rho2;
+  const ffl::ff ri1 = ffl::from_double(1.0 / r1), ri2 = ffl::from_double(1.0 / r2);
+  const ffl::ff kappa = ffl::from_double(r1 * r2 / (r1 + r2));
+  ffl::ff lam{0.f, 0.f};
   for (int t = 0;; ++t) {
-    lam = kappa * (log_dot_exp_neg(A, FB, n, r1, lane) - log_dot_exp_neg(B, GB, m, r2, lane));
+    const ffl::ff la = log_dot_exp_neg(A, FB2, n, ri1, lane), lb = log_dot_exp_neg(B, GB2, m, ri2, lane);
+    lam = ffl::mul(kappa, ffl::add(la, ffl::neg(lb)));
     if (t == n_iter) break;
-    for (int i = lane; i < n; i += 32) AT[i] = A[i] > 0.f ? (double)A[i] * exp(-(FB[i] + lam) / r1) : 0.0;
-    for (int j = lane; j < m; j += 32) BT[j] = B[j] > 0.f ? (double)B[j] * exp(-(GB[j] - lam) / r2) : 0.0;
+    // a~ and b~ divided by their common mass m (Prop. 1): ln m = la - lambda / rho1.  The walk
+    // depends on the masses only through comparisons of their partial sums, which the common
+    // factor leaves unchanged; it keeps every a~_i, b~_j <= 1
+    const ffl::ff lnm = ffl::add(la, ffl::neg(ffl::mul(lam, ri1)));
+    for (int i = lane; i < n; i += 32) {
+      ffl::ff v{0.f, 0.f};
+      if (A[i] > 0.f) {
+        const ffl::ff e = ffl::add(ffl::neg(ffl::mul(ffl::add(ffl::ff{FB2[i].x, FB2[i].y}, lam), ri1)), ffl::neg(lnm));
+        v = w_exp_ff(A[i], e);
+      }
+      AT2[i] = make_float2(v.hi, v.lo);
+    }
+    for (int j = lane; j < m; j += 32) {
+      ffl::ff v{0.f, 0.f};
+      if (B[j] > 0.f) {
+        const ffl::ff e =
+            ffl::add(ffl::neg(ffl::mul(ffl::add(ffl::ff{GB2[j].x, GB2[j].y}, ffl::neg(lam)), ri2)), ffl::neg(lnm));
+        v = w_exp_ff(B[j], e);
+      }
+      BT2[j] = make_float2(v.hi, v.lo);
+    }
     __syncwarp();
     if (lane == 0) {
       // SolveOT1D, the duals of the north-west corner coupling.  The masses not yet
-      // transported enter only through dm = fl(m_j - m_i): "point i is exhausted first"
-      // is m_i <= m_j, i.e. dm >= 0, and the next dm is fl(dm - a~_{i+1}) after i moves,
-      // fl(dm + b~_{j+1}) after j moves, the same roundings as tracking (m_i, m_j) in FP64,
-      // so the walk takes the same branches with one dependent FP64 add a step.  The
-      // potentials run in float pairs on the FP32 pipes; the next point and mass of both
-      // sides are loaded ahead of each decision.
+      // transported enter only through dm = m_j - m_i: "point i is exhausted first" is
+      // m_i <= m_j, i.e. dm >= 0; the next dm is dm - a~_{i+1} after i moves, dm + b~_{j+1}
+      // after j moves, each a float-pair sum, so the walk takes the oracle's branches except
+      // where dm is within ~1e-13 of a tie.  The potentials run in float pairs; the next point
+      // and mass of both sides are loaded ahead of each decision.
       float2* R2 = reinterpret_cast<float2*>(R);
       float2* S2 = reinterpret_cast<float2*>(S);
       int i = 0, j = 0;
@@ -136,38 +197,48 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
       ffl::ff ri{0.f, 0.f}, sj = cost_ff(xi, yj, p);
       R2[0] = make_float2(0.f, 0.f);
       S2[0] = make_float2(sj.hi, sj.lo);
-      double dm = BT[0] - AT[0];
-      double na = n > 1 ? AT[1] : 0.0, nb = m > 1 ? BT[1] : 0.0;
+      ffl::ff dm = ffl::add(ffl::ff{BT2[0].x, BT2[0].y}, ffl::neg(ffl::ff{AT2[0].x, AT2[0].y}));
+      float2 na = n > 1 ? AT2[1] : make_float2(0.f, 0.f), nb = m > 1 ? BT2[1] : make_float2(0.f, 0.f);
       float nx = n > 1 ? X[1] : 0.f, ny = m > 1 ? Y[1] : 0.f;
       while (i < n - 1 || j < m - 1) {
-        // dm is never -0 (masses are >= +0), so its sign bit decides dm >= 0 without an FP64 compare
-        if ((__double_as_longlong(dm) >= 0 && i < n - 1) || j == m - 1) {
+        // dm >= 0 (its sign is the sign of hi, or of lo when hi is 0)
+        const bool ge = dm.hi > 0.f || (dm.hi == 0.f && dm.lo >= 0.f);
+        if ((ge && i < n - 1) || j == m - 1) {
           ++i;
-          dm -= na;
+          dm = ffl::add(dm, ffl::ff{-na.x, -na.y});
           xi = nx;
-          if (i + 1 < n) { na = AT[i + 1]; nx = X[i + 1]; }
+          if (i + 1 < n) { na = AT2[i + 1]; nx = X[i + 1]; }
           ri = ffl::add(cost_ff(xi, yj, p), ffl::neg(sj));
           R2[i] = make_float2(ri.hi, ri.lo);
         } else {
           ++j;
-          dm += nb;
+          dm = ffl::add(dm, ffl::ff{nb.x, nb.y});
           yj = ny;
-          if (j + 1 < m) { nb = BT[j + 1]; ny = Y[j + 1]; }
+          if (j + 1 < m) { nb = BT2[j + 1]; ny = Y[j + 1]; }
           sj = ffl::add(cost_ff(xi, yj, p), ffl::neg(ri));
           S2[j] = make_float2(sj.hi, sj.lo);
         }
       }
     }
     __syncwarp();
-    const double gm = 2.0 / (2.0 + (double)t);
+    // (fb, gb) <- (1 - gamma) (fb, gb) + gamma (r, s), gamma = 2 / (2 + t)
+    const ffl::ff gm = ffl::from_double(2.0 / (2.0 + (double)t));
+    const ffl::ff g1 = ffl::add(ffl::neg(gm), 1.f);
     const float2* R2 = reinterpret_cast<const float2*>(R);
     const float2* S2 = reinterpret_cast<const float2*>(S);
-    for (int i = lane; i < n; i += 32) FB[i] = (1.0 - gm) * FB[i] + gm * ((double)R2[i].x + (double)R2[i].y);
-    for (int j = lane; j < m; j += 32) GB[j] = (1.0 - gm) * GB[j] + gm * ((double)S2[j].x + (double)S2[j].y);
+    for (int i = lane; i < n; i += 32) {
+      const ffl::ff v = ffl::add(ffl::mul(ffl::ff{FB2[i].x, FB2[i].y}, g1), ffl::mul(ffl::ff{R2[i].x, R2[i].y}, gm));
+      FB2[i] = make_float2(v.hi, v.lo);
+    }
+    for (int j = lane; j < m; j += 32) {
+      const ffl::ff v = ffl::add(ffl::mul(ffl::ff{GB2[j].x, GB2[j].y}, g1), ffl::mul(ffl::ff{S2[j].x, S2[j].y}, gm));
+      GB2[j] = make_float2(v.hi, v.lo);
+    }
     __syncwarp();
   }
-  for (int i = lane; i < n; i += 32) F[i] = FB[i] + lam;
-  for (int j = lane; j < m; j += 32) G[j] = GB[j] - lam;
+  const double ld = ffl::to_double(lam);
+  for (int i = lane; i < n; i += 32) F[i] = ffl::to_double(ffl::ff{FB2[i].x, FB2[i].y}) + ld;
+  for (int j = lane; j < m; j += 32) G[j] = ffl::to_double(ffl::ff{GB2[j].x, GB2[j].y}) - ld;
   if (lane == 0) status[k] = UOT_OK;
 }
 
