@@ -94,10 +94,12 @@ __device__ ffl::ff log_dot_exp_neg(const float* __restrict__ w, const float2* v,
 
 // |x - y|^p as a float pair: x - y exactly (two_sum), then its square (p = 2),
 // its magnitude (p = 1), or an FP64 power for other p
-__device__ __forceinline__ ffl::ff cost_ff(float xi, float yj, double p) {
+// (pmode: 2 for p = 2, 1 for p = 1, 0 otherwise, decided once outside the walk, whose every
+// comparison of the FP64 p would otherwise take the slow FP64 pipe)
+__device__ __forceinline__ ffl::ff cost_ff(float xi, float yj, int pmode, double p) {
   const ffl::ff d = ffl::two_sum(xi, -yj);
-  if (p == 2.0) return ffl::mul(d, d);
-  if (p == 1.0) return d.hi < 0.f ? ffl::neg(d) : d;
+  if (pmode == 2) return ffl::mul(d, d);
+  if (pmode == 1) return d.hi < 0.f ? ffl::neg(d) : d;
   return ffl::from_double(pow(fabs((double)d.hi + (double)d.lo), p));
 }
 
@@ -192,9 +194,10 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
       // and mass of both sides are loaded ahead of each decision.
       float2* R2 = reinterpret_cast<float2*>(R);
       float2* S2 = reinterpret_cast<float2*>(S);
+      const int pmode = p == 2.0 ? 2 : (p == 1.0 ? 1 : 0);
       int i = 0, j = 0;
       float xi = X[0], yj = Y[0];
-      ffl::ff ri{0.f, 0.f}, sj = cost_ff(xi, yj, p);
+      ffl::ff ri{0.f, 0.f}, sj = cost_ff(xi, yj, pmode, p);
       R2[0] = make_float2(0.f, 0.f);
       S2[0] = make_float2(sj.hi, sj.lo);
       ffl::ff dm = ffl::add(ffl::ff{BT2[0].x, BT2[0].y}, ffl::neg(ffl::ff{AT2[0].x, AT2[0].y}));
@@ -208,14 +211,14 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
           dm = ffl::add(dm, ffl::ff{-na.x, -na.y});
           xi = nx;
           if (i + 1 < n) { na = AT2[i + 1]; nx = X[i + 1]; }
-          ri = ffl::add(cost_ff(xi, yj, p), ffl::neg(sj));
+          ri = ffl::add(cost_ff(xi, yj, pmode, p), ffl::neg(sj));
           R2[i] = make_float2(ri.hi, ri.lo);
         } else {
           ++j;
           dm = ffl::add(dm, ffl::ff{nb.x, nb.y});
           yj = ny;
           if (j + 1 < m) { nb = BT2[j + 1]; ny = Y[j + 1]; }
-          sj = ffl::add(cost_ff(xi, yj, p), ffl::neg(ri));
+          sj = ffl::add(cost_ff(xi, yj, pmode, p), ffl::neg(ri));
           S2[j] = make_float2(sj.hi, sj.lo);
         }
       }
