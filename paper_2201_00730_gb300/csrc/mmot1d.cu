@@ -1,5 +1,7 @@
 // 1-D unbalanced multi-marginal OT and barycenters (Sec. 5) by Frank-Wolfe on
-// the translation-invariant functional H, batched: one warp per problem, FP64.
+// the translation-invariant functional H, batched: one warp per problem, in
+// float pairs (about 44 bits; FP64 runs at a small fraction of the FP32 rate on
+// this GPU, and the walk's dependent FP64 chain bounded the kernel).
 //
 // A problem has K measures (x_k, alpha_k) on the line with sorted points,
 // barycentric weights omega_k >= 0 summing to one, the rho KL penalties and
@@ -19,8 +21,11 @@
 //   fb_k <- (1 - tau_t) fb_k + tau_t r_k,  tau_t = 2 / (2 + t).
 // The output is the translated pair f_k = fb_k + lambda_k and the barycenter of
 // the plan that SolveMOT returns at the final iterate: the points B(tuple) of
-// its tuples of positive mass, with those masses as weights.  The walk runs in
-// FP64 with the oracle's order of operations, so its branches are the same.
+// its tuples of positive mass, with those masses as weights.  The walk keeps the
+// oracle's order of operations on float pairs and the re-weighted masses divided
+// by their common mass (no comparison sees the factor; the output masses are
+// multiplied back), so its branches are the oracle's except within about 1e-13
+// of a tie.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -28,6 +33,7 @@
 #include <string>
 #include <vector>
 
+#include "ffloat.cuh"
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -48,89 +54,140 @@ __device__ __forceinline__ double mm_warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double mm_warp_max(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+
+using ffl::ff;
+
+__device__ __forceinline__ ff ld_ff(const float2* p, long long i) {
+  const float2 v = p[i];
+  return ff{v.x, v.y};
+}
+__device__ __forceinline__ void st_ff(float2* p, long long i, ff v) { p[i] = make_float2(v.hi, v.lo); }
+// a < b and a > 0 for normalised float pairs
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool ff_pos(ff a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
+__device__ __forceinline__ ff ff_max(ff a, ff b) { return ff_lt(a, b) ? b : a; }
+__device__ __forceinline__ ff mm_warp_sum_ff(ff v) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ffl::add(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+__device__ __forceinline__ ff mm_warp_max_ff(ff v) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_max(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
   return v;
 }
 
-// log <w, e^{-v / c}> over the entries with w > 0 (largest exponent taken out first)
-__device__ double mm_log_dot_exp(const float* __restrict__ w, const double* v, int n, double c, int lane) {
-  double mx = -INFINITY;
-  for (int i = lane; i < n; i += 32)
-    if (w[i] > 0.f) mx = fmax(mx, -v[i] / c);
-  mx = mm_warp_max(mx);
-  double sm = 0.0;
-  for (int i = lane; i < n; i += 32)
-    if (w[i] > 0.f) sm += (double)w[i] * exp(-v[i] / c - mx);
-  sm = mm_warp_sum(sm);
-  return mx + log(sm);
+constexpr double kMMLog2e = 1.44269504088896340736;
+constexpr ff kMMLog2eff{(float)kMMLog2e, (float)(kMMLog2e - (double)(float)kMMLog2e)};
+
+// w e^y for w >= 0 and a float pair y with w e^y <= 1 (y may be large when w is tiny): the power
+// of two is split off first so that the table exp2 stays within its range
+__device__ __forceinline__ ff mm_w_exp(float w, ff y) {
+  ff z = ffl::mul(y, kMMLog2eff);
+  float sc = 1.f;
+  if (z.hi > 60.f) {
+    const float k = ceilf(z.hi) - 60.f;
+    z = ffl::add(z, -k);
+    sc = ffl::pow2f((int)k);
+  }
+  return ffl::mul(ffl::exp2(z), w * sc);
 }
 
-// lambda_k of the K-marginal rho KL dual at the potentials v (all lanes get them)
+// log <w, e^{-v cinv}> over the entries with w > 0 (largest exponent taken out first)
+__device__ ff mm_log_dot_exp(const float* __restrict__ w, const float2* v, int n, ff cinv, int lane) {
+  ff mx{-INFINITY, 0.f};
+  for (int i = lane; i < n; i += 32)
+    if (w[i] > 0.f) mx = ff_max(mx, ffl::neg(ffl::mul(ld_ff(v, i), cinv)));
+  mx = mm_warp_max_ff(mx);
+  ff sm{0.f, 0.f};
+  for (int i = lane; i < n; i += 32)
+    if (w[i] > 0.f) {
+      const ff e = ffl::add(ffl::neg(ffl::mul(ld_ff(v, i), cinv)), ffl::neg(mx));
+      sm = ffl::add(sm, ffl::mul(ffl::exp2(ffl::mul(e, kMMLog2eff)), w[i]));
+    }
+  sm = mm_warp_sum_ff(sm);
+  return ffl::add(mx, ffl::log_ff(sm));
+}
+
+// Per-problem constants as float pairs (the FP64 work done once): omega_k, 1 / (omega_k rho),
+// omega_k rho and omega_k / sum_l omega_l.
 template <int K>
-__device__ void mm_lambda(const MMProb& P, const float* __restrict__ alpha, double* const (&v)[K], int lane,
-                          double (&lam)[K]) {
-  double q[K], wsum = 0.0, s = 0.0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) q[k] = mm_log_dot_exp(alpha + P.off[k], v[k], P.n[k], P.omega[k] * P.rho, lane);
+struct MMConst {
+  ff w[K], cinv[K], orho[K], ofrac[K];
+};
+
+// lambda_k of the K-marginal rho KL dual at the potentials v (all lanes get them), and q_k
+template <int K>
+__device__ void mm_lambda(const MMProb& P, const MMConst<K>& C, const float* __restrict__ alpha,
+                          float2* const (&v)[K], int lane, ff (&lam)[K], ff (&q)[K]) {
+  ff s{0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    wsum += P.omega[k];
-    s += P.omega[k] * P.rho * q[k];
+    q[k] = mm_log_dot_exp(alpha + P.off[k], v[k], P.n[k], C.cinv[k], lane);
+    s = ffl::add(s, ffl::mul(C.orho[k], q[k]));
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) lam[k] = P.omega[k] * P.rho * q[k] - P.omega[k] / wsum * s;
+  for (int k = 0; k < K; ++k) lam[k] = ffl::add(ffl::mul(C.orho[k], q[k]), ffl::neg(ffl::mul(C.ofrac[k], s)));
 }
 
-// C(z) = sum_k omega_k (z_k - B(z))^2 and B(z), in the oracle's order of operations
+// C(z) = sum_k omega_k (z_k - B(z))^2 and B(z), in the oracle's order of operations (float pairs)
 template <int K>
-__device__ __forceinline__ double mm_cost(const double (&z)[K], const double (&w)[K], double* bary) {
-  double b = 0.0;
+__device__ __forceinline__ ff mm_cost(const float (&z)[K], const ff (&w)[K], ff* bary) {
+  ff b{0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < K; ++k) b += w[k] * z[k];
-  double c = 0.0;
+  for (int k = 0; k < K; ++k) b = ffl::add(b, ffl::mul(w[k], z[k]));
+  ff c{0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < K; ++k) c += w[k] * ((z[k] - b) * (z[k] - b));
-  if (bary) *bary = b;
+  for (int k = 0; k < K; ++k) {
+    const ff d = ffl::add(ffl::neg(b), z[k]);
+    c = ffl::add(c, ffl::mul(w[k], ffl::mul(d, d)));
+  }
+  *bary = b;
   return c;
 }
 
-// SolveMOT (Alg. 3) on lane 0 between the re-weighted measures at[k]; writes the
-// potentials r[k]; with bx / bw (nullable) also the plan's barycenter points and
-// masses (tuples of positive mass, in plan order), returning their number.
+// SolveMOT (Alg. 3) on lane 0 between the re-weighted measures at[k] (divided by their common mass,
+// which no comparison sees); writes the potentials r[k]; with bx / bw (nullable) also the plan's
+// barycenter points and masses (tuples of positive mass, in plan order; the masses times mscale,
+// the common mass), returning their number.  Float pairs: the branches are the oracle's except
+// within about 1e-13 of a tie between remaining masses.
 template <int K>
-__device__ int mm_walk(const MMProb& P, const float* __restrict__ x, double* const (&at)[K], double* const (&r)[K],
-                       double* bx, double* bw) {
-  double w[K], z[K], rem[K], cur[K];
+__device__ int mm_walk(const MMProb& P, const MMConst<K>& C, const float* __restrict__ x, float2* const (&at)[K],
+                       float2* const (&r)[K], double* bx, double* bw, ff mscale) {
+  float z[K];
+  ff rem[K], cur[K];
   int idx[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    w[k] = P.omega[k];
     idx[k] = 0;
-    z[k] = (double)x[P.off[k]];
-    rem[k] = at[k][0];
-    r[k][0] = 0.0;
-    cur[k] = 0.0;
+    z[k] = x[P.off[k]];
+    rem[k] = ld_ff(at[k], 0);
+    st_ff(r[k], 0, ff{0.f, 0.f});
+    cur[k] = ff{0.f, 0.f};
   }
-  double b = 0.0;
-  r[0][0] = mm_cost<K>(z, w, &b);
-  cur[0] = r[0][0];
+  ff b;
+  cur[0] = mm_cost<K>(z, C.w, &b);
+  st_ff(r[0], 0, cur[0]);
   int nb = 0;
   for (;;) {
     // the measure with the least remaining mass among those that can still move
     int p = -1;
+    ff mass{0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (idx[k] < P.n[k] - 1 && (p < 0 || rem[k] < rem[p])) p = k;
+      if (idx[k] < P.n[k] - 1 && (p < 0 || ff_lt(rem[k], mass))) {
+        p = k;
+        mass = rem[k];
+      }
     if (p < 0) break;
-    const double mass = rem[p];
-    if (bx && mass > 0.0) {
-      bx[nb] = b;
-      bw[nb] = mass;
+    if (bx && ff_pos(mass)) {
+      bx[nb] = ffl::to_double(b);
+      bw[nb] = ffl::to_double(ffl::mul(mass, mscale));
       ++nb;
     }
+    const ff nm = ffl::neg(mass);
 #pragma unroll
-    for (int k = 0; k < K; ++k) rem[k] = rem[k] - mass;
+    for (int k = 0; k < K; ++k) rem[k] = ffl::add(rem[k], nm);
     // the new point of measure p; the potentials of the others stay where they are
     int np = 0;
 #pragma unroll
@@ -139,24 +196,24 @@ __device__ int mm_walk(const MMProb& P, const float* __restrict__ x, double* con
     const long long op = P.off[p];
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (k == p) z[k] = (double)x[op + np];
-    const double c = mm_cost<K>(z, w, &b);
-    double others = 0.0;
+      if (k == p) z[k] = x[op + np];
+    const ff c = mm_cost<K>(z, C.w, &b);
+    ff others{0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (k != p) others += cur[k];
-    const double v = c - others;
+      if (k != p) others = ffl::add(others, cur[k]);
+    const ff v = ffl::add(c, ffl::neg(others));
 #pragma unroll
     for (int k = 0; k < K; ++k)
       if (k == p) {
         cur[k] = v;
-        rem[k] = at[k][np];
+        rem[k] = ld_ff(at[k], np);
       }
-    r[p][np] = v;
+    st_ff(r[p], np, v);
   }
-  if (bx && rem[0] > 0.0) {
-    bx[nb] = b;  // the last tuple takes the mass left
-    bw[nb] = rem[0];
+  if (bx && ff_pos(rem[0])) {
+    bx[nb] = ffl::to_double(b);  // the last tuple takes the mass left
+    bw[nb] = ffl::to_double(ffl::mul(rem[0], mscale));
     ++nb;
   }
   return nb;
@@ -171,15 +228,16 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
   const int pk = blockIdx.x * kMMWarps + (threadIdx.x >> 5);
   if (pk >= count) return;  // whole warp
   const MMProb P = probs[pk];
-  double* FB[K];
-  double* AT[K];
-  double* R[K];
+  // working vectors as float pairs in the double-sized slots of the workspace
+  float2* FB[K];
+  float2* AT[K];
+  float2* R[K];
   bool bad_w = false, bad_x = false;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    FB[k] = fb_all + P.off[k];
-    AT[k] = at_all + P.off[k];
-    R[k] = r_all + P.off[k];
+    FB[k] = reinterpret_cast<float2*>(fb_all + P.off[k]);
+    AT[k] = reinterpret_cast<float2*>(at_all + P.off[k]);
+    R[k] = reinterpret_cast<float2*>(r_all + P.off[k]);
     const float* X = x + P.off[k];
     const float* A = alpha + P.off[k];
     double tot = 0.0;
@@ -203,38 +261,65 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
     }
     return;
   }
+  MMConst<K> C;
+  {
+    double wsum = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) wsum += P.omega[k];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      C.w[k] = ffl::from_double(P.omega[k]);
+      C.cinv[k] = ffl::from_double(1.0 / (P.omega[k] * P.rho));
+      C.orho[k] = ffl::from_double(P.omega[k] * P.rho);
+      C.ofrac[k] = ffl::from_double(P.omega[k] / wsum);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    for (int i = lane; i < P.n[k]; i += 32) FB[k][i] = 0.0;
+    for (int i = lane; i < P.n[k]; i += 32) st_ff(FB[k], i, ff{0.f, 0.f});
   __syncwarp();
-  double lam[K];
+  ff lam[K], q[K], lnm{0.f, 0.f};
+  // a~_k = alpha_k e^{-(fb_k + lambda_k) / (omega_k rho)} divided by their common mass m
+  // (ln m = q_0 - lambda_0 / (omega_0 rho)), which keeps them <= 1
   auto reweight = [&]() {
-    mm_lambda<K>(P, alpha, FB, lane, lam);
+    mm_lambda<K>(P, C, alpha, FB, lane, lam, q);
+    lnm = ffl::add(q[0], ffl::neg(ffl::mul(lam[0], C.cinv[0])));
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const float* A = alpha + P.off[k];
-      const double c = P.omega[k] * P.rho;
-      for (int i = lane; i < P.n[k]; i += 32) AT[k][i] = (double)A[i] * exp(-(FB[k][i] + lam[k]) / c);
+      for (int i = lane; i < P.n[k]; i += 32) {
+        ff v{0.f, 0.f};
+        if (A[i] > 0.f) {
+          const ff e = ffl::add(ffl::neg(ffl::mul(ffl::add(ld_ff(FB[k], i), lam[k]), C.cinv[k])), ffl::neg(lnm));
+          v = mm_w_exp(A[i], e);
+        }
+        st_ff(AT[k], i, v);
+      }
     }
     __syncwarp();
   };
   for (int t = 0; t < n_iter; ++t) {
     reweight();
-    if (lane == 0) (void)mm_walk<K>(P, x, AT, R, nullptr, nullptr);
+    if (lane == 0) (void)mm_walk<K>(P, C, x, AT, R, nullptr, nullptr, ff{1.f, 0.f});
     __syncwarp();
-    const double tau = 2.0 / (2.0 + (double)t);
+    const ff tau = ffl::from_double(2.0 / (2.0 + (double)t));
+    const ff t1 = ffl::add(ffl::neg(tau), 1.f);
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      for (int i = lane; i < P.n[k]; i += 32) FB[k][i] = (1.0 - tau) * FB[k][i] + tau * R[k][i];
+      for (int i = lane; i < P.n[k]; i += 32)
+        st_ff(FB[k], i, ffl::add(ffl::mul(ld_ff(FB[k], i), t1), ffl::mul(ld_ff(R[k], i), tau)));
     __syncwarp();
   }
   // the translated potentials, and the barycenter of the plan at the final iterate
   reweight();
 #pragma unroll
-  for (int k = 0; k < K; ++k)
-    for (int i = lane; i < P.n[k]; i += 32) f[P.off[k] + i] = FB[k][i] + lam[k];
+  for (int k = 0; k < K; ++k) {
+    const double lk = ffl::to_double(lam[k]);
+    for (int i = lane; i < P.n[k]; i += 32) f[P.off[k] + i] = ffl::to_double(ld_ff(FB[k], i)) + lk;
+  }
   if (lane == 0) {
-    blen[pk] = mm_walk<K>(P, x, AT, R, bx + P.bofs, bw + P.bofs);
+    const ff m = ffl::exp2(ffl::mul(lnm, kMMLog2eff));
+    blen[pk] = mm_walk<K>(P, C, x, AT, R, bx + P.bofs, bw + P.bofs, m);
     status[pk] = UOT_OK;
   }
 }
