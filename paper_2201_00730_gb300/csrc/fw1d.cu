@@ -4,14 +4,13 @@
 //   lambda* = rho1 rho2 / (rho1 + rho2) (log<a, e^{-fb/rho1}> - log<b, e^{-gb/rho2}>)   (Prop. 2)
 //   a~ = a e^{-(fb + lambda*)/rho1},  b~ = b e^{-(gb - lambda*)/rho2}              (Eq. fw-updated-histo)
 // with all lanes (a~ and b~ divided by their common mass, which the walk does
-// not see), then lane 0 walks the two sorted point lists once to get the
-// duals (r, s) of the balanced 1-D OT between a~ and b~ (SolveOT1D, Alg. 1:
-// the point whose remaining mass is smaller is exhausted first, and each newly
-// reached point's potential is the current pair's cost minus the other side's
-// current potential), and all lanes take the step
+// not see), then the warp walks the two sorted point lists to get the duals
+// (r, s) of the balanced 1-D OT between a~ and b~ (SolveOT1D, Alg. 1: the point
+// whose remaining mass is smaller is exhausted first, and each newly reached
+// point's potential is the current pair's cost minus the other side's current
+// potential) as a merge path split over the lanes, and all lanes take the step
 //   (fb, gb) <- (1 - gamma_t)(fb, gb) + gamma_t (r, s),  gamma_t = 2 / (2 + t).
-// The walk is sequential by nature (O(N + M) dependent steps, one float-pair
-// add each); the batch supplies the parallelism.  Working vectors live in the
+// The batch supplies the rest of the parallelism.  Working vectors live in the
 // workspace, indexed by the problems' offsets (a~ and b~ in shared memory when
 // the problem is small enough).
 #include <cuda_runtime.h>
@@ -103,6 +102,42 @@ __device__ __forceinline__ ffl::ff cost_ff(float xi, float yj, int pmode, double
   return ffl::from_double(pow(fabs((double)d.hi + (double)d.lo), p));
 }
 
+// a < b for normalised float pairs
+__device__ __forceinline__ bool ff_lt(float2 a, float2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
+
+// v[0..n) <- its inclusive prefix sums, float pairs, on one warp (a contiguous chunk per lane,
+// the chunk totals scanned across the lanes)
+__device__ void prefix_sum_ff(float2* v, int n, int lane) {
+  const int c = (n + 31) / 32, b = min(n, lane * c), e = min(n, b + c);
+  ffl::ff t{0.f, 0.f};
+  for (int k = b; k < e; ++k) t = ffl::add(t, ffl::ff{v[k].x, v[k].y});
+  for (int o = 1; o < 32; o <<= 1) {
+    const float h = __shfl_up_sync(0xffffffffu, t.hi, o), l = __shfl_up_sync(0xffffffffu, t.lo, o);
+    if (lane >= o) t = ffl::add(t, ffl::ff{h, l});
+  }
+  // the sum of the chunks before this lane's
+  const float h = __shfl_up_sync(0xffffffffu, t.hi, 1), l = __shfl_up_sync(0xffffffffu, t.lo, 1);
+  ffl::ff run = lane == 0 ? ffl::ff{0.f, 0.f} : ffl::ff{h, l};
+  for (int k = b; k < e; ++k) {
+    run = ffl::add(run, ffl::ff{v[k].x, v[k].y});
+    v[k] = make_float2(run.hi, run.lo);
+  }
+}
+
+// The number of A-events among the first s events of the merge of A_0..A_{n-2} and B_0..B_{m-2}
+// (ties to A): the largest i in [max(0, s - (m-1)), min(s, n-1)] with A_{i-1} <= B_{s-i}, a B index
+// past m - 2 counting as +infinity (the predicate holds at the lower end and falls with i).
+__device__ int merge_i(const float2* A, int n, const float2* B, int m, int s) {
+  int lo = max(0, s - (m - 1)), hi = min(s, n - 1);
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const bool ok = (s - mid >= m - 1) || !ff_lt(B[s - mid], A[mid - 1]);
+    if (ok) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(32 * kFWWarps)
 k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const float* __restrict__ x,
        const float* __restrict__ a, const float* __restrict__ y, const float* __restrict__ b, double* fb_all,
@@ -185,40 +220,71 @@ k_fw1d(const FWProb* __restrict__ probs, int count, int n_iter, double p, const 
       BT2[j] = make_float2(v.hi, v.lo);
     }
     __syncwarp();
-    if (lane == 0) {
-      // SolveOT1D, the duals of the north-west corner coupling.  The masses not yet
-      // transported enter only through dm = m_j - m_i: "point i is exhausted first" is
-      // m_i <= m_j, i.e. dm >= 0; the next dm is dm - a~_{i+1} after i moves, dm + b~_{j+1}
-      // after j moves, each a float-pair sum, so the walk takes the oracle's branches except
-      // where dm is within ~1e-13 of a tie.  The potentials run in float pairs; the next point
-      // and mass of both sides are loaded ahead of each decision.
+    // SolveOT1D, the duals of the north-west corner coupling, on the whole warp.  With A_i, B_j
+    // the partial sums of a~ and b~, the untransported masses at (i, j) differ by B_j - A_i, so
+    // "point i is exhausted first" is A_i <= B_j: the walk's path is the merge of the sorted
+    // sequences A_0..A_{N-2} and B_0..B_{M-2} (ties to A).  Each lane takes an equal share of
+    // the N + M - 2 steps, finds its starting point by a binary search on that merge, and walks
+    // it; a newly reached point's potential is the current pair's cost minus the other side's
+    // potential, so a share maps its starting i-potential x to c + sigma x (sigma = +-1), and a
+    // warp scan of those maps gives every share its starting value before the second walk,
+    // which writes the potentials.  Branches are the oracle's except within ~1e-13 of a tie.
+    prefix_sum_ff(AT2, n, lane);
+    prefix_sum_ff(BT2, m, lane);
+    __syncwarp();
+    {
+      const int pmode = p == 2.0 ? 2 : (p == 1.0 ? 1 : 0);
+      const int steps = (n - 1) + (m - 1);
+      const int s0 = (int)((long long)lane * steps / 32), s1 = (int)((long long)(lane + 1) * steps / 32);
+      const int i0 = merge_i(AT2, n, BT2, m, s0), j0 = s0 - i0;
+      // first walk: the share's map of its starting i-potential
+      ffl::ff cR{0.f, 0.f}, cS = cost_ff(X[i0], Y[j0], pmode, p);
+      float sgR = 1.f, sgS = -1.f;
+      {
+        int i = i0, j = j0;
+        for (int st = s0; st < s1; ++st) {
+          if (i < n - 1 && (j == m - 1 || !ff_lt(BT2[j], AT2[i]))) {
+            ++i;
+            cR = ffl::add(cost_ff(X[i], Y[j], pmode, p), ffl::neg(cS));
+            sgR = -sgS;
+          } else {
+            ++j;
+            cS = ffl::add(cost_ff(X[i], Y[j], pmode, p), ffl::neg(cR));
+            sgS = -sgR;
+          }
+        }
+      }
+      // inclusive scan of the maps x -> c + sigma x, composed in walk order
+      ffl::ff c = cR;
+      float sg = sgR;
+      for (int o = 1; o < 32; o <<= 1) {
+        const float ch = __shfl_up_sync(0xffffffffu, c.hi, o), cl = __shfl_up_sync(0xffffffffu, c.lo, o);
+        const float sp = __shfl_up_sync(0xffffffffu, sg, o);
+        if (lane >= o) {
+          c = ffl::add(c, ffl::ff{sg * ch, sg * cl});
+          sg *= sp;
+        }
+      }
+      // the share's starting i-potential: the composition over the lanes before it, applied to r_0 = 0
+      float rh = __shfl_up_sync(0xffffffffu, c.hi, 1), rl = __shfl_up_sync(0xffffffffu, c.lo, 1);
+      if (lane == 0) rh = rl = 0.f;
+      // second walk: the potentials
       float2* R2 = reinterpret_cast<float2*>(R);
       float2* S2 = reinterpret_cast<float2*>(S);
-      const int pmode = p == 2.0 ? 2 : (p == 1.0 ? 1 : 0);
-      int i = 0, j = 0;
-      float xi = X[0], yj = Y[0];
-      ffl::ff ri{0.f, 0.f}, sj = cost_ff(xi, yj, pmode, p);
-      R2[0] = make_float2(0.f, 0.f);
-      S2[0] = make_float2(sj.hi, sj.lo);
-      ffl::ff dm = ffl::add(ffl::ff{BT2[0].x, BT2[0].y}, ffl::neg(ffl::ff{AT2[0].x, AT2[0].y}));
-      float2 na = n > 1 ? AT2[1] : make_float2(0.f, 0.f), nb = m > 1 ? BT2[1] : make_float2(0.f, 0.f);
-      float nx = n > 1 ? X[1] : 0.f, ny = m > 1 ? Y[1] : 0.f;
-      while (i < n - 1 || j < m - 1) {
-        // dm >= 0 (its sign is the sign of hi, or of lo when hi is 0)
-        const bool ge = dm.hi > 0.f || (dm.hi == 0.f && dm.lo >= 0.f);
-        if ((ge && i < n - 1) || j == m - 1) {
+      ffl::ff ri{rh, rl}, sj = ffl::add(cost_ff(X[i0], Y[j0], pmode, p), ffl::ff{-rh, -rl});
+      if (lane == 0) {
+        R2[0] = make_float2(0.f, 0.f);
+        S2[0] = make_float2(sj.hi, sj.lo);
+      }
+      int i = i0, j = j0;
+      for (int st = s0; st < s1; ++st) {
+        if (i < n - 1 && (j == m - 1 || !ff_lt(BT2[j], AT2[i]))) {
           ++i;
-          dm = ffl::add(dm, ffl::ff{-na.x, -na.y});
-          xi = nx;
-          if (i + 1 < n) { na = AT2[i + 1]; nx = X[i + 1]; }
-          ri = ffl::add(cost_ff(xi, yj, pmode, p), ffl::neg(sj));
+          ri = ffl::add(cost_ff(X[i], Y[j], pmode, p), ffl::neg(sj));
           R2[i] = make_float2(ri.hi, ri.lo);
         } else {
           ++j;
-          dm = ffl::add(dm, ffl::ff{nb.x, nb.y});
-          yj = ny;
-          if (j + 1 < m) { nb = BT2[j + 1]; ny = Y[j + 1]; }
-          sj = ffl::add(cost_ff(xi, yj, pmode, p), ffl::neg(ri));
+          sj = ffl::add(cost_ff(X[i], Y[j], pmode, p), ffl::neg(ri));
           S2[j] = make_float2(sj.hi, sj.lo);
         }
       }
