@@ -14,12 +14,14 @@
 // O accumulates in TMEM without any rescaling.  Output: the partials of the
 // moment sweeps, (m_i + R_i, sum_j mult_j P_ij, moments) per (row, slot).
 //
-// Roles (one CTA per SM, 17 warps): lane 0 of warp 16 issues the copies and
-// MMAs; warps 0..15 read the S accumulators (warp w: TMEM lanes 32 (w % 4) ..
-// +31, key quarter w / 4 of each 128-key tile), keep the maxima, form P and
-// the value sums, write P, and at the end of a segment read O.  Handoffs on
-// mbarriers, every wait bounded (a wait that gives up stops every role; the
-// issuer then lets every copy and MMA in flight land).
+// Roles (one CTA per SM, 18 warps): lane 0 of warp 16 issues the MMAs, lane 0
+// of warp 17 the copies (each buffer refilled once the MMAs that read it have
+// completed, which the MMAs signal through tcgen05.commit); warps 0..15 read the
+// S accumulators (warp w: TMEM lanes 32 (w % 4) .. +31, key quarter w / 4 of
+// each 128-key tile), keep the maxima, form P and the value sums, write P, and
+// at the end of a segment read O.  Handoffs on mbarriers, every wait bounded (a
+// wait that gives up stops every role; each issuing role then lets its own
+// copies or MMAs in flight land).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -40,7 +42,8 @@ constexpr int kKeys = 128;     // keys per tile (N of S, K of O)
 constexpr int kStages = 2;     // key-tile and Z-tile buffers
 constexpr int kMaxChunk = 4096;  // keys per CTA (H and mult in shared memory)
 constexpr int kConsWarps = 16;
-constexpr int kAllThreads = 32 * (kConsWarps + 1);
+constexpr int kMmaWarp = kConsWarps, kCopyWarp = kConsWarps + 1;  // the MMA and copy issuers
+constexpr int kAllThreads = 32 * (kConsWarps + 2);
 constexpr uint32_t kColS = 0;      // two 128-column S accumulators
 constexpr uint32_t kColPh = 256;   // P hi: 64 columns (128 keys, two FP16 a column)
 constexpr uint32_t kColPl = 320;   // P lo
@@ -114,6 +117,9 @@ struct MBars {
   uint64_t s_empty[2];        // the consumers read an S accumulator
   uint64_t p_full;            // the consumers wrote P
   uint64_t o_done[2];         // O MMAs of a pass-2 tile completed (by parity of the pass-2 count)
+  uint64_t a_free;            // the S MMAs of a row block's last job completed (A may be replaced)
+  uint64_t b_free[kStages];   // the S MMAs that read a key stage completed
+  uint64_t z_free[kStages];   // the O MMAs that read a Z^T stage completed
   uint32_t tmem;
   int err;
   float hq[3][kRows];         // column quarters 1..3 of a row: maxima, then sums
@@ -206,6 +212,11 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
       tc::mbar_init(&br.o_done[b], 1);
     }
     tc::mbar_init(&br.p_full, kConsWarps);
+    tc::mbar_init(&br.a_free, 1);
+    for (int b = 0; b < kStages; ++b) {
+      tc::mbar_init(&br.b_free[b], 1);
+      tc::mbar_init(&br.z_free[b], 1);
+    }
     tc::fence_mbar_init();
     br.err = 0;
   }
@@ -256,32 +267,61 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
   tc::fence_after_sync();
   const uint32_t tmem = br.tmem;
   volatile int* err = &br.err;
-  const int NJ = jb.njobs, NP = jb.npass2;
+  const int NJ = jb.njobs;
 
-  if (warp == kConsWarps) {
-    // ------------------------------------------------------------------ issuer
+  if (warp == kCopyWarp) {
+    // --------------------------------------------------------------- producer
+    // (copies in job order: job j's query block, key tile and, in pass 2, Z^T tile, each once the
+    // MMAs that read its buffer before have completed; all of those belong to earlier jobs)
     if (lane == 0) {
-      int b_arm[kStages] = {}, b_use[kStages] = {}, z_arm[kStages] = {}, z_use[kStages] = {};
-      int a_arm = 0, a_use = 0;
-      int s_commit = -1, s_seen = -1, o_commit = -1, o_seen = -1;
-      auto copy_b = [&](int j) {
-        const int st = j % kStages;
-        copy_pieces(B + (size_t)st * bytesB, reinterpret_cast<const char*>(opk) + (size_t)jb.jt[j] * bytesB, bytesB,
-                    &br.b_full[st]);
-        ++b_arm[st];
-      };
-      auto copy_z = [&](int n) {
-        const int st = n % kStages;
-        copy_pieces(Z + (size_t)st * bytesZ, reinterpret_cast<const char*>(zt) + (size_t)jb.ztile[n] * bytesZ, bytesZ,
-                    &br.z_full[st]);
-        ++z_arm[st];
-      };
-      if (NJ > 0) {
-        copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)jb.jr[0] * bytesA, bytesA, &br.a_full);
-        ++a_arm;
+      int b_arm[kStages] = {}, z_arm[kStages] = {};
+      int a_arm = 0, nfree = 0, np = 0;
+      for (int j = 0; j < NJ && !*err; ++j) {
+        const bool pass2 = jb.jf[j] & 1;
+        bool ok = true;
+        if (j == 0 || jb.jr[j] != jb.jr[j - 1]) {
+          if (j > 0) {
+            ok = tc::mbar_wait(&br.a_free, (uint32_t)(nfree & 1), spin);
+            ++nfree;
+          }
+          if (!ok) { *err = 1; break; }
+          copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)jb.jr[j] * bytesA, bytesA, &br.a_full);
+          ++a_arm;
+        }
+        {
+          const int st = j % kStages;
+          if (j >= kStages && !tc::mbar_wait(&br.b_free[st], (uint32_t)(((j - kStages) / kStages) & 1), spin)) {
+            *err = 1;
+            break;
+          }
+          copy_pieces(B + (size_t)st * bytesB, reinterpret_cast<const char*>(opk) + (size_t)jb.jt[j] * bytesB, bytesB,
+                      &br.b_full[st]);
+          ++b_arm[st];
+        }
+        if (pass2) {
+          const int zs = np % kStages;
+          if (np >= kStages && !tc::mbar_wait(&br.z_free[zs], (uint32_t)(((np - kStages) / kStages) & 1), spin)) {
+            *err = 1;
+            break;
+          }
+          copy_pieces(Z + (size_t)zs * bytesZ, reinterpret_cast<const char*>(zt) + (size_t)jb.ztile[np] * bytesZ,
+                      bytesZ, &br.z_full[zs]);
+          ++z_arm[zs];
+          ++np;
+        }
       }
-      for (int j = 0; j < NJ && j < kStages; ++j) copy_b(j);
-      for (int n = 0; n < NP && n < kStages; ++n) copy_z(n);
+      // this role's copies land before the CTA ends, whoever stopped (each barrier's latest phase; bounded)
+      if (a_arm > 0) (void)tc::mbar_wait(&br.a_full, (uint32_t)((a_arm - 1) & 1), kSpin);
+      for (int st = 0; st < kStages; ++st) {
+        if (b_arm[st] > 0) (void)tc::mbar_wait(&br.b_full[st], (uint32_t)((b_arm[st] - 1) & 1), kSpin);
+        if (z_arm[st] > 0) (void)tc::mbar_wait(&br.z_full[st], (uint32_t)((z_arm[st] - 1) & 1), kSpin);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    // -------------------------------------------------------------------- MMA
+    if (lane == 0) {
+      int a_use = 0, s_commit = -1, o_commit = -1;
       const uint64_t dAh = tc::smem_desc(tc::smem_addr(A), 128, sbo);
       const uint64_t dAl = dAh + (uint64_t)(KS * 16);
       const uint32_t idS = tc::idesc_f16(kRows, kKeys), idO = tc::idesc_f16(kRows, dim16);
@@ -290,20 +330,11 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
         const int st = j % kStages, b = j % 2;
         const bool pass2 = jb.jf[j] & 1;
         bool ok = true;
-        if (j > 0 && jb.jr[j] != jb.jr[j - 1]) {
-          // new row block: its rows replace A once the S MMAs of job j - 1, the last to read A, completed
-          ok = tc::mbar_wait(&br.s_done[(j - 1) % 2], (uint32_t)(((j - 1) / 2) & 1), spin);
-          if (!ok) { *err = 1; break; }
-          s_seen = j - 1 > s_seen ? j - 1 : s_seen;
-          copy_pieces(A, reinterpret_cast<const char*>(opq) + (size_t)jb.jr[j] * bytesA, bytesA, &br.a_full);
-          ++a_arm;
-        }
-        if (a_use < a_arm) {
+        if (j == 0 || jb.jr[j] != jb.jr[j - 1]) {
           ok = tc::mbar_wait(&br.a_full, (uint32_t)(a_use & 1), spin);
-          if (ok) ++a_use;
+          ++a_use;
         }
         ok = ok && tc::mbar_wait(&br.b_full[st], (uint32_t)((j / kStages) & 1), spin);
-        if (ok) ++b_use[st];
         ok = ok && (j < 2 || tc::mbar_wait(&br.s_empty[b], (uint32_t)(((j - 2) / 2) & 1), spin));
         if (!ok) { *err = 1; break; }
         tc::fence_after_sync();
@@ -318,18 +349,13 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
 #pragma unroll
           for (int k = 0; k < KS; ++k) tc::mma_f16(d, dAh + 16 * k, dBl + 16 * k, idS, true);
           tc::commit(&br.s_done[b]);
+          tc::commit(&br.b_free[st]);
+          if (j == NJ - 1 || jb.jr[j + 1] != jb.jr[j]) tc::commit(&br.a_free);
           s_commit = j;
-        }
-        // key stage of job j - 1 -> job j - 1 + kStages, once the S MMAs of job j - 1 completed
-        if (j >= 1 && j - 1 + kStages < NJ) {
-          if (!tc::mbar_wait(&br.s_done[(j - 1) % 2], (uint32_t)(((j - 1) / 2) & 1), spin)) { *err = 1; break; }
-          s_seen = j - 1 > s_seen ? j - 1 : s_seen;
-          copy_b(j - 1 + kStages);
         }
         if (pass2) {
           const int zs = np % kStages;
           ok = tc::mbar_wait(&br.z_full[zs], (uint32_t)((np / kStages) & 1), spin);
-          if (ok) ++z_use[zs];
           ok = ok && tc::mbar_wait(&br.p_full, (uint32_t)(np & 1), spin);
           if (!ok) { *err = 1; break; }
           tc::fence_after_sync();
@@ -345,28 +371,17 @@ k_sweep_umma_mom(const __half* __restrict__ opq, const float* __restrict__ nq2, 
 #pragma unroll
           for (int k = 0; k < kKeys / 16; ++k) tc::mma_f16_tmem_a(d, tmem + kColPh + 8 * k, dZl + 16 * k, idO, true);
           tc::commit(&br.o_done[np % 2]);
+          tc::commit(&br.z_free[zs]);
           o_commit = np;
-          // Z stage of pass-2 job np - 1 -> np - 1 + kStages, once its O MMAs completed
-          if (np >= 1 && np - 1 + kStages < NP) {
-            if (!tc::mbar_wait(&br.o_done[(np - 1) % 2], (uint32_t)(((np - 1) / 2) & 1), spin)) { *err = 1; break; }
-            o_seen = np - 1 > o_seen ? np - 1 : o_seen;
-            copy_z(np - 1 + kStages);
-          }
           ++np;
         }
       }
-      if (*err) {
-        // drain: copies armed but not consumed, MMAs committed but not seen complete (bounded)
-        for (; a_use < a_arm; ++a_use) (void)tc::mbar_wait(&br.a_full, (uint32_t)(a_use & 1), kSpin);
-        for (int st = 0; st < kStages; ++st) {
-          for (; b_use[st] < b_arm[st]; ++b_use[st]) (void)tc::mbar_wait(&br.b_full[st], (uint32_t)(b_use[st] & 1), kSpin);
-          for (; z_use[st] < z_arm[st]; ++z_use[st]) (void)tc::mbar_wait(&br.z_full[st], (uint32_t)(z_use[st] & 1), kSpin);
-        }
-        for (int j = s_seen + 1; j <= s_commit; ++j)
-          if (j + 2 > s_commit) (void)tc::mbar_wait(&br.s_done[j % 2], (uint32_t)((j / 2) & 1), kSpin);
-        for (int n = o_seen + 1; n <= o_commit; ++n)
-          if (n + 2 > o_commit) (void)tc::mbar_wait(&br.o_done[n % 2], (uint32_t)((n / 2) & 1), kSpin);
-      }
+      // the MMAs committed complete before the CTA ends, whoever stopped (the latest phase of each
+      // barrier; immediate when the consumers saw them; bounded)
+      for (int j = s_commit - 1; j <= s_commit; ++j)
+        if (j >= 0) (void)tc::mbar_wait(&br.s_done[j % 2], (uint32_t)((j / 2) & 1), kSpin);
+      for (int n = o_commit - 1; n <= o_commit; ++n)
+        if (n >= 0) (void)tc::mbar_wait(&br.o_done[n % 2], (uint32_t)((n / 2) & 1), kSpin);
     }
     __syncwarp();
   } else {
