@@ -7,7 +7,8 @@
 // barycentric weights omega_k >= 0 summing to one, the rho KL penalties and
 // the squared-distance ground cost, whose multi-marginal form is
 //   C(z_1..z_K) = sum_k omega_k (z_k - B(z))^2,  B(z) = sum_k omega_k z_k.
-// Each Frank-Wolfe step computes, with all lanes,
+// Each Frank-Wolfe step computes, with all lanes (the SolveMOT walk too: a
+// merge path over the warp, see mm_walk),
 //   q_k = log <alpha_k, e^{-fb_k / (omega_k rho)}>,
 //   lambda_k = omega_k rho q_k - omega_k / (sum_l omega_l) sum_l omega_l rho q_l
 //     (the optimal translation of the K-marginal dual, Sec. 5, rho KL setting),
@@ -30,6 +31,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -41,6 +43,9 @@ namespace {
 
 constexpr int kMMWarps = 4;  // problems per CTA
 constexpr int kMMMaxK = 8;   // measures per problem
+// a problem with at most this many points in all keeps its re-weighted masses (and their partial
+// sums, which the walk's rank searches probe) in shared memory
+constexpr int kMMSmemPoints = 2048;
 
 struct MMProb {
   long long off[kMMMaxK];  // first point of each measure (x, alpha, f and the workspace vectors)
@@ -146,76 +151,253 @@ __device__ __forceinline__ ff mm_cost(const float (&z)[K], const ff (&w)[K], ff*
   return c;
 }
 
-// SolveMOT (Alg. 3) on lane 0 between the re-weighted measures at[k] (divided by their common mass,
-// which no comparison sees); writes the potentials r[k]; with bx / bw (nullable) also the plan's
-// barycenter points and masses (tuples of positive mass, in plan order; the masses times mscale,
-// the common mass), returning their number.  Float pairs: the branches are the oracle's except
-// within about 1e-13 of a tie between remaining masses.
+// v[0..n) <- its inclusive prefix sums, float pairs, on one warp (a contiguous chunk per lane,
+// the chunk totals scanned across the lanes).  A point of zero weight (w[i] == 0) then gets
+// exactly its predecessor's sum: the scan's association differs between chunks, and a sum that
+// differed in its last bits would turn that point's zero mass into a tiny positive one.
+__device__ void mm_prefix_sum(float2* v, const float* __restrict__ w, int n, int lane) {
+  const int c = (n + 31) / 32, b = min(n, lane * c), e = min(n, b + c);
+  ff t{0.f, 0.f};
+  int lnz = -1;  // the last point of nonzero weight in this lane's chunk
+  for (int k = b; k < e; ++k) {
+    t = ffl::add(t, ld_ff(v, k));
+    if (w[k] != 0.f) lnz = k;
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const float h = __shfl_up_sync(0xffffffffu, t.hi, o), l = __shfl_up_sync(0xffffffffu, t.lo, o);
+    const int z = __shfl_up_sync(0xffffffffu, lnz, o);
+    if (lane >= o) {
+      t = ffl::add(t, ff{h, l});
+      lnz = max(lnz, z);
+    }
+  }
+  const float h = __shfl_up_sync(0xffffffffu, t.hi, 1), l = __shfl_up_sync(0xffffffffu, t.lo, 1);
+  int carry = __shfl_up_sync(0xffffffffu, lnz, 1);  // the last nonzero point before this chunk
+  if (lane == 0) carry = -1;
+  ff run = lane == 0 ? ff{0.f, 0.f} : ff{h, l};
+  for (int k = b; k < e; ++k) {
+    run = ffl::add(run, ld_ff(v, k));
+    if (w[k] != 0.f) st_ff(v, k, run);
+  }
+  __syncwarp();
+  for (int k = b; k < e; ++k) {
+    if (w[k] == 0.f) st_ff(v, k, carry >= 0 ? ld_ff(v, carry) : ff{0.f, 0.f});
+    else carry = k;
+  }
+}
+
+// number of entries of the sorted a[0..n) that are <= v (le) or < v (!le)
+__device__ __forceinline__ int mm_count(const float2* a, int n, ff v, bool le) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const ff x = ld_ff(a, mid);
+    if (le ? !ff_lt(v, x) : ff_lt(x, v)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The walk's state after s steps: the events are (k, i) for i <= N_k - 2 with value A^k_i (the
+// partial sums), taken in (value, k, i) order.  Finds the event of rank s and returns in idx the
+// number of events of each measure before it (all N_k - 1 when s is past the last event).
 template <int K>
-__device__ int mm_walk(const MMProb& P, const MMConst<K>& C, const float* __restrict__ x, float2* const (&at)[K],
-                       float2* const (&r)[K], double* bx, double* bw, ff mscale) {
-  float z[K];
-  ff rem[K], cur[K];
-  int idx[K];
+__device__ void mm_state_at(const MMProb& P, float2* const (&A)[K], int s, int total, int (&idx)[K]) {
+  if (s >= total) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) idx[k] = P.n[k] - 1;
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    idx[k] = 0;
-    z[k] = x[P.off[k]];
-    rem[k] = ld_ff(at[k], 0);
-    st_ff(r[k], 0, ff{0.f, 0.f});
-    cur[k] = ff{0.f, 0.f};
+    int lo = 0, hi = P.n[k] - 2;
+    while (lo <= hi) {
+      const int i = (lo + hi) >> 1;
+      const ff v = ld_ff(A[k], i);
+      int r = i;
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (q != k) r += mm_count(A[q], P.n[q] - 1, v, q < k);
+      if (r == s) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) idx[q] = q == k ? i : mm_count(A[q], P.n[q] - 1, v, q < k);
+        return;
+      }
+      if (r < s) lo = i + 1;
+      else hi = i - 1;
+    }
   }
-  ff b;
-  cur[0] = mm_cost<K>(z, C.w, &b);
-  st_ff(r[0], 0, cur[0]);
-  int nb = 0;
-  for (;;) {
-    // the measure with the least remaining mass among those that can still move
-    int p = -1;
-    ff mass{0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < K; ++k) idx[k] = 0;  // not reached: every rank below the total has an event
+}
+
+// SolveMOT (Alg. 3) on the whole warp between the re-weighted measures (at[k]: the masses divided
+// by their common mass; replaced here by their partial sums A^k).  Every step takes the movable
+// measure of least A^k_{idx_k} (lowest index on ties), so the walk is the stable K-way merge of the
+// partial-sum sequences: each lane takes an equal share of the steps, finds its starting tuple by
+// a rank search on that merge, and walks it.  The current potentials always sum to the current
+// tuple's cost, so a newly reached point's potential is its measure's previous one plus the
+// change of that cost: a share shifts each measure's potential by a sum of cost changes, and a
+// warp scan of those K sums gives every share its starting potentials for the second walk, which
+// writes them.  With bx / bw (nullable) also the plan's barycenter points and masses (tuples of
+// positive mass in plan order, the masses times mscale; their places from a warp scan of the
+// shares' counts); returns their number (on every lane).  Float pairs: the branches are the
+// oracle's except within about 1e-13 of a tie between partial sums.
+template <int K>
+__device__ int mm_walk(const MMProb& P, const MMConst<K>& C, const float* __restrict__ x,
+                       const float* __restrict__ alpha, float2* const (&at)[K], float2* const (&r)[K], double* bx,
+                       double* bw, ff mscale, int lane) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) mm_prefix_sum(at[k], alpha + P.off[k], P.n[k], lane);
+  __syncwarp();
+  int total = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) total += P.n[k] - 1;
+  const int s0 = (int)((long long)lane * total / 32), s1 = (int)((long long)(lane + 1) * total / 32);
+  int idx0[K];
+  mm_state_at<K>(P, at, s0, total, idx0);
+  // the value of event s0 - 1 (the largest value among the events taken), 0 at the start
+  ff prev0{0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (idx0[k] > 0) prev0 = ff_max(prev0, ld_ff(at[k], idx0[k] - 1));
+  // first walk: each measure's summed cost changes, and the count of positive masses
+  ff d[K];
+  int npos = 0;
+  {
+    int idx[K];
+    float z[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      idx[k] = idx0[k];
+      z[k] = x[P.off[k] + idx[k]];
+      d[k] = ff{0.f, 0.f};
+    }
+    ff b, Cc = mm_cost<K>(z, C.w, &b), prev = prev0;
+    for (int st = s0; st < s1; ++st) {
+      int p = -1;
+      ff v{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (idx[k] < P.n[k] - 1) {
+          const ff a = ld_ff(at[k], idx[k]);
+          if (p < 0 || ff_lt(a, v)) { p = k; v = a; }
+        }
+      if (ff_pos(ffl::add(v, ffl::neg(prev)))) ++npos;
+      prev = v;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k == p) {
+          ++idx[k];
+          z[k] = x[P.off[k] + idx[k]];
+        }
+      const ff Cn = mm_cost<K>(z, C.w, &b);
+      const ff dc = ffl::add(Cn, ffl::neg(Cc));
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k == p) d[k] = ffl::add(d[k], dc);
+      Cc = Cn;
+    }
+  }
+  // exclusive scans over the lanes: starting potentials and output places
+  ff cur[K];
+  {
+    float z0[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) z0[k] = x[P.off[k]];
+    ff b0;
+    const ff c00 = mm_cost<K>(z0, C.w, &b0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      ff t = d[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const float h = __shfl_up_sync(0xffffffffu, t.hi, o), l = __shfl_up_sync(0xffffffffu, t.lo, o);
+        if (lane >= o) t = ffl::add(t, ff{h, l});
+      }
+      const float h = __shfl_up_sync(0xffffffffu, t.hi, 1), l = __shfl_up_sync(0xffffffffu, t.lo, 1);
+      const ff ex = lane == 0 ? ff{0.f, 0.f} : ff{h, l};
+      cur[k] = k == 0 ? ffl::add(c00, ex) : ex;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) st_ff(r[k], 0, k == 0 ? c00 : ff{0.f, 0.f});
+    }
+  }
+  int cnt = npos;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, cnt, o);
+    if (lane >= o) cnt += v;
+  }
+  const int all = __shfl_sync(0xffffffffu, cnt, 31);
+  int out = cnt - npos;
+  // second walk: the potentials (and the barycenter entries)
+  {
+    int idx[K];
+    float z[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      idx[k] = idx0[k];
+      z[k] = x[P.off[k] + idx[k]];
+    }
+    ff b, Cc = mm_cost<K>(z, C.w, &b), prev = prev0;
+    for (int st = s0; st < s1; ++st) {
+      int p = -1;
+      ff v{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (idx[k] < P.n[k] - 1) {
+          const ff a = ld_ff(at[k], idx[k]);
+          if (p < 0 || ff_lt(a, v)) { p = k; v = a; }
+        }
+      const ff mass = ffl::add(v, ffl::neg(prev));
+      if (ff_pos(mass)) {
+        if (bx) {
+          bx[out] = ffl::to_double(b);
+          bw[out] = ffl::to_double(ffl::mul(mass, mscale));
+        }
+        ++out;
+      }
+      prev = v;
+      int np = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k == p) {
+          np = ++idx[k];
+          z[k] = x[P.off[k] + idx[k]];
+        }
+      const ff Cn = mm_cost<K>(z, C.w, &b);
+      const ff dc = ffl::add(Cn, ffl::neg(Cc));
+      Cc = Cn;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k == p) {
+          cur[k] = ffl::add(cur[k], dc);
+          st_ff(r[k], np, cur[k]);
+        }
+    }
+  }
+  // the last tuple takes the mass left: A^0 at its last point minus the last event's value
+  int nb = all;
+  {
+    ff last{0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (idx[k] < P.n[k] - 1 && (p < 0 || ff_lt(rem[k], mass))) {
-        p = k;
-        mass = rem[k];
+      if (P.n[k] > 1) last = ff_max(last, ld_ff(at[k], P.n[k] - 2));
+    const ff mass = ffl::add(ld_ff(at[0], P.n[0] - 1), ffl::neg(last));
+    if (ff_pos(mass)) {
+      if (bx && lane == 0) {
+        float z[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) z[k] = x[P.off[k] + P.n[k] - 1];
+        ff b;
+        (void)mm_cost<K>(z, C.w, &b);
+        bx[all] = ffl::to_double(b);
+        bw[all] = ffl::to_double(ffl::mul(mass, mscale));
       }
-    if (p < 0) break;
-    if (bx && ff_pos(mass)) {
-      bx[nb] = ffl::to_double(b);
-      bw[nb] = ffl::to_double(ffl::mul(mass, mscale));
       ++nb;
     }
-    const ff nm = ffl::neg(mass);
-#pragma unroll
-    for (int k = 0; k < K; ++k) rem[k] = ffl::add(rem[k], nm);
-    // the new point of measure p; the potentials of the others stay where they are
-    int np = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (k == p) np = ++idx[k];
-    const long long op = P.off[p];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (k == p) z[k] = x[op + np];
-    const ff c = mm_cost<K>(z, C.w, &b);
-    ff others{0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (k != p) others = ffl::add(others, cur[k]);
-    const ff v = ffl::add(c, ffl::neg(others));
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (k == p) {
-        cur[k] = v;
-        rem[k] = ld_ff(at[k], np);
-      }
-    st_ff(r[p], np, v);
   }
-  if (bx && ff_pos(rem[0])) {
-    bx[nb] = ffl::to_double(b);  // the last tuple takes the mass left
-    bw[nb] = ffl::to_double(ffl::mul(rem[0], mscale));
-    ++nb;
-  }
+  __syncwarp();
   return nb;
 }
 
@@ -229,14 +411,21 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
   if (pk >= count) return;  // whole warp
   const MMProb P = probs[pk];
   // working vectors as float pairs in the double-sized slots of the workspace
+  extern __shared__ float2 mm_smem[];
   float2* FB[K];
   float2* AT[K];
   float2* R[K];
   bool bad_w = false, bad_x = false;
+  int npts = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) npts += P.n[k];
+  const bool in_smem = npts <= kMMSmemPoints;
+  int soff = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     FB[k] = reinterpret_cast<float2*>(fb_all + P.off[k]);
-    AT[k] = reinterpret_cast<float2*>(at_all + P.off[k]);
+    AT[k] = in_smem ? mm_smem + (threadIdx.x >> 5) * kMMSmemPoints + soff : reinterpret_cast<float2*>(at_all + P.off[k]);
+    soff += P.n[k];
     R[k] = reinterpret_cast<float2*>(r_all + P.off[k]);
     const float* X = x + P.off[k];
     const float* A = alpha + P.off[k];
@@ -300,7 +489,7 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
   };
   for (int t = 0; t < n_iter; ++t) {
     reweight();
-    if (lane == 0) (void)mm_walk<K>(P, C, x, AT, R, nullptr, nullptr, ff{1.f, 0.f});
+    (void)mm_walk<K>(P, C, x, alpha, AT, R, nullptr, nullptr, ff{1.f, 0.f}, lane);
     __syncwarp();
     const ff tau = ffl::from_double(2.0 / (2.0 + (double)t));
     const ff t1 = ffl::add(ffl::neg(tau), 1.f);
@@ -317,9 +506,10 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
     const double lk = ffl::to_double(lam[k]);
     for (int i = lane; i < P.n[k]; i += 32) f[P.off[k] + i] = ffl::to_double(ld_ff(FB[k], i)) + lk;
   }
+  const ff m = ffl::exp2(ffl::mul(lnm, kMMLog2eff));
+  const int nb = mm_walk<K>(P, C, x, alpha, AT, R, bx + P.bofs, bw + P.bofs, m, lane);
   if (lane == 0) {
-    const ff m = ffl::exp2(ffl::mul(lnm, kMMLog2eff));
-    blen[pk] = mm_walk<K>(P, C, x, AT, R, bx + P.bofs, bw + P.bofs, m);
+    blen[pk] = nb;
     status[pk] = UOT_OK;
   }
 }
@@ -387,10 +577,19 @@ uot_status validate_mm(const uot_mmot1d_batch* b, MMLayout* L) {
   } while (0)
 
 template <int K>
-void launch_mm(int blocks, cudaStream_t st, const MMProb* probs, int count, int n_iter, const float* x,
-               const float* alpha, double* fb, double* at, double* r, double* f, double* bx, double* bw, int* blen,
-               int* status) {
-  k_mmot1d<K><<<blocks, 32 * kMMWarps, 0, st>>>(probs, count, n_iter, x, alpha, fb, at, r, f, bx, bw, blen, status);
+cudaError_t launch_mm(int blocks, cudaStream_t st, const MMProb* probs, int count, int n_iter, const float* x,
+                      const float* alpha, double* fb, double* at, double* r, double* f, double* bx, double* bw,
+                      int* blen, int* status) {
+  constexpr size_t smem = sizeof(float2) * kMMWarps * kMMSmemPoints;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_mmot1d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr != cudaSuccess) return attr;
+  k_mmot1d<K><<<blocks, 32 * kMMWarps, smem, st>>>(probs, count, n_iter, x, alpha, fb, at, r, f, bx, bw, blen,
+                                                   status);
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -446,15 +645,17 @@ uot_status uot_mmot1d_batched(const uot_mmot1d_batch* b, double* f, double* bary
   double* r = reinterpret_cast<double*>(base + L.r);
   MMCUDA(cudaMemcpyAsync(d_probs, probs.data(), sizeof(MMProb) * count, cudaMemcpyHostToDevice, st));
   const int blocks = (count + kMMWarps - 1) / kMMWarps;
+  cudaError_t le = cudaSuccess;
   switch (K) {
-    case 2: launch_mm<2>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 3: launch_mm<3>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 4: launch_mm<4>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 5: launch_mm<5>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 6: launch_mm<6>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 7: launch_mm<7>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    default: launch_mm<8>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status);
+    case 2: le = launch_mm<2>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
+    case 3: le = launch_mm<3>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
+    case 4: le = launch_mm<4>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
+    case 5: le = launch_mm<5>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
+    case 6: le = launch_mm<6>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
+    case 7: le = launch_mm<7>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
+    default: le = launch_mm<8>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status);
   }
+  MMCUDA(le);
   note_launch();
   MMCUDA(cudaGetLastError());
   std::vector<int> hs(count), hl(count);
