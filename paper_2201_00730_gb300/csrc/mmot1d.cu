@@ -198,39 +198,6 @@ __device__ __forceinline__ int mm_count(const float2* a, int n, ff v, bool le) {
   return lo;
 }
 
-// The walk's state after s steps: the events are (k, i) for i <= N_k - 2 with value A^k_i (the
-// partial sums), taken in (value, k, i) order.  Finds the event of rank s and returns in idx the
-// number of events of each measure before it (all N_k - 1 when s is past the last event).
-template <int K>
-__device__ void mm_state_at(const MMProb& P, float2* const (&A)[K], int s, int total, int (&idx)[K]) {
-  if (s >= total) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) idx[k] = P.n[k] - 1;
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    int lo = 0, hi = P.n[k] - 2;
-    while (lo <= hi) {
-      const int i = (lo + hi) >> 1;
-      const ff v = ld_ff(A[k], i);
-      int r = i;
-#pragma unroll
-      for (int q = 0; q < K; ++q)
-        if (q != k) r += mm_count(A[q], P.n[q] - 1, v, q < k);
-      if (r == s) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) idx[q] = q == k ? i : mm_count(A[q], P.n[q] - 1, v, q < k);
-        return;
-      }
-      if (r < s) lo = i + 1;
-      else hi = i - 1;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) idx[k] = 0;  // not reached: every rank below the total has an event
-}
-
 // SolveMOT (Alg. 3) on the whole warp between the re-weighted measures (at[k]: the masses divided
 // by their common mass; replaced here by their partial sums A^k).  Every step takes the movable
 // measure of least A^k_{idx_k} (lowest index on ties), so the walk is the stable K-way merge of the
@@ -245,8 +212,8 @@ __device__ void mm_state_at(const MMProb& P, float2* const (&A)[K], int s, int t
 // oracle's except within about 1e-13 of a tie between partial sums.
 template <int K>
 __device__ int mm_walk(const MMProb& P, const MMConst<K>& C, const float* __restrict__ x,
-                       const float* __restrict__ alpha, float2* const (&at)[K], float2* const (&r)[K], double* bx,
-                       double* bw, ff mscale, int lane) {
+                       const float* __restrict__ alpha, float2* const (&at)[K], int* const (&rk)[K],
+                       float2* const (&r)[K], double* bx, double* bw, ff mscale, int lane) {
 #pragma unroll
   for (int k = 0; k < K; ++k) mm_prefix_sum(at[k], alpha + P.off[k], P.n[k], lane);
   __syncwarp();
@@ -254,8 +221,32 @@ __device__ int mm_walk(const MMProb& P, const MMConst<K>& C, const float* __rest
 #pragma unroll
   for (int k = 0; k < K; ++k) total += P.n[k] - 1;
   const int s0 = (int)((long long)lane * total / 32), s1 = (int)((long long)(lane + 1) * total / 32);
+  // the rank of every event in the merge, all lanes over all events (uniform work): event (k, i)
+  // comes after i events of its own measure, the events of lower measures of value <= its own and
+  // those of higher measures of smaller value
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int i = lane; i < P.n[k] - 1; i += 32) {
+      const ff v = ld_ff(at[k], i);
+      int rnk = i;
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (q != k) rnk += mm_count(at[q], P.n[q] - 1, v, q < k);
+      rk[k][i] = rnk;
+    }
+  __syncwarp();
+  // the lane's starting tuple: per measure, the number of its events of rank below s0
   int idx0[K];
-  mm_state_at<K>(P, at, s0, total, idx0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int lo = 0, hi = P.n[k] - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (rk[k][mid] < s0) lo = mid + 1;
+      else hi = mid;
+    }
+    idx0[k] = lo;
+  }
   // the value of event s0 - 1 (the largest value among the events taken), 0 at the start
   ff prev0{0.f, 0.f};
 #pragma unroll
@@ -404,7 +395,8 @@ __device__ int mm_walk(const MMProb& P, const MMConst<K>& C, const float* __rest
 template <int K>
 __global__ void __launch_bounds__(32 * kMMWarps)
 k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* __restrict__ x,
-         const float* __restrict__ alpha, double* fb_all, double* at_all, double* r_all, double* __restrict__ f,
+         const float* __restrict__ alpha, double* fb_all, double* at_all, double* r_all, int* rk_all,
+         double* __restrict__ f,
          double* __restrict__ bx, double* __restrict__ bw, int* __restrict__ blen, int* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int pk = blockIdx.x * kMMWarps + (threadIdx.x >> 5);
@@ -415,6 +407,7 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
   float2* FB[K];
   float2* AT[K];
   float2* R[K];
+  int* RK[K];
   bool bad_w = false, bad_x = false;
   int npts = 0;
 #pragma unroll
@@ -425,6 +418,8 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
   for (int k = 0; k < K; ++k) {
     FB[k] = reinterpret_cast<float2*>(fb_all + P.off[k]);
     AT[k] = in_smem ? mm_smem + (threadIdx.x >> 5) * kMMSmemPoints + soff : reinterpret_cast<float2*>(at_all + P.off[k]);
+    RK[k] = in_smem ? reinterpret_cast<int*>(mm_smem + kMMWarps * kMMSmemPoints) + (threadIdx.x >> 5) * kMMSmemPoints + soff
+                    : rk_all + P.off[k];
     soff += P.n[k];
     R[k] = reinterpret_cast<float2*>(r_all + P.off[k]);
     const float* X = x + P.off[k];
@@ -489,7 +484,7 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
   };
   for (int t = 0; t < n_iter; ++t) {
     reweight();
-    (void)mm_walk<K>(P, C, x, alpha, AT, R, nullptr, nullptr, ff{1.f, 0.f}, lane);
+    (void)mm_walk<K>(P, C, x, alpha, AT, RK, R, nullptr, nullptr, ff{1.f, 0.f}, lane);
     __syncwarp();
     const ff tau = ffl::from_double(2.0 / (2.0 + (double)t));
     const ff t1 = ffl::add(ffl::neg(tau), 1.f);
@@ -507,7 +502,7 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
     for (int i = lane; i < P.n[k]; i += 32) f[P.off[k] + i] = ffl::to_double(ld_ff(FB[k], i)) + lk;
   }
   const ff m = ffl::exp2(ffl::mul(lnm, kMMLog2eff));
-  const int nb = mm_walk<K>(P, C, x, alpha, AT, R, bx + P.bofs, bw + P.bofs, m, lane);
+  const int nb = mm_walk<K>(P, C, x, alpha, AT, RK, R, bx + P.bofs, bw + P.bofs, m, lane);
   if (lane == 0) {
     blen[pk] = nb;
     status[pk] = UOT_OK;
@@ -517,7 +512,7 @@ k_mmot1d(const MMProb* __restrict__ probs, int count, int n_iter, const float* _
 size_t mm_align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct MMLayout {
-  size_t probs, status, blen, fb, at, r, total;
+  size_t probs, status, blen, fb, at, r, rk, total;
   long long lx;    // length of the packed point arrays
   long long lb;    // length of the packed barycenter arrays
 };
@@ -561,6 +556,7 @@ uot_status validate_mm(const uot_mmot1d_batch* b, MMLayout* L) {
   L->fb = take(sizeof(double) * lx);
   L->at = take(sizeof(double) * lx);
   L->r = take(sizeof(double) * lx);
+  L->rk = take(sizeof(int) * lx);
   L->total = off;
   L->lx = lx;
   L->lb = lb;
@@ -578,17 +574,17 @@ uot_status validate_mm(const uot_mmot1d_batch* b, MMLayout* L) {
 
 template <int K>
 cudaError_t launch_mm(int blocks, cudaStream_t st, const MMProb* probs, int count, int n_iter, const float* x,
-                      const float* alpha, double* fb, double* at, double* r, double* f, double* bx, double* bw,
-                      int* blen, int* status) {
-  constexpr size_t smem = sizeof(float2) * kMMWarps * kMMSmemPoints;
+                      const float* alpha, double* fb, double* at, double* r, int* rk, double* f, double* bx,
+                      double* bw, int* blen, int* status) {
+  constexpr size_t smem = (sizeof(float2) + sizeof(int)) * kMMWarps * kMMSmemPoints;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
     attr = cudaFuncSetAttribute(k_mmot1d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr != cudaSuccess) return attr;
-  k_mmot1d<K><<<blocks, 32 * kMMWarps, smem, st>>>(probs, count, n_iter, x, alpha, fb, at, r, f, bx, bw, blen,
-                                                   status);
+  k_mmot1d<K><<<blocks, 32 * kMMWarps, smem, st>>>(probs, count, n_iter, x, alpha, fb, at, r, rk, f, bx, bw,
+                                                   blen, status);
   return cudaSuccess;
 }
 
@@ -643,17 +639,18 @@ uot_status uot_mmot1d_batched(const uot_mmot1d_batch* b, double* f, double* bary
   double* fb = reinterpret_cast<double*>(base + L.fb);
   double* at = reinterpret_cast<double*>(base + L.at);
   double* r = reinterpret_cast<double*>(base + L.r);
+  int* rk = reinterpret_cast<int*>(base + L.rk);
   MMCUDA(cudaMemcpyAsync(d_probs, probs.data(), sizeof(MMProb) * count, cudaMemcpyHostToDevice, st));
   const int blocks = (count + kMMWarps - 1) / kMMWarps;
   cudaError_t le = cudaSuccess;
   switch (K) {
-    case 2: le = launch_mm<2>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 3: le = launch_mm<3>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 4: le = launch_mm<4>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 5: le = launch_mm<5>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 6: le = launch_mm<6>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    case 7: le = launch_mm<7>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status); break;
-    default: le = launch_mm<8>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, f, bary_x, bary_w, d_blen, d_status);
+    case 2: le = launch_mm<2>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status); break;
+    case 3: le = launch_mm<3>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status); break;
+    case 4: le = launch_mm<4>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status); break;
+    case 5: le = launch_mm<5>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status); break;
+    case 6: le = launch_mm<6>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status); break;
+    case 7: le = launch_mm<7>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status); break;
+    default: le = launch_mm<8>(blocks, st, d_probs, count, b->n_iter, b->x, b->alpha, fb, at, r, rk, f, bary_x, bary_w, d_blen, d_status);
   }
   MMCUDA(le);
   note_launch();
