@@ -44,7 +44,7 @@ namespace {
 constexpr int kMMWarps = 4;  // problems per CTA
 constexpr int kMMMaxK = 8;   // measures per problem
 // a problem with at most this many points in all keeps its re-weighted masses (and their partial
-// sums, which the walk's rank searches probe) in shared memory
+// sums and the ranks of the walk's events) in shared memory
 constexpr int kMMSmemPoints = 2048;
 
 struct MMProb {
@@ -201,8 +201,8 @@ __device__ __forceinline__ int mm_count(const float2* a, int n, ff v, bool le) {
 // SolveMOT (Alg. 3) on the whole warp between the re-weighted measures (at[k]: the masses divided
 // by their common mass; replaced here by their partial sums A^k).  Every step takes the movable
 // measure of least A^k_{idx_k} (lowest index on ties), so the walk is the stable K-way merge of the
-// partial-sum sequences: each lane takes an equal share of the steps, finds its starting tuple by
-// a rank search on that merge, and walks it.  The current potentials always sum to the current
+// partial-sum sequences: the lanes rank every event of that merge together, each lane takes an
+// equal share of the steps, reads its starting tuple off the ranks, and walks it.  The current potentials always sum to the current
 // tuple's cost, so a newly reached point's potential is its measure's previous one plus the
 // change of that cost: a share shifts each measure's potential by a sum of cost changes, and a
 // warp scan of those K sums gives every share its starting potentials for the second walk, which
